@@ -1,0 +1,186 @@
+"""CPU oracle for the dense full-tableau simplex (arXiv 2211.10979, Section III).
+
+TEST INFRASTRUCTURE ONLY: the tests, ``__graft_entry__.smoke()`` and the
+CPU-baseline leg of ``bench.py`` may import this package; the library's product
+path never does.  The arithmetic lives in ``simplex_oracle.c`` (plain C, FP64,
+single-threaded); this module only compiles it with gcc and marshals arrays.
+
+Every step follows the paper's Section III in order: the Initialization Step
+(Table I tableau with the slack basis), Step 1 (Dantzig entering column),
+Step 2 (minimum-ratio leaving row), Step 3 (pivoting) and the
+Iterate/Finalization Step.  The readings taken where the paper is silent are
+listed in the C file's header.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "simplex_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle_simplex.so")
+_lock = threading.Lock()
+_lib = None
+
+OPTIMAL, UNBOUNDED, ITER_LIMIT, NUMERIC, INVALID = 0, 1, 2, 3, -1
+STATUS_NAMES = {0: "OPTIMAL", 1: "UNBOUNDED", 2: "ITER_LIMIT", 3: "NUMERIC", -1: "INVALID"}
+
+
+class _Opts(ctypes.Structure):
+    _fields_ = [
+        ("rule", ctypes.c_int),
+        ("eps_d", ctypes.c_double),
+        ("eps_p", ctypes.c_double),
+        ("max_iters", ctypes.c_long),
+        ("k_cyc", ctypes.c_int),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile simplex_oracle.c into a shared library next to it (gcc)."""
+    with _lock:
+        if (not force and os.path.exists(_LIB)
+                and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+            return _LIB
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.orc_build.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, dp, ip]
+        lib.orc_build.restype = ctypes.c_int
+        lib.orc_entering.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_double]
+        lib.orc_entering.restype = ctypes.c_int
+        lib.orc_leaving.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, ctypes.c_int,
+                                    ctypes.c_int, ctypes.c_double, dp]
+        lib.orc_leaving.restype = ctypes.c_int
+        lib.orc_pivot.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int, dp, dp]
+        lib.orc_pivot.restype = None
+        lib.orc_solve.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, ctypes.POINTER(_Opts),
+                                  ctypes.POINTER(ctypes.c_long), ip, ip, ctypes.c_long]
+        lib.orc_solve.restype = ctypes.c_int
+        lib.orc_extract.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, dp, dp, dp]
+        lib.orc_extract.restype = None
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _ip(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+@dataclass
+class Options:
+    rule: int = 0            # 0 = Dantzig + Bland fallback, 1 = Bland
+    eps_d: float = 1e-9
+    eps_p: float = 1e-9
+    max_iters: int = -1      # -1 = 50 (m + n)
+    k_cyc: int = 50
+
+    def c(self) -> _Opts:
+        return _Opts(self.rule, self.eps_d, self.eps_p, self.max_iters, self.k_cyc)
+
+
+@dataclass
+class Result:
+    status: int
+    iters: int
+    x: np.ndarray
+    y: np.ndarray
+    obj: float
+    basis: np.ndarray
+    qlog: np.ndarray
+    plog: np.ndarray
+    T: np.ndarray
+
+
+def build_tableau(A, b, c):
+    """Initialization Step: returns (T (m+1) x (n+m+1), basis[m])."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    m, n = A.shape
+    T = np.empty((m + 1, n + m + 1), dtype=np.float64)
+    basis = np.empty(m, dtype=np.int32)
+    rc = _load().orc_build(m, n, _dp(A), _dp(b), _dp(c), _dp(T), _ip(basis))
+    if rc != 0:
+        raise ValueError("invalid LP (need m, n > 0 and finite b >= 0)")
+    return T, basis
+
+
+def entering(T, m, n, bland=False, eps_d=1e-9) -> int:
+    """Step 1 on tableau T; -1 if optimal."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    return int(_load().orc_entering(m, n, _dp(T), int(bland), eps_d))
+
+
+def leaving(T, basis, m, n, q, bland=False, eps_p=1e-9):
+    """Step 2 on tableau T and column q; returns (p, min ratio), p = -1 if unbounded."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    basis = np.ascontiguousarray(basis, dtype=np.int32)
+    ratio = ctypes.c_double(0.0)
+    p = _load().orc_leaving(m, n, _dp(T), _ip(basis), q, int(bland), eps_p, ctypes.byref(ratio))
+    return int(p), ratio.value
+
+
+def pivot(T, m, n, p, q):
+    """Step 3 in place on a C-contiguous float64 tableau."""
+    assert T.flags.c_contiguous and T.dtype == np.float64
+    r = np.empty(T.shape[1], dtype=np.float64)
+    f = np.empty(T.shape[0], dtype=np.float64)
+    _load().orc_pivot(m, n, _dp(T), p, q, _dp(r), _dp(f))
+
+
+def solve_tableau(T, basis, m, n, opts: Options | None = None, log_cap: int = 1 << 20):
+    """Iterate Steps 1-3 in place on (T, basis); returns (status, iters, qlog, plog)."""
+    opts = opts or Options()
+    assert T.flags.c_contiguous and T.dtype == np.float64
+    assert basis.flags.c_contiguous and basis.dtype == np.int32
+    cap = int(log_cap)
+    qlog = np.full(cap, -1, dtype=np.int32)
+    plog = np.full(cap, -1, dtype=np.int32)
+    it = ctypes.c_long(0)
+    o = opts.c()
+    st = _load().orc_solve(m, n, _dp(T), _ip(basis), ctypes.byref(o), ctypes.byref(it),
+                           _ip(qlog), _ip(plog), cap)
+    k = min(it.value, cap)
+    return int(st), int(it.value), qlog[:k].copy(), plog[:k].copy()
+
+
+def extract(T, basis, m, n):
+    """x (n), y (m), objective from a tableau."""
+    x = np.empty(n, dtype=np.float64)
+    y = np.empty(m, dtype=np.float64)
+    obj = ctypes.c_double(0.0)
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    basis = np.ascontiguousarray(basis, dtype=np.int32)
+    _load().orc_extract(m, n, _dp(T), _ip(basis), _dp(x), _dp(y), ctypes.byref(obj))
+    return x, y, obj.value
+
+
+def solve(A, b, c, opts: Options | None = None, log_cap: int = 1 << 20) -> Result:
+    """Full solve: Initialization Step, then Steps 1-3 until termination."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    m, n = A.shape
+    T, basis = build_tableau(A, b, c)
+    st, it, qlog, plog = solve_tableau(T, basis, m, n, opts, log_cap)
+    x, y, obj = extract(T, basis, m, n)
+    return Result(st, it, x, y, obj, basis, qlog, plog, T)
