@@ -1,0 +1,174 @@
+/*
+ * tabsimplex.h -- C ABI of the GB300 (sm_103a) dense full-tableau simplex.
+ *
+ * The method is the standard full-tableau simplex of arXiv 2211.10979,
+ * Section III: maximize c^T x subject to A x <= b, x >= 0 (A is m x n), started
+ * from the slack basis of Table I, then per iteration
+ *   Step 1  entering column: most negative objective-row coefficient (Dantzig),
+ *   Step 2  leaving row: minimum ratio rhs_i / T[i][q] over T[i][q] > 0,
+ *   Step 3  pivoting: T[i][j] -= T[i][q] * T[p][j] / T[p][q] for i != p and the
+ *           pivot row divided by T[p][q],
+ * until no negative coefficient is left (optimal) or column q has no positive
+ * entry (unbounded) (Section III, Iterate/Finalization Step).
+ *
+ * Tableau layout on the device (one per handle): (m + 1) rows x W = n + m + 1
+ * logical columns, row-major with a padded leading dimension.  Row 0 is the
+ * objective row [-c, 0 | z]; rows 1..m are [A, I_m | b].  The constant z column
+ * of Table I is not stored (it never changes).  Variable indices are 0-based:
+ * 0..n-1 are x_1..x_n, n..n+m-1 are the slacks of constraints 1..m.
+ *
+ * Threads: calls on one handle are not thread-safe; distinct handles are
+ * independent.  Every function that can fail records a message retrievable with
+ * lp_last_error() on the calling thread.
+ *
+ * Device memory comes from the allocator installed with lp_set_allocator()
+ * (default: cudaMallocAsync/cudaFreeAsync on the handle's stream).
+ */
+#ifndef TABSIMPLEX_H
+#define TABSIMPLEX_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Opaque handle: owns the device tableau and all work buffers of one LP. */
+typedef struct lp_handle *lp_t;
+
+/* Termination status and error codes.  Non-negative values are outcomes of the
+ * iteration (Section III, Iterate/Finalization Step, plus the guards added
+ * here); negative values are errors. */
+typedef enum {
+    LP_OPTIMAL = 0,      /* no objective-row entry below -eps_d                 */
+    LP_UNBOUNDED = 1,    /* entering column has no entry above eps_p            */
+    LP_ITER_LIMIT = 2,   /* max_iters pivots done, not yet optimal              */
+    LP_ERR_NUMERIC = 3,  /* pivot element or minimum ratio not finite           */
+    LP_ERR_INVALID = -1, /* bad argument (sizes, NULL, b < 0, non-finite data)  */
+    LP_ERR_NOMEM = -2,   /* device allocation failed                            */
+    LP_ERR_CUDA = -3,    /* a CUDA runtime call failed                          */
+    LP_ERR_TIMEOUT = -4, /* a device-wide barrier wait exceeded its time limit  */
+    LP_ERR_STATE = -5    /* call out of order (e.g. solution before a solve)    */
+} lp_status;
+
+enum { LP_RULE_DANTZIG = 0, LP_RULE_BLAND = 1 };
+enum { LP_PATH_AUTO = 0, LP_PATH_PERSISTENT = 1, LP_PATH_MULTILAUNCH = 2 };
+
+/* Solve options.  Initialise with lp_options_init() and change fields. */
+typedef struct {
+    int rule;                     /* LP_RULE_DANTZIG (with Bland fallback on
+                                     cycling) or LP_RULE_BLAND                  */
+    double eps_d;                 /* Step 1: column j may enter iff
+                                     T[0][j] < -eps_d (default 1e-9)            */
+    double eps_p;                 /* Step 2: row i is eligible iff
+                                     T[i][q] > eps_p (default 1e-9)             */
+    long long max_iters;          /* pivot cap; < 0 means 50 (m + n)            */
+    int k_cyc;                    /* consecutive pivots with minimum ratio <= 0
+                                     before switching to Bland's rule until the
+                                     next positive-ratio pivot; <= 0 disables
+                                     (default 50)                               */
+    long long barrier_timeout_ns; /* limit of one device-wide barrier wait
+                                     (default 2e9 ns); on expiry the solve ends
+                                     with LP_ERR_TIMEOUT                        */
+    int path;                     /* LP_PATH_AUTO: persistent cooperative kernel
+                                     when it can be launched, else one launch
+                                     per phase                                  */
+    int skip_zero_columns;        /* 1 (default): Step 3 leaves untouched every
+                                     32-byte group of columns whose scaled pivot
+                                     row entries are all zero (their update is
+                                     the identity); 0: update every column      */
+    int threads;                  /* threads per block, 0 = default (256)       */
+    int blocks;                   /* grid size cap, 0 = all co-resident blocks  */
+    long long log_capacity;       /* pivots whose (q, p) pair is recorded;
+                                     0 = none                                   */
+    void *stream;                 /* cudaStream_t to run on; NULL = the
+                                     handle's own stream                        */
+} lp_options;
+
+/* Per-solve measurements (device time from CUDA events on the solve stream). */
+typedef struct {
+    long long iters;              /* pivots performed                           */
+    double build_ms;              /* tableau build (Initialization Step)        */
+    double pivot_ms;              /* all pivot kernels (Steps 1-3 + iterate)    */
+    long long kernel_launches;    /* kernels launched by the solve              */
+    double dense_update_bytes;    /* sum over pivots of 2 (m+1) W s bytes       */
+    double update_bytes;          /* sum over pivots of the bytes Step 3 has to
+                                     move: 64 (m + 1) bytes per 32-byte column
+                                     group it updates (read + write)            */
+    int path;                     /* LP_PATH_PERSISTENT or LP_PATH_MULTILAUNCH  */
+    int grid;                     /* blocks of the pivot kernels                */
+    int block;                    /* threads per block                          */
+    int ld;                       /* leading dimension of the tableau (elems)   */
+} lp_stats;
+
+/* Fill *opt with the defaults listed above.  NULL is ignored. */
+void lp_options_init(lp_options *opt);
+
+/* Create an LP from HOST arrays (Section III problem statement, Table I):
+ * A is m x n row-major, b has m entries, c has n entries, all float64.  The
+ * data are copied to the device; the caller keeps ownership of its arrays.
+ * Requires m > 0, n > 0, every entry finite and b >= 0 (the slack basis must be
+ * feasible: Section III, Initialization Step; no phase I).  Returns NULL on
+ * error (see lp_last_error()).  Runs on the current CUDA device. */
+lp_t lp_create(int m, int n, const double *A, const double *b, const double *c);
+
+/* Same as lp_create with DEVICE pointers (current device).  The arrays are
+ * referenced, not copied: they must stay valid and unchanged until
+ * lp_destroy.  `stream` (cudaStream_t, may be NULL for the legacy default
+ * stream) is the stream on which the arrays are ready; it becomes the handle's
+ * stream.  Validation (finite data, b >= 0) runs on the device. */
+lp_t lp_create_device(int m, int n, const double *dA, const double *db,
+                      const double *dc, void *stream);
+
+/* Build the tableau from (A, b, c) with the slack basis (Section III,
+ * Initialization Step, Table I) and iterate Steps 1-3 (Section III; Section IV
+ * Steps 1-4 on one GPU) until termination.  Blocks until the device is done and
+ * returns the termination status (>= 0) or an error (< 0).  May be called
+ * again: every call starts over from the slack basis.  opt == NULL uses the
+ * defaults. */
+lp_status lp_solve(lp_t h, const lp_options *opt);
+
+/* Read the solution out of the final tableau (Table I layout): x_j is the
+ * right-hand side of the row where x_j is basic, else 0 (n entries); y_i is the
+ * objective-row entry of the slack column of constraint i (m entries, the dual
+ * values); obj is the objective row's right-hand side; basis[i] is the 0-based
+ * variable basic in constraint row i+1 (m entries); iters is the number of
+ * pivots.  Every output is a HOST pointer and may be NULL.  Returns the status
+ * of the last solve, or LP_ERR_STATE before any solve. */
+lp_status lp_get_solution(lp_t h, double *x, double *y, double *obj, int *basis,
+                          long long *iters);
+
+/* Copy the current tableau to HOST memory T ((m + 1) x (n + m + 1) row-major,
+ * float64, without the padding).  Returns LP_ERR_STATE before any solve. */
+lp_status lp_get_tableau(lp_t h, double *T);
+
+/* Copy the recorded (q, p) pairs of the last solve (q = entering column,
+ * p = leaving row in 1..m) to HOST arrays of `cap` entries; *count receives the
+ * number of pivots recorded (min(iters, log_capacity)). */
+lp_status lp_get_pivot_log(lp_t h, int *q, int *p, long long cap, long long *count);
+
+/* Measurements of the last solve. */
+lp_status lp_get_stats(lp_t h, lp_stats *stats);
+
+/* Free the handle and all its device memory.  NULL is ignored. */
+void lp_destroy(lp_t h);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *lp_last_error(void);
+
+/* Install the device allocator used by later lp_create* calls (process-wide).
+ * alloc(bytes, stream, ctx) returns a device pointer or NULL; free(ptr, bytes,
+ * stream, ctx) releases it.  Passing NULL for both restores the default
+ * (cudaMallocAsync / cudaFreeAsync).  Returns 0, or -1 if only one is NULL. */
+typedef void *(*lp_alloc_fn)(size_t bytes, void *stream, void *ctx);
+typedef void (*lp_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
+int lp_set_allocator(lp_alloc_fn alloc_fn, lp_free_fn free_fn, void *ctx);
+
+/* Version string of the library. */
+const char *lp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TABSIMPLEX_H */

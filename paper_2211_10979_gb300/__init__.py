@@ -1,0 +1,146 @@
+"""GB300-native dense full-tableau simplex (arXiv 2211.10979, Section III).
+
+The product path is the CUDA library ``libtabsimplex.so`` (C ABI in
+``include/tabsimplex.h``); this package binds it with ctypes (``abi``) and adds
+a small convenience layer (``solve``, ``Problem``) plus the hook that routes
+the library's device allocations through PyTorch's caching allocator.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import abi
+from .abi import (LP_ERR_CUDA, LP_ERR_INVALID, LP_ERR_NOMEM, LP_ERR_NUMERIC, LP_ERR_STATE,
+                  LP_ERR_TIMEOUT, LP_ITER_LIMIT, LP_OPTIMAL, LP_PATH_AUTO, LP_PATH_MULTILAUNCH,
+                  LP_PATH_PERSISTENT, LP_RULE_BLAND, LP_RULE_DANTZIG, LP_UNBOUNDED, STATUS_NAMES,
+                  lp_create, lp_create_device, lp_destroy, lp_get_pivot_log, lp_get_solution,
+                  lp_get_stats, lp_get_tableau, lp_last_error, lp_options, lp_options_init,
+                  lp_set_allocator, lp_solve, lp_stats, lp_version)
+
+__all__ = [n for n in dir(abi) if n.startswith(("lp_", "LP_"))] + [
+    "STATUS_NAMES", "Solution", "Problem", "solve", "use_torch_allocator", "options"]
+
+_torch_hooks = None
+
+
+def use_torch_allocator() -> None:
+    """Route the library's device allocations through torch's caching allocator."""
+    global _torch_hooks
+    if _torch_hooks is not None:
+        return
+    import torch
+
+    def _alloc(nbytes, stream, ctx):
+        try:
+            dev = torch.cuda.current_device()
+            return torch.cuda.caching_allocator_alloc(int(nbytes), dev, int(stream or 0))
+        except Exception:   # noqa: BLE001 - reported to the library as NULL
+            return None
+
+    def _free(ptr, nbytes, stream, ctx):
+        torch.cuda.caching_allocator_delete(int(ptr))
+
+    hooks = (abi.ALLOC_FN(_alloc), abi.FREE_FN(_free))
+    if abi.lp_set_allocator(hooks[0], hooks[1], None) != 0:
+        raise RuntimeError(abi.lp_last_error())
+    _torch_hooks = hooks
+
+
+def options(**kw) -> lp_options:
+    """lp_options with the library defaults, then the given fields."""
+    o = lp_options_init()
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(f"lp_options has no field {k!r}")
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class Solution:
+    status: int
+    iters: int
+    x: np.ndarray
+    y: np.ndarray
+    obj: float
+    basis: np.ndarray
+    stats: dict
+
+
+class Problem:
+    """Owns one lp_t handle (host or device inputs)."""
+
+    def __init__(self, A, b, c, device: bool = False, stream=None):
+        if device:
+            m, n = A.shape
+            self.m, self.n = int(m), int(n)
+            self._keep = (A, b, c)          # the library references device inputs
+            self.h = lp_create_device(self.m, self.n, A, b, c, stream)
+        else:
+            A = np.ascontiguousarray(A, dtype=np.float64)
+            b = np.ascontiguousarray(b, dtype=np.float64)
+            c = np.ascontiguousarray(c, dtype=np.float64)
+            self.m, self.n = A.shape
+            self.h = lp_create(self.m, self.n, A, b, c)
+
+    def solve(self, opts: lp_options | None = None) -> int:
+        st = lp_solve(self.h, opts)
+        if st < 0 and st != LP_ERR_TIMEOUT:
+            raise RuntimeError(f"lp_solve failed ({STATUS_NAMES.get(st, st)}): {lp_last_error()}")
+        return st
+
+    def solution(self) -> Solution:
+        x = np.empty(self.n, dtype=np.float64)
+        y = np.empty(self.m, dtype=np.float64)
+        obj = np.empty(1, dtype=np.float64)
+        basis = np.empty(self.m, dtype=np.int32)
+        st, it = lp_get_solution(self.h, x, y, obj, basis)
+        return Solution(st, it, x, y, float(obj[0]), basis, lp_get_stats(self.h).as_dict())
+
+    def tableau(self) -> np.ndarray:
+        T = np.empty((self.m + 1, self.n + self.m + 1), dtype=np.float64)
+        st = lp_get_tableau(self.h, T)
+        if st != 0:
+            raise RuntimeError(lp_last_error())
+        return T
+
+    def pivot_log(self, cap: int):
+        q = np.empty(cap, dtype=np.int32)
+        p = np.empty(cap, dtype=np.int32)
+        st, k = lp_get_pivot_log(self.h, q, p, cap)
+        if st != 0:
+            raise RuntimeError(lp_last_error())
+        return q[:k].copy(), p[:k].copy()
+
+    def stats(self) -> dict:
+        return lp_get_stats(self.h).as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:   # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def solve(A, b, c, **opts) -> Solution:
+    """Create, solve and read out one LP from host arrays."""
+    with Problem(A, b, c) as pr:
+        pr.solve(options(**opts))
+        return pr.solution()
+
+
+del ctypes

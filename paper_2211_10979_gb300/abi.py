@@ -1,0 +1,187 @@
+"""ctypes binding of the C ABI in include/tabsimplex.h (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and does no
+arithmetic of the method: the whole solve runs in the library's CUDA kernels.
+Loading fails loudly when the shared library has not been built: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libtabsimplex.so")
+
+LP_OPTIMAL, LP_UNBOUNDED, LP_ITER_LIMIT, LP_ERR_NUMERIC = 0, 1, 2, 3
+LP_ERR_INVALID, LP_ERR_NOMEM, LP_ERR_CUDA, LP_ERR_TIMEOUT, LP_ERR_STATE = -1, -2, -3, -4, -5
+STATUS_NAMES = {0: "OPTIMAL", 1: "UNBOUNDED", 2: "ITER_LIMIT", 3: "NUMERIC", -1: "INVALID",
+                -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE"}
+LP_RULE_DANTZIG, LP_RULE_BLAND = 0, 1
+LP_PATH_AUTO, LP_PATH_PERSISTENT, LP_PATH_MULTILAUNCH = 0, 1, 2
+
+# every symbol include/tabsimplex.h declares
+EXPORTS = ("lp_options_init", "lp_create", "lp_create_device", "lp_solve", "lp_get_solution",
+           "lp_get_tableau", "lp_get_pivot_log", "lp_get_stats", "lp_destroy", "lp_last_error",
+           "lp_set_allocator", "lp_version")
+
+
+class lp_options(ctypes.Structure):
+    _fields_ = [
+        ("rule", ctypes.c_int),
+        ("eps_d", ctypes.c_double),
+        ("eps_p", ctypes.c_double),
+        ("max_iters", ctypes.c_longlong),
+        ("k_cyc", ctypes.c_int),
+        ("barrier_timeout_ns", ctypes.c_longlong),
+        ("path", ctypes.c_int),
+        ("skip_zero_columns", ctypes.c_int),
+        ("threads", ctypes.c_int),
+        ("blocks", ctypes.c_int),
+        ("log_capacity", ctypes.c_longlong),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class lp_stats(ctypes.Structure):
+    _fields_ = [
+        ("iters", ctypes.c_longlong),
+        ("build_ms", ctypes.c_double),
+        ("pivot_ms", ctypes.c_double),
+        ("kernel_launches", ctypes.c_longlong),
+        ("dense_update_bytes", ctypes.c_double),
+        ("update_bytes", ctypes.c_double),
+        ("path", ctypes.c_int),
+        ("grid", ctypes.c_int),
+        ("block", ctypes.c_int),
+        ("ld", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Load the shared library (raises if it is missing: build it first)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise RuntimeError(
+                f"{path} is missing: build it with `python -m paper_2211_10979_gb300.build` "
+                "(the solver has no CPU fallback)")
+        lib = ctypes.CDLL(path)
+        vp, dp, ip = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)
+        llp = ctypes.POINTER(ctypes.c_longlong)
+        sig = {
+            "lp_options_init": (None, [ctypes.POINTER(lp_options)]),
+            "lp_create": (vp, [ctypes.c_int, ctypes.c_int, vp, vp, vp]),
+            "lp_create_device": (vp, [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]),
+            "lp_solve": (ctypes.c_int, [vp, ctypes.POINTER(lp_options)]),
+            "lp_get_solution": (ctypes.c_int, [vp, vp, vp, vp, vp, llp]),
+            "lp_get_tableau": (ctypes.c_int, [vp, vp]),
+            "lp_get_pivot_log": (ctypes.c_int, [vp, vp, vp, ctypes.c_longlong, llp]),
+            "lp_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(lp_stats)]),
+            "lp_destroy": (None, [vp]),
+            "lp_last_error": (ctypes.c_char_p, []),
+            "lp_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, vp]),
+            "lp_version": (ctypes.c_char_p, []),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        del dp, ip
+        _lib = lib
+        return lib
+
+
+def _ptr(a):
+    """Address of a numpy array, a torch tensor, an int address, or None."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    if hasattr(a, "ctypes"):
+        return a.ctypes.data
+    raise TypeError(f"cannot take the address of {type(a)}")
+
+
+# ------------------------------------------------------------- entry points
+def lp_options_init() -> lp_options:
+    o = lp_options()
+    load().lp_options_init(ctypes.byref(o))
+    return o
+
+
+def lp_last_error() -> str:
+    return (load().lp_last_error() or b"").decode()
+
+
+def lp_version() -> str:
+    return load().lp_version().decode()
+
+
+def lp_create(m: int, n: int, A, b, c) -> int:
+    """A, b, c: C-contiguous float64 host arrays. Returns the handle (int)."""
+    h = load().lp_create(int(m), int(n), _ptr(A), _ptr(b), _ptr(c))
+    if not h:
+        raise ValueError(lp_last_error())
+    return h
+
+
+def lp_create_device(m: int, n: int, dA, db, dc, stream=None) -> int:
+    """dA, db, dc: device float64 buffers (torch tensors or addresses)."""
+    h = load().lp_create_device(int(m), int(n), _ptr(dA), _ptr(db), _ptr(dc), stream)
+    if not h:
+        raise ValueError(lp_last_error())
+    return h
+
+
+def lp_solve(h: int, opts: lp_options | None = None) -> int:
+    return int(load().lp_solve(h, ctypes.byref(opts) if opts is not None else None))
+
+
+def lp_get_solution(h: int, x=None, y=None, obj=None, basis=None):
+    """Fills the given host arrays (numpy); returns (status, iters)."""
+    it = ctypes.c_longlong(0)
+    st = load().lp_get_solution(h, _ptr(x), _ptr(y), _ptr(obj), _ptr(basis), ctypes.byref(it))
+    return int(st), int(it.value)
+
+
+def lp_get_tableau(h: int, T) -> int:
+    return int(load().lp_get_tableau(h, _ptr(T)))
+
+
+def lp_get_pivot_log(h: int, q, p, cap: int):
+    cnt = ctypes.c_longlong(0)
+    st = load().lp_get_pivot_log(h, _ptr(q), _ptr(p), int(cap), ctypes.byref(cnt))
+    return int(st), int(cnt.value)
+
+
+def lp_get_stats(h: int) -> lp_stats:
+    s = lp_stats()
+    st = load().lp_get_stats(h, ctypes.byref(s))
+    if st != 0:
+        raise RuntimeError(lp_last_error())
+    return s
+
+
+def lp_destroy(h: int) -> None:
+    if h:
+        load().lp_destroy(h)
+
+
+def lp_set_allocator(alloc_fn, free_fn, ctx=None) -> int:
+    return int(load().lp_set_allocator(alloc_fn, free_fn, ctx))

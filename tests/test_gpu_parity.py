@@ -1,0 +1,197 @@
+"""CUDA path vs the CPU oracle, through the C ABI (needs a GPU).
+
+FP64 parity bar (from the arithmetic both sides share: IEEE division for the
+pivot row and ratios, one fused multiply-add per updated entry, comparisons
+only in the reductions): the pivot sequence, the final basis and every entry
+of the tableau are EQUAL to the oracle's (tolerance 0); x, y and the objective
+are copies of tableau entries and are equal too.
+"""
+import numpy as np
+import pytest
+
+import lpgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tsx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_10979_gb300 import build
+    build.build()
+    import paper_2211_10979_gb300 as mod
+    mod.use_torch_allocator()
+    return mod
+
+
+def _gpu_run(tsx, A, b, c, **kw):
+    kw.setdefault("log_capacity", 100000)
+    with tsx.Problem(A, b, c) as pr:
+        st = pr.solve(tsx.options(**kw))
+        sol = pr.solution()
+        T = pr.tableau()
+        q, p = pr.pivot_log(kw["log_capacity"])
+        return st, sol, T, q, p, pr.stats()
+
+
+def _oracle_run(A, b, c, **kw):
+    return oracle.solve(A, b, c, oracle.Options(**kw))
+
+
+def _assert_same(gpu, ref):
+    st, sol, T, q, p, _ = gpu
+    assert st == ref.status, (st, ref.status)
+    assert sol.iters == ref.iters
+    np.testing.assert_array_equal(q, ref.qlog[:len(q)])
+    np.testing.assert_array_equal(p, ref.plog[:len(p)])
+    np.testing.assert_array_equal(sol.basis, ref.basis)
+    np.testing.assert_array_equal(T, ref.T)
+    np.testing.assert_array_equal(sol.x, ref.x)
+    np.testing.assert_array_equal(sol.y, ref.y)
+    assert sol.obj == ref.obj
+
+
+SHAPES = [(1, 1), (1, 7), (7, 1), (3, 4), (16, 16), (37, 53), (64, 64), (100, 300),
+          (300, 100), (129, 257), (256, 256)]
+
+
+@pytest.mark.parametrize("m,n", SHAPES)
+@pytest.mark.parametrize("path", [1, 2])
+def test_full_solve_bit_exact(tsx, m, n, path):
+    A, b, c = lpgen.dense_lp(m, n, 1 + m + n)
+    ref = _oracle_run(A, b, c)
+    _assert_same(_gpu_run(tsx, A, b, c, path=path), ref)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3, 4, 5, 6, 7, 8])
+def test_config_256_seeds(tsx, seed):
+    A, b, c = lpgen.dense_lp(256, 256, seed)
+    ref = _oracle_run(A, b, c)
+    assert ref.status == oracle.OPTIMAL
+    _assert_same(_gpu_run(tsx, A, b, c), ref)
+
+
+@pytest.mark.parametrize("skip", [0, 1])
+@pytest.mark.parametrize("threads,blocks", [(128, 1), (256, 2), (512, 3), (256, 7), (256, 0)])
+def test_launch_shapes_agree(tsx, skip, threads, blocks):
+    A, b, c = lpgen.dense_lp(300, 200, 11)
+    ref = _oracle_run(A, b, c)
+    _assert_same(_gpu_run(tsx, A, b, c, skip_zero_columns=skip, threads=threads, blocks=blocks), ref)
+
+
+@pytest.mark.parametrize("k", [0, 1, 2, 5, 17])
+def test_tableau_after_k_pivots(tsx, k):
+    A, b, c = lpgen.dense_lp(200, 150, 21)
+    ref = _oracle_run(A, b, c, max_iters=k)
+    st, sol, T, q, p, _ = _gpu_run(tsx, A, b, c, max_iters=k)
+    assert st == ref.status == oracle.ITER_LIMIT
+    assert sol.iters == k
+    np.testing.assert_array_equal(T, ref.T)
+
+
+def test_golden_hand_traces(tsx, golden_dir):
+    import json
+    import os
+    for name in ("two_pivots_dyadic.json", "one_pivot.json", "unbounded_after_one.json"):
+        g = json.load(open(os.path.join(golden_dir, name)))
+        A = np.array(g["A"], dtype=np.float64)
+        b = np.array(g["b"], dtype=np.float64)
+        c = np.array(g["c"], dtype=np.float64)
+        for path in (1, 2):
+            st, sol, T, q, p, _ = _gpu_run(tsx, A, b, c, path=path)
+            assert tsx.STATUS_NAMES[st] == g["status"]
+            assert q.tolist() == [s["q"] for s in g["steps"]]
+            assert p.tolist() == [s["p"] for s in g["steps"]]
+            np.testing.assert_array_equal(T, np.array(g["steps"][-1]["T"], dtype=np.float64))
+            assert sol.obj == g["obj"]
+
+
+def test_cycling_lp_bland_fallback(tsx):
+    A = np.array([[0.5, -5.5, -2.5, 9.0], [0.5, -1.5, -0.5, 1.0], [1.0, 0.0, 0.0, 0.0]])
+    b = np.array([0.0, 0.0, 1.0])
+    c = np.array([10.0, -57.0, -9.0, -24.0])
+    for kw in ({"k_cyc": 3}, {"k_cyc": 50}, {"rule": 1}, {"k_cyc": 0, "max_iters": 200}):
+        ref = _oracle_run(A, b, c, **kw)
+        for path in (1, 2):
+            _assert_same(_gpu_run(tsx, A, b, c, path=path, **kw), ref)
+
+
+def test_unbounded_and_zero_objective(tsx):
+    A = np.array([[1.0, -2.0], [1.0, 0.0]])
+    b = np.array([4.0, 3.0])
+    c = np.array([0.0, 1.0])
+    _assert_same(_gpu_run(tsx, A, b, c), _oracle_run(A, b, c))
+    A, b, _ = lpgen.dense_lp(5, 4, 3)
+    c = -np.ones(4)
+    _assert_same(_gpu_run(tsx, A, b, c), _oracle_run(A, b, c))
+
+
+def test_degenerate_duplicate_rows(tsx):
+    A0, b0, c = lpgen.dense_lp(40, 30, 11)
+    A = np.vstack([A0, A0[:10], np.ones((3, 30))])
+    b = np.concatenate([b0, b0[:10], np.full(3, 50.0)])
+    _assert_same(_gpu_run(tsx, A, b, c), _oracle_run(A, b, c))
+
+
+def test_device_inputs_match_host_inputs(tsx):
+    import torch
+    A, b, c = lpgen.dense_lp(120, 90, 5)
+    ref = _oracle_run(A, b, c)
+    dA, db, dc = (torch.from_numpy(v).cuda() for v in (A, b, c))
+    s = torch.cuda.current_stream().cuda_stream
+    with tsx.Problem(dA, db, dc, device=True, stream=s) as pr:
+        assert pr.solve(tsx.options(stream=s)) == tsx.LP_OPTIMAL
+        sol = pr.solution()
+        np.testing.assert_array_equal(pr.tableau(), ref.T)
+        np.testing.assert_array_equal(sol.x, ref.x)
+        # a second solve on the same handle starts over and repeats the result
+        assert pr.solve() == tsx.LP_OPTIMAL
+        np.testing.assert_array_equal(pr.tableau(), ref.T)
+
+
+def test_invalid_inputs_rejected_on_device(tsx):
+    A, b, c = lpgen.dense_lp(4, 3, 1)
+    bad_b = b.copy()
+    bad_b[2] = -1.0
+    with pytest.raises(ValueError, match="b >= 0"):
+        tsx.Problem(A, bad_b, c)
+    bad_A = A.copy()
+    bad_A[1, 1] = np.nan
+    with pytest.raises(ValueError, match="finite"):
+        tsx.Problem(bad_A, b, c)
+    with pytest.raises(ValueError, match="finite"):
+        tsx.Problem(A, b, np.array([1.0, np.inf, 2.0]))
+
+
+def test_state_errors(tsx):
+    A, b, c = lpgen.dense_lp(4, 3, 1)
+    with tsx.Problem(A, b, c) as pr:
+        assert tsx.lp_get_solution(pr.h)[0] == tsx.LP_ERR_STATE
+        assert tsx.lp_solve(pr.h, tsx.options(threads=96)) == tsx.LP_ERR_INVALID
+        assert tsx.lp_solve(pr.h, tsx.options(eps_d=-1.0)) == tsx.LP_ERR_INVALID
+
+
+def test_barrier_timeout_reports_and_context_survives(tsx):
+    # a zero wait budget makes every barrier wait expire at once: the kernel
+    # must report LP_ERR_TIMEOUT (no trap, no hang) and later solves still work
+    A, b, c = lpgen.dense_lp(256, 256, 1)
+    with tsx.Problem(A, b, c) as pr:
+        st = tsx.lp_solve(pr.h, tsx.options(path=1, blocks=8, barrier_timeout_ns=0))
+        assert st == tsx.LP_ERR_TIMEOUT
+        assert "barrier" in tsx.lp_last_error()
+        assert pr.solve() == tsx.LP_OPTIMAL
+        np.testing.assert_array_equal(pr.tableau(), _oracle_run(A, b, c).T)
+
+
+def test_stats_account_for_the_update(tsx):
+    A, b, c = lpgen.dense_lp(256, 256, 2)
+    st, sol, T, q, p, stats = _gpu_run(tsx, A, b, c)
+    m, n = 256, 256
+    W = n + m + 1
+    assert stats["iters"] == sol.iters > 0
+    assert stats["dense_update_bytes"] == 2.0 * (m + 1) * W * 8 * sol.iters
+    assert 0 < stats["update_bytes"] <= 2.0 * (m + 1) * stats["ld"] * 8 * sol.iters
+    assert stats["pivot_ms"] > 0 and stats["kernel_launches"] >= 3
