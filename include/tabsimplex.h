@@ -167,6 +167,45 @@ int lp_set_allocator(lp_alloc_fn alloc_fn, lp_free_fn free_fn, void *ctx);
 /* Version string of the library. */
 const char *lp_version(void);
 
+/* Solve without allocating any device memory.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * themselves or let the library do it -- for example a plugin running inside
+ * a host application whose own memory pool has reserved the GPU's memory, or a
+ * latency-sensitive loop that must not call cudaMalloc/cudaFree, which can
+ * block on or synchronise with other work on the device.
+ *
+ * Same computation as lp_create_device + lp_solve (tableau build from the
+ * slack basis, then Steps 1-3 until termination), with every buffer supplied by
+ * the caller and the work buffers (pivot column, scaled pivot row, reduction
+ * partials, status and barrier words) taken from one fixed array that the
+ * library holds in device global memory: LP_NOALLOC_SCRATCH_BYTES (2 MiB) on
+ * every GPU that loads the library, kept until the process exits.
+ *   dA, db, dc  device inputs (m x n row-major, m, n float64), read only;
+ *               every entry finite and b >= 0, else LP_ERR_INVALID
+ *   dT          device output, (m + 1) x ld float64, 32-byte aligned; receives
+ *               the final tableau (rows: objective, constraints 1..m; columns:
+ *               x_1..x_n, slacks, right-hand side at n + m, zeros after)
+ *   ld          leading dimension of dT in elements: >= n + m + 1, multiple of 4
+ *   dbasis      device output, m ints: variable basic in constraint row i + 1
+ *   opt         options as for lp_solve (NULL = defaults); opt->stream is the
+ *               stream used; log_capacity must be 0 and blocks <= 1024
+ *   iters       host output (may be NULL): pivots performed
+ * The work buffers need 8 (m + 1) + 8 ld + 16 ceil(ld / 128) + 16 * 1024 bytes
+ * plus 1 KiB of alignment and state, at most LP_NOALLOC_SCRATCH_BYTES (about
+ * m + ld <= 2.4e5, e.g. m = n = 80000); larger sizes return LP_ERR_INVALID
+ * before any device work, with the sizes in lp_last_error().
+ * The first call on a device looks up the array's device address on that
+ * device (the current one); make that first call before any stream capture.
+ * Every call on a device uses the same array and leaves its contents behind
+ * (each call resets what must start from zero), so calls whose GPU work
+ * overlaps -- concurrent streams or host threads -- race: serialise them.
+ * Blocks until the device is done; returns the termination status (>= 0) or
+ * an error (< 0). */
+#define LP_NOALLOC_SCRATCH_BYTES (2u * 1024u * 1024u)
+lp_status lp_solve_noalloc(int m, int n, const double *dA, const double *db,
+                           const double *dc, double *dT, long long ld,
+                           int *dbasis, const lp_options *opt, long long *iters);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,7 +18,7 @@ from .abi import (LP_ERR_CUDA, LP_ERR_INVALID, LP_ERR_NOMEM, LP_ERR_NUMERIC, LP_
                   LP_PATH_PERSISTENT, LP_RULE_BLAND, LP_RULE_DANTZIG, LP_UNBOUNDED, STATUS_NAMES,
                   lp_create, lp_create_device, lp_destroy, lp_get_pivot_log, lp_get_solution,
                   lp_get_stats, lp_get_tableau, lp_last_error, lp_options, lp_options_init,
-                  lp_set_allocator, lp_solve, lp_stats, lp_version)
+                  lp_set_allocator, lp_solve, lp_solve_noalloc, lp_stats, lp_version)
 
 __all__ = [n for n in dir(abi) if n.startswith(("lp_", "LP_"))] + [
     "STATUS_NAMES", "Solution", "Problem", "solve", "use_torch_allocator", "options"]

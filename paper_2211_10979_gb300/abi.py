@@ -24,7 +24,10 @@ LP_PATH_AUTO, LP_PATH_PERSISTENT, LP_PATH_MULTILAUNCH = 0, 1, 2
 # every symbol include/tabsimplex.h declares
 EXPORTS = ("lp_options_init", "lp_create", "lp_create_device", "lp_solve", "lp_get_solution",
            "lp_get_tableau", "lp_get_pivot_log", "lp_get_stats", "lp_destroy", "lp_last_error",
-           "lp_set_allocator", "lp_version")
+           "lp_set_allocator", "lp_version", "lp_solve_noalloc")
+
+# capacity of the library's fixed work-buffer array used by lp_solve_noalloc
+LP_NOALLOC_SCRATCH_BYTES = 2 * 1024 * 1024
 
 
 class lp_options(ctypes.Structure):
@@ -95,6 +98,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "lp_last_error": (ctypes.c_char_p, []),
             "lp_set_allocator": (ctypes.c_int, [ALLOC_FN, FREE_FN, vp]),
             "lp_version": (ctypes.c_char_p, []),
+            "lp_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp,
+                                                ctypes.c_longlong, vp, ctypes.POINTER(lp_options),
+                                                llp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -181,6 +187,19 @@ def lp_get_stats(h: int) -> lp_stats:
 def lp_destroy(h: int) -> None:
     if h:
         load().lp_destroy(h)
+
+
+def lp_solve_noalloc(m: int, n: int, dA, db, dc, dT, ld: int, dbasis,
+                     opts: lp_options | None = None):
+    """Solve into caller-owned device buffers without any device allocation.
+
+    dA, db, dc: device inputs; dT: device (m+1) x ld float64 output; dbasis:
+    device int32 output (m).  Returns (status, iters)."""
+    it = ctypes.c_longlong(0)
+    st = load().lp_solve_noalloc(int(m), int(n), _ptr(dA), _ptr(db), _ptr(dc), _ptr(dT), int(ld),
+                                 _ptr(dbasis), ctypes.byref(opts) if opts is not None else None,
+                                 ctypes.byref(it))
+    return int(st), int(it.value)
 
 
 def lp_set_allocator(alloc_fn, free_fn, ctx=None) -> int:

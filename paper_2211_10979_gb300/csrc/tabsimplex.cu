@@ -797,3 +797,202 @@ lp_status lp_get_stats(lp_t h, lp_stats* stats) {
     *stats = h->stats;
     return LP_OPTIMAL;
 }
+
+// ------------------------------------------------------- no-allocation solve
+// lp_solve_noalloc: the pivot kernels run on work buffers carved out of one
+// file-scope device array instead of allocated memory, for callers that cannot
+// allocate device memory (see tabsimplex.h).  The array is a host-side stand-in
+// in host code; its device address on each device is looked up once with
+// cudaGetSymbolAddress and passed to the kernels.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[LP_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kNoAllocMaxGrid = 1024;   // ratio-partial slots in the array
+constexpr int kNoAllocMaxDevices = 64;
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Device address of the array on the current device (set up on first use).
+static void* noalloc_scratch(int device) {
+    if (device < 0 || device >= kNoAllocMaxDevices) {
+        set_error("lp_solve_noalloc: device ordinal %d out of range", device);
+        return nullptr;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess || !ptr) {
+            set_error("lp_solve_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+            return nullptr;
+        }
+        g_noalloc_ptr[device] = ptr;
+    }
+    return g_noalloc_ptr[device];
+}
+
+template <int NT>
+static lp_status noalloc_nt(int m, int n, const double* dA, const double* db, const double* dc, double* dT,
+                            int ld, int* dbasis, const lp_options& o, long long* iters_out, char* base,
+                            size_t off_R, size_t off_cp, size_t off_rp, size_t off_st) {
+    cudaStream_t s = (cudaStream_t)o.stream;
+    int device = 0;
+    CUDA_TRY(cudaGetDevice(&device), LP_ERR_CUDA);
+    Params P{};
+    P.T = dT;
+    P.ld = ld;
+    P.m = m;
+    P.n = n;
+    P.W = n + m + 1;
+    P.basis = dbasis;
+    P.F = (double*)base;
+    P.R = (double*)(base + off_R);
+    P.cpart = (ArgPart*)(base + off_cp);
+    P.rpart = (RatPart*)(base + off_rp);
+    P.st = (DevState*)(base + off_st);
+    P.qlog = nullptr;
+    P.plog = nullptr;
+    P.log_cap = 0;
+    P.eps_d = o.eps_d;
+    P.eps_p = o.eps_p;
+    P.max_iters = o.max_iters < 0 ? 50LL * ((long long)m + n) : o.max_iters;
+    P.k_cyc = o.k_cyc;
+    P.rule = o.rule;
+    P.timeout_ns = std::max(0LL, o.barrier_timeout_ns);
+    P.nstrips = (ld + kStripCols - 1) / kStripCols;
+    P.nrc = (m + 1 + kUnitRows - 1) / kUnitRows;
+    P.nunits = (long long)P.nstrips * P.nrc;
+    P.skip_zero = o.skip_zero_columns ? 1 : 0;
+
+    // validate the inputs: the state word starts from zero on every call
+    k_reset_state<<<1, 32, 0, s>>>(P.st);
+    {
+        const size_t total = (size_t)m * n + m + n;
+        int g = (int)std::min<size_t>((total + 255) / 256, 4096);
+        k_validate<<<g, 256, 0, s>>>(m, n, dA, db, dc, P.st);
+    }
+    int bad = 0;
+    CUDA_TRY(cudaMemcpyAsync(&bad, &P.st->bad, sizeof(int), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+    CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
+    if (bad) {
+        set_error("lp_solve_noalloc: inputs must be finite with b >= 0");
+        return LP_ERR_INVALID;
+    }
+
+    const long long want = (P.nunits + NT / 32 - 1) / (NT / 32);
+    int coresident = max_coresident<NT>(device);
+    int grid = (int)std::min<long long>(std::max<long long>(1, want), std::max(1, coresident));
+    grid = std::min(grid, kNoAllocMaxGrid);
+    if (o.blocks > 0) grid = std::min(grid, o.blocks);
+    int coop = 0;
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
+    int path = o.path;
+    if (path == LP_PATH_AUTO) path = (coop && coresident > 0) ? LP_PATH_PERSISTENT : LP_PATH_MULTILAUNCH;
+    if (path == LP_PATH_PERSISTENT && (!coop || coresident <= 0)) {
+        set_error("lp_solve_noalloc: persistent path requested but cooperative launch is unavailable");
+        return LP_ERR_CUDA;
+    }
+
+    k_reset_state<<<1, 32, 0, s>>>(P.st);
+    {
+        const size_t groups = (size_t)(m + 1) * (size_t)(ld / 4);
+        int g = (int)std::min<size_t>((groups + 255) / 256, 152 * 16);
+        k_build<<<g, 256, 0, s>>>(m, n, n + m + 1, ld, dA, db, dc, dT, dbasis);
+    }
+    CUDA_TRY(cudaGetLastError(), LP_ERR_CUDA);
+    if (path == LP_PATH_PERSISTENT) {
+        cudaError_t e = launch_persistent<NT>(P, grid, s);
+        if (e != cudaSuccess) {
+            if (o.path != LP_PATH_AUTO) {
+                set_error("lp_solve_noalloc: cooperative launch failed: %s", cudaGetErrorString(e));
+                return LP_ERR_CUDA;
+            }
+            cudaGetLastError();
+            path = LP_PATH_MULTILAUNCH;
+        }
+    }
+    if (path == LP_PATH_MULTILAUNCH) {
+        k_ml_init<<<grid, NT, 0, s>>>(P);
+        int status = kRunning;
+        int batch = 4;
+        for (;;) {
+            for (int k = 0; k < batch; ++k) {
+                k_ml_select<NT><<<grid, NT, 0, s>>>(P);
+                k_ml_stage<NT><<<grid, NT, 0, s>>>(P);
+                k_ml_update<NT><<<grid, NT, 0, s>>>(P);
+            }
+            CUDA_TRY(cudaGetLastError(), LP_ERR_CUDA);
+            CUDA_TRY(cudaMemcpyAsync(&status, &P.st->status, sizeof(int), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+            CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
+            if (status != kRunning) break;
+            batch = std::min(batch * 2, 64);
+        }
+    }
+    DevState hs{};
+    CUDA_TRY(cudaMemcpyAsync(&hs, P.st, sizeof(DevState), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+    CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
+    if (iters_out) *iters_out = hs.iters;
+    if (hs.status == kRunning) {
+        set_error("lp_solve_noalloc: kernel ended without a status");
+        return LP_ERR_CUDA;
+    }
+    if (hs.status == kTimeout) set_error("lp_solve_noalloc: a grid barrier wait exceeded %lld ns", (long long)P.timeout_ns);
+    return (lp_status)hs.status;
+}
+
+lp_status lp_solve_noalloc(int m, int n, const double* dA, const double* db, const double* dc, double* dT,
+                           long long ld, int* dbasis, const lp_options* opt, long long* iters) {
+    if (iters) *iters = 0;
+    if (!dA || !db || !dc || !dT || !dbasis) {
+        set_error("lp_solve_noalloc: NULL pointer argument");
+        return LP_ERR_INVALID;
+    }
+    if (m <= 0 || n <= 0 || (long long)n + m + 1 > (long long)INT_MAX - 256) {
+        set_error("lp_solve_noalloc: need m > 0, n > 0 (got m=%d, n=%d)", m, n);
+        return LP_ERR_INVALID;
+    }
+    if (ld < (long long)n + m + 1 || ld % 4 != 0 || ld > (long long)INT_MAX - 256) {
+        set_error("lp_solve_noalloc: ld must be >= n + m + 1 = %lld and a multiple of 4 (got %lld)",
+                  (long long)n + m + 1, ld);
+        return LP_ERR_INVALID;
+    }
+    if (((uintptr_t)dT & 31u) != 0) {
+        set_error("lp_solve_noalloc: dT must be 32-byte aligned");
+        return LP_ERR_INVALID;
+    }
+    lp_options o;
+    if (opt)
+        o = *opt;
+    else
+        lp_options_init(&o);
+    if (!(o.eps_d >= 0.0) || !(o.eps_p >= 0.0) || o.rule < 0 || o.rule > 1 || o.path < 0 || o.path > 2 ||
+        o.log_capacity != 0 || o.blocks < 0 || o.blocks > kNoAllocMaxGrid) {
+        set_error("lp_solve_noalloc: invalid options (log_capacity must be 0, blocks <= %d)", kNoAllocMaxGrid);
+        return LP_ERR_INVALID;
+    }
+    // layout of the array: F | R | cpart | rpart | state
+    const size_t nstrips = ((size_t)ld + kStripCols - 1) / kStripCols;
+    const size_t off_R = align_up((size_t)(m + 1) * sizeof(double), 256);
+    const size_t off_cp = align_up(off_R + (size_t)ld * sizeof(double), 256);
+    const size_t off_rp = align_up(off_cp + nstrips * sizeof(ArgPart), 256);
+    const size_t off_st = align_up(off_rp + (size_t)kNoAllocMaxGrid * sizeof(RatPart), 256);
+    const size_t need = align_up(off_st + sizeof(DevState), 256);
+    if (need > (size_t)LP_NOALLOC_SCRATCH_BYTES) {
+        set_error("lp_solve_noalloc: m=%d, ld=%lld need %zu bytes of work buffers, more than the %u-byte "
+                  "fixed array; use lp_create/lp_solve for this size",
+                  m, ld, need, (unsigned)LP_NOALLOC_SCRATCH_BYTES);
+        return LP_ERR_INVALID;
+    }
+    int device = 0;
+    CUDA_TRY(cudaGetDevice(&device), LP_ERR_CUDA);
+    char* base = (char*)noalloc_scratch(device);
+    if (!base) return LP_ERR_CUDA;
+    const int nt = o.threads ? o.threads : 256;
+    switch (nt) {
+        case 128: return noalloc_nt<128>(m, n, dA, db, dc, dT, (int)ld, dbasis, o, iters, base, off_R, off_cp, off_rp, off_st);
+        case 256: return noalloc_nt<256>(m, n, dA, db, dc, dT, (int)ld, dbasis, o, iters, base, off_R, off_cp, off_rp, off_st);
+        case 512: return noalloc_nt<512>(m, n, dA, db, dc, dT, (int)ld, dbasis, o, iters, base, off_R, off_cp, off_rp, off_st);
+        default:
+            set_error("lp_solve_noalloc: threads must be 0, 128, 256 or 512 (got %d)", nt);
+            return LP_ERR_INVALID;
+    }
+}
