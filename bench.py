@@ -304,13 +304,15 @@ def run_gpu(args, rank, world, local):
         finally:
             tsx.lp_destroy(h)
 
-    e2e_step(seeds[0])
-    if dist:
-        dist.barrier()
-    t0 = time.perf_counter()
-    e2e_piv = sum(e2e_step(seeds[k % len(seeds)]) for k in range(args.e2e_steps))
-    torch.cuda.synchronize(dev)
-    e2e_secs = time.perf_counter() - t0
+    e2e_piv, e2e_secs = 0, 0.0
+    if args.e2e_steps > 0:
+        e2e_step(seeds[0])
+        if dist:
+            dist.barrier()
+        t0 = time.perf_counter()
+        e2e_piv = sum(e2e_step(seeds[k % len(seeds)]) for k in range(args.e2e_steps))
+        torch.cuda.synchronize(dev)
+        e2e_secs = time.perf_counter() - t0
 
     per_rank = [(pivots, secs, e2e_piv, e2e_secs)]
     if dist:
@@ -319,7 +321,7 @@ def run_gpu(args, rank, world, local):
         dist.all_gather(allt, t)
         per_rank = [tuple(v.tolist()) for v in allt]
     value, tmax = combine_ranks([(p, s) for p, s, _, _ in per_rank])
-    e2e_value, _ = combine_ranks([(p, s) for _, _, p, s in per_rank])
+    e2e_value = combine_ranks([(p, s) for _, _, p, s in per_rank])[0] if args.e2e_steps > 0 else None
 
     if rank == 0:
         peak, peak_src = measured_peaks()
@@ -356,6 +358,10 @@ def run_gpu(args, rank, world, local):
                 "kernel": "k_pivot_persistent",
                 "bytes_per_launch": upd_bytes, "kernel_ms_per_launch": kernel_ms,
                 "dense_equivalent_gbs": dense_bytes / (kernel_ms / 1000.0) / 1e9,
+                "phase_us_per_pivot": dict(zip(
+                    ["ratio", "stage", "update", "wait_ratio", "wait_stage", "wait_update"],
+                    [round(1000.0 * sum(st["phase_ms"][k] for st in stats) / max(1, pivots), 3)
+                     for k in range(6)])),
             },
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * (m * n + m + n),

@@ -99,6 +99,10 @@ typedef struct {
     int grid;                     /* blocks of the pivot kernels                */
     int block;                    /* threads per block                          */
     int ld;                       /* leading dimension of the tableau (elems)   */
+    double phase_ms[6];           /* persistent path, as seen by block 0: work
+                                     time of {ratio test (Steps 1-2), pivot-row
+                                     staging, rank-1 update (Step 3)}, then the
+                                     barrier wait after each of them            */
 } lp_stats;
 
 /* Fill *opt with the defaults listed above.  NULL is ignored. */
@@ -190,9 +194,9 @@ const char *lp_version(void);
  *   opt         options as for lp_solve (NULL = defaults); opt->stream is the
  *               stream used; log_capacity must be 0 and blocks <= 1024
  *   iters       host output (may be NULL): pivots performed
- * The work buffers need 8 (m + 1) + 8 ld + 16 ceil(ld / 128) + 16 * 1024 bytes
- * plus 1 KiB of alignment and state, at most LP_NOALLOC_SCRATCH_BYTES (about
- * m + ld <= 2.4e5, e.g. m = n = 80000); larger sizes return LP_ERR_INVALID
+ * The work buffers need 8 (m + 1) + 9 ld + 16 ceil(ld / 128) + 16 * 1024 bytes
+ * plus about 1.5 KiB of alignment and state, at most LP_NOALLOC_SCRATCH_BYTES
+ * (about m + ld <= 2.2e5, e.g. m = n = 70000); larger sizes return LP_ERR_INVALID
  * before any device work, with the sizes in lp_last_error().
  * The first call on a device looks up the array's device address on that
  * device (the current one); make that first call before any stream capture.

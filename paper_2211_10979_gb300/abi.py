@@ -59,10 +59,13 @@ class lp_stats(ctypes.Structure):
         ("grid", ctypes.c_int),
         ("block", ctypes.c_int),
         ("ld", ctypes.c_int),
+        ("phase_ms", ctypes.c_double * 6),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["phase_ms"] = list(self.phase_ms)
+        return d
 
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)

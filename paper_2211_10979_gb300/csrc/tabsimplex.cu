@@ -72,6 +72,7 @@ struct lp_handle {
     double* T = nullptr;
     double* F = nullptr;
     double* R = nullptr;
+    int* act = nullptr;
     ArgPart* cpart = nullptr;
     RatPart* rpart = nullptr;
     DevState* st = nullptr;
@@ -120,9 +121,12 @@ __global__ void k_reset_state(DevState* st) {
         st->bad = 0;
         st->iters = 0;
         st->active_sectors = 0;
+        st->nact = 0;
+        st->next_slot = 0;
         st->theta = 0.0;
         st->bar_count = 0;
         st->bar_gen = 0;
+        for (int k = 0; k < 6; ++k) st->phase_ns[k] = 0;
     }
 }
 
@@ -207,44 +211,72 @@ __device__ __forceinline__ void degeneracy_step(const Params& P, double theta, i
     }
 }
 
-__device__ __forceinline__ void finish(const Params& P, int status, long long it, int bland, int degen) {
+__device__ __forceinline__ void finish(const Params& P, int status, long long it, int bland, int degen,
+                                       const long long* ph) {
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         atomicCAS(&P.st->status, kRunning, status);
         P.st->iters = it;
         P.st->bland = bland;
         P.st->degen_run = degen;
+        for (int k = 0; k < 6; ++k) P.st->phase_ns[k] = ph[k];
     }
 }
+
+// Phase timer of block 0, thread 0 (other threads keep it at zero).
+struct PhaseClock {
+    long long acc[6] = {0, 0, 0, 0, 0, 0};
+    long long t = 0;
+    bool on = false;
+    __device__ void start() {
+        on = blockIdx.x == 0 && threadIdx.x == 0;
+        if (on) t = global_ns();
+    }
+    __device__ void lap(int k) {   // closes interval k, opens the next one
+        if (on) {
+            const long long now = global_ns();
+            acc[k] += now - t;
+            t = now;
+        }
+    }
+};
 
 // Steps 1-3 iterated inside one cooperative launch; three grid barriers per
 // pivot (after P2, after P3, after P4).  Every block takes the same decisions
 // from the same reduced values, so all leave the loop together.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_pivot_persistent(Params P) {
+__global__ void __launch_bounds__(NT, 512 / NT) k_pivot_persistent(Params P) {
     __shared__ BlockScratch s;
+    PhaseClock clk;
     phase_init_argmin(P);
     if (!grid_barrier(P.st, P.timeout_ns, s)) return;
     long long it = 0;
     int bland = P.rule == 1 ? 1 : 0;
     int degen = 0;
+    clk.start();
     for (;;) {
         const ArgPart e = phase_entering(P, s);           // Step 1
         const int q = bland ? e.jfirst : e.j;
-        if (q == INT_MAX) { finish(P, kOptimal, it, bland, degen); return; }
-        if (it >= P.max_iters) { finish(P, kIterLimit, it, bland, degen); return; }
+        if (q == INT_MAX) { finish(P, kOptimal, it, bland, degen, clk.acc); return; }
+        if (it >= P.max_iters) { finish(P, kIterLimit, it, bland, degen, clk.acc); return; }
         phase_ratio(P, q, bland, s);                      // Step 2 (block partials)
+        clk.lap(0);
         if (!grid_barrier(P.st, P.timeout_ns, s)) return;
+        clk.lap(3);
         const RatPart l = phase_leaving(P, s);            // Step 2 (global)
-        if (l.i == INT_MAX) { finish(P, kUnbounded, it, bland, degen); return; }
+        if (l.i == INT_MAX) { finish(P, kUnbounded, it, bland, degen, clk.acc); return; }
         const double piv = __ldcg(P.F + l.i);
-        if (!isfinite(piv) || !isfinite(l.r)) { finish(P, kNumeric, it, bland, degen); return; }
+        if (!isfinite(piv) || !isfinite(l.r)) { finish(P, kNumeric, it, bland, degen, clk.acc); return; }
         phase_stage_row(P, l.i, piv, s);                  // Step 3 (pivot row)
         if (blockIdx.x == 0 && threadIdx.x == 0) record_pivot(P, it, q, l.i);
+        clk.lap(1);
         if (!grid_barrier(P.st, P.timeout_ns, s)) return;
+        clk.lap(4);
         phase_update(P, l.i);                             // Step 3 (rank-1 update)
         ++it;
         degeneracy_step(P, l.r, bland, degen);
+        clk.lap(2);
         if (!grid_barrier(P.st, P.timeout_ns, s)) return;
+        clk.lap(5);
     }
 }
 
@@ -294,7 +326,7 @@ __global__ void __launch_bounds__(NT) k_ml_stage(Params P) {
 }
 
 template <int NT>
-__global__ void __launch_bounds__(NT) k_ml_update(Params P) {
+__global__ void __launch_bounds__(NT, 512 / NT) k_ml_update(Params P) {
     if (P.st->status != kRunning) return;
     const int p = P.st->p;
     phase_update(P, p);
@@ -425,11 +457,12 @@ static lp_handle* create_common(int m, int n, cudaStream_t stream, bool own_stre
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
     h->max_grid = std::max(1, nsm) * 32;   // rpart capacity (>= any co-resident grid)
     const int nstrips = (h->ld + kStripCols - 1) / kStripCols;
-    // one allocation: T | F | R | cpart | rpart | st | basis | sol
+    // one allocation: T | F | R | act | cpart | rpart | st | basis | sol
     const size_t sz_T = (size_t)(m + 1) * (size_t)h->ld * sizeof(double);
     const size_t off_F = align_up(sz_T, 256);
     const size_t off_R = align_up(off_F + (size_t)(m + 1) * sizeof(double), 256);
-    const size_t off_cp = align_up(off_R + (size_t)h->ld * sizeof(double), 256);
+    const size_t off_act = align_up(off_R + (size_t)h->ld * sizeof(double), 256);
+    const size_t off_cp = align_up(off_act + (size_t)(h->ld / 4) * sizeof(int), 256);
     const size_t off_rp = align_up(off_cp + (size_t)nstrips * sizeof(ArgPart), 256);
     const size_t off_st = align_up(off_rp + (size_t)h->max_grid * sizeof(RatPart), 256);
     const size_t off_bs = align_up(off_st + sizeof(DevState), 256);
@@ -446,6 +479,7 @@ static lp_handle* create_common(int m, int n, cudaStream_t stream, bool own_stre
     h->T = (double*)base;
     h->F = (double*)(base + off_F);
     h->R = (double*)(base + off_R);
+    h->act = (int*)(base + off_act);
     h->cpart = (ArgPart*)(base + off_cp);
     h->rpart = (RatPart*)(base + off_rp);
     h->st = (DevState*)(base + off_st);
@@ -576,6 +610,7 @@ static lp_status solve_nt(lp_handle* h, const lp_options& o, cudaStream_t s) {
     P.basis = h->basis;
     P.F = h->F;
     P.R = h->R;
+    P.act = h->act;
     P.cpart = h->cpart;
     P.rpart = h->rpart;
     P.st = h->st;
@@ -669,12 +704,21 @@ static lp_status solve_nt(lp_handle* h, const lp_options& o, cudaStream_t s) {
     h->stats.pivot_ms = ms_pivot;
     h->stats.kernel_launches = launches;
     h->stats.dense_update_bytes = 2.0 * (double)(m + 1) * (double)h->W * sizeof(double) * (double)hs.iters;
-    h->stats.update_bytes = P.skip_zero ? 64.0 * (double)(m + 1) * (double)hs.active_sectors
-                                        : 2.0 * (double)(m + 1) * (double)h->ld * sizeof(double) * (double)hs.iters;
+    // bytes Step 3 moves: read + write of every listed 32-B group in rows
+    // 1..m except p, read + write of the objective row and write of row p over
+    // all groups; plus the side traffic of Steps 1-2 and the staging: column q
+    // and right-hand-side sectors (m + 1 rows), pivot row read, R write + read.
+    {
+        const double nsec = (double)(h->ld / 4);
+        const double upd = 64.0 * (double)(m - 1) * (double)hs.active_sectors + 96.0 * nsec * (double)hs.iters;
+        const double side = (64.0 * (double)(m + 1) + 24.0 * (double)h->ld) * (double)hs.iters;
+        h->stats.update_bytes = upd + side;
+    }
     h->stats.path = path;
     h->stats.grid = grid;
     h->stats.block = NT;
     h->stats.ld = h->ld;
+    for (int k = 0; k < 6; ++k) h->stats.phase_ms[k] = 1e-6 * (double)hs.phase_ns[k];
 
     h->iters = hs.iters;
     h->solved = true;
@@ -833,7 +877,7 @@ static void* noalloc_scratch(int device) {
 template <int NT>
 static lp_status noalloc_nt(int m, int n, const double* dA, const double* db, const double* dc, double* dT,
                             int ld, int* dbasis, const lp_options& o, long long* iters_out, char* base,
-                            size_t off_R, size_t off_cp, size_t off_rp, size_t off_st) {
+                            size_t off_R, size_t off_act, size_t off_cp, size_t off_rp, size_t off_st) {
     cudaStream_t s = (cudaStream_t)o.stream;
     int device = 0;
     CUDA_TRY(cudaGetDevice(&device), LP_ERR_CUDA);
@@ -846,6 +890,7 @@ static lp_status noalloc_nt(int m, int n, const double* dA, const double* db, co
     P.basis = dbasis;
     P.F = (double*)base;
     P.R = (double*)(base + off_R);
+    P.act = (int*)(base + off_act);
     P.cpart = (ArgPart*)(base + off_cp);
     P.rpart = (RatPart*)(base + off_rp);
     P.st = (DevState*)(base + off_st);
@@ -969,10 +1014,11 @@ lp_status lp_solve_noalloc(int m, int n, const double* dA, const double* db, con
         set_error("lp_solve_noalloc: invalid options (log_capacity must be 0, blocks <= %d)", kNoAllocMaxGrid);
         return LP_ERR_INVALID;
     }
-    // layout of the array: F | R | cpart | rpart | state
+    // layout of the array: F | R | act | cpart | rpart | state
     const size_t nstrips = ((size_t)ld + kStripCols - 1) / kStripCols;
     const size_t off_R = align_up((size_t)(m + 1) * sizeof(double), 256);
-    const size_t off_cp = align_up(off_R + (size_t)ld * sizeof(double), 256);
+    const size_t off_act = align_up(off_R + (size_t)ld * sizeof(double), 256);
+    const size_t off_cp = align_up(off_act + (size_t)(ld / 4) * sizeof(int), 256);
     const size_t off_rp = align_up(off_cp + nstrips * sizeof(ArgPart), 256);
     const size_t off_st = align_up(off_rp + (size_t)kNoAllocMaxGrid * sizeof(RatPart), 256);
     const size_t need = align_up(off_st + sizeof(DevState), 256);
@@ -988,9 +1034,9 @@ lp_status lp_solve_noalloc(int m, int n, const double* dA, const double* db, con
     if (!base) return LP_ERR_CUDA;
     const int nt = o.threads ? o.threads : 256;
     switch (nt) {
-        case 128: return noalloc_nt<128>(m, n, dA, db, dc, dT, (int)ld, dbasis, o, iters, base, off_R, off_cp, off_rp, off_st);
-        case 256: return noalloc_nt<256>(m, n, dA, db, dc, dT, (int)ld, dbasis, o, iters, base, off_R, off_cp, off_rp, off_st);
-        case 512: return noalloc_nt<512>(m, n, dA, db, dc, dT, (int)ld, dbasis, o, iters, base, off_R, off_cp, off_rp, off_st);
+        case 128: return noalloc_nt<128>(m, n, dA, db, dc, dT, (int)ld, dbasis, o, iters, base, off_R, off_act, off_cp, off_rp, off_st);
+        case 256: return noalloc_nt<256>(m, n, dA, db, dc, dT, (int)ld, dbasis, o, iters, base, off_R, off_act, off_cp, off_rp, off_st);
+        case 512: return noalloc_nt<512>(m, n, dA, db, dc, dT, (int)ld, dbasis, o, iters, base, off_R, off_act, off_cp, off_rp, off_st);
         default:
             set_error("lp_solve_noalloc: threads must be 0, 128, 256 or 512 (got %d)", nt);
             return LP_ERR_INVALID;

@@ -32,7 +32,13 @@ namespace tsx {
 constexpr int kRunning = 100;      // status while the iteration is in progress
 constexpr int kStripCols = 128;    // columns of one warp strip (32 lanes x 4)
 constexpr int kUnitRows = 32;      // rows of one work unit (one strip)
-constexpr int kRowsInFlight = 8;   // rows loaded before the first store
+#ifndef TSX_ROWS_IN_FLIGHT
+#define TSX_ROWS_IN_FLIGHT 8
+#endif
+#ifndef TSX_GRAB
+#define TSX_GRAB 2
+#endif
+constexpr int kRowsInFlight = TSX_ROWS_IN_FLIGHT;   // rows loaded before the first store
 constexpr int kMaxWarps = 32;      // warps per block upper bound (1024 threads)
 
 // status codes (same values as lp_status in tabsimplex.h)
@@ -62,6 +68,11 @@ struct DevState {
     double theta;                      // minimum ratio of the current pivot
     unsigned bar_count;                // grid barrier: blocks arrived
     unsigned bar_gen;                  // grid barrier: generation
+    unsigned nact;                     // active 32-B column groups of this pivot
+    unsigned next_slot;                // P4 work counter (slots handed out)
+    long long phase_ns[6];             // block 0's time per phase: work of
+                                       // {select+ratio, stage, update}, then the
+                                       // barrier wait after each of them
 };
 
 struct Params {
@@ -70,6 +81,7 @@ struct Params {
     int* basis;          // m: variable basic in row i+1
     double* F;           // m+1: column q of the tableau before the update
     double* R;           // ld: scaled pivot row
+    int* act;            // ld/4: indices of the 32-B column groups Step 3 updates
     ArgPart* cpart;      // nstrips: objective-row argmin partial per strip
     RatPart* rpart;      // grid blocks: ratio-test partial per block
     DevState* st;
@@ -345,10 +357,15 @@ __device__ ArgPart phase_entering(const Params& P, BlockScratch& s) {
 }
 
 // P2: ratio test on column q and copy of column q into F; one partial per block.
+// Row i goes to block i mod G, so the FP64 divisions spread over every SM.
 __device__ void phase_ratio(const Params& P, int q, int bland, BlockScratch& s) {
     RatPart best = rat_none();
     const long long nth = (long long)gridDim.x * blockDim.x;
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i <= P.m; i += nth) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {   // counted again in P3 / P4
+        P.st->nact = 0;
+        P.st->next_slot = 0;
+    }
+    for (long long i = (long long)threadIdx.x * gridDim.x + blockIdx.x; i <= P.m; i += nth) {
         const double* row = P.T + (size_t)i * (size_t)P.ld;
         const double a = __ldcg(row + q);
         __stcg(P.F + i, a);
@@ -371,95 +388,148 @@ __device__ RatPart phase_leaving(const Params& P, BlockScratch& s) {
     return block_rat(a, s);
 }
 
-// P3b: R[j] = T[p][j] / piv over the padded row; counts the 32-B column groups
-// with a nonzero entry (the groups P4 has to update when skipping).
+// P3b: pivot-row staging.  (1) The 32-B column groups of row p holding a
+// nonzero entry -- exactly the groups whose scaled entries R can be nonzero --
+// are compacted into P.act (warp ballot, one atomic per warp; the order of the
+// list does not matter, every group is updated independently).  With
+// skip_zero == 0 every group is listed.  (2) R[j] = T[p][j] / piv over the
+// padded row, element j on block j mod G so the divisions spread over all SMs.
 __device__ void phase_stage_row(const Params& P, int p, double piv, BlockScratch& s) {
     const double* row = P.T + (size_t)p * (size_t)P.ld;
+    const int lane = threadIdx.x & 31;
     const long long nsec = P.ld / 4;
-    const long long nth = (long long)gridDim.x * blockDim.x;
-    unsigned long long nz = 0;
-    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < nsec; k += nth) {
-        sec4 v = ld_sector_cg(row + 4 * k);
-        sec4 r;
-        r.x = v.x / piv;
-        r.y = v.y / piv;
-        r.z = v.z / piv;
-        r.w = v.w / piv;
-        st_sector(P.R + 4 * k, r);
-        nz += (r.x != 0.0 || r.y != 0.0 || r.z != 0.0 || r.w != 0.0) ? 1ull : 0ull;
+    const long long wi = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
+    const long long nwi = (long long)(blockDim.x >> 5) * gridDim.x;
+    for (long long base = wi * 32; base < nsec; base += nwi * 32) {
+        const long long k = base + lane;
+        bool nz = false;
+        if (k < nsec) {
+            if (P.skip_zero) {
+                const sec4 v = ld_sector_cg(row + 4 * k);
+                nz = v.x != 0.0 || v.y != 0.0 || v.z != 0.0 || v.w != 0.0;
+            } else {
+                nz = true;
+            }
+        }
+        const unsigned mask = __ballot_sync(0xffffffffu, nz);
+        if (mask) {
+            unsigned off = 0;
+            if (lane == 0) off = atomicAdd(&P.st->nact, (unsigned)__popc(mask));
+            off = __shfl_sync(0xffffffffu, off, 0);
+            if (nz) P.act[off + __popc(mask & ((1u << lane) - 1u))] = (int)k;
+        }
     }
-    nz = block_sum(nz, s);
-    if (threadIdx.x == 0 && nz) atomicAdd(&P.st->active_sectors, nz);
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    for (long long e = (long long)threadIdx.x * gridDim.x + blockIdx.x; e < P.ld; e += nth)
+        __stcg(P.R + e, __ldcg(row + e) / piv);
 }
 
-// P4: the rank-1 update, one warp per (strip, 32-row unit), contiguous unit
-// ranges per warp in strip-major order (the scaled pivot row of a strip stays
-// in registers across the warp's units).  Rows i != p: T = fma(-F[i], R, T);
-// row p: T = R.  With skip_zero, a lane whose four R entries are all zero
-// touches only the objective row and row p.  The warp that updates the
-// objective row of a strip writes that strip's argmin partial.
-__device__ void phase_update(const Params& P, int p) {
+// P4a: the objective row and the pivot row, every column group.  One warp per
+// strip of 128 columns: T[0][j] = fma(-F[0], R[j], T[0][j]) with the strip's
+// argmin partial of the new objective row (the next Step 1's input), and
+// T[p][j] = R[j].
+__device__ void phase_update_edge_rows(const Params& P, int p) {
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const long long u0 = gw * P.nunits / nw;
-    const long long u1 = (gw + 1) * P.nunits / nw;
-    const int rows = P.m + 1;
+    const double f0 = __ldcg(P.F);
     const int jend = P.W - 1;
-    int strip = -1, j = 0;
-    bool act = false, live = false;
-    sec4 r = make_sec4(0.0, 0.0, 0.0, 0.0);
-    for (long long u = u0; u < u1; ++u) {
-        const int s = (int)(u / P.nrc);
-        const int rc = (int)(u - (long long)s * P.nrc);
-        if (s != strip) {
-            strip = s;
-            j = s * kStripCols + lane * 4;
-            act = j < P.ld;
-            r = act ? ld_sector_cg(P.R + j) : make_sec4(0.0, 0.0, 0.0, 0.0);
-            live = act && (!P.skip_zero || r.x != 0.0 || r.y != 0.0 || r.z != 0.0 || r.w != 0.0);
-        }
-        const int i0 = rc * kUnitRows;
-        const int i1 = min(i0 + kUnitRows, rows);
-        const double fl = (i0 + lane < i1) ? __ldcg(P.F + i0 + lane) : 0.0;
+    for (long long s = gw; s < P.nstrips; s += nw) {
+        const int j = (int)s * kStripCols + lane * 4;
         ArgPart a = arg_none();
-        for (int ib = i0; ib < i1; ib += kRowsInFlight) {
-            sec4 v[kRowsInFlight];
-#pragma unroll
-            for (int k = 0; k < kRowsInFlight; ++k) {
-                const int i = ib + k;
-                const bool go = act && i < i1 && (live || i == 0) && i != p;
-                if (go) v[k] = ld_sector_stream(P.T + (size_t)i * (size_t)P.ld + j);
-            }
-#pragma unroll
-            for (int k = 0; k < kRowsInFlight; ++k) {
-                const int i = ib + k;
-                const double f = __shfl_sync(0xffffffffu, fl, (i - i0) & 31);
-                if (act && i < i1 && (live || i == 0 || i == p)) {
-                    sec4 o;
-                    if (i == p) {
-                        o = r;
-                    } else {
-                        o.x = __fma_rn(-f, r.x, v[k].x);
-                        o.y = __fma_rn(-f, r.y, v[k].y);
-                        o.z = __fma_rn(-f, r.z, v[k].z);
-                        o.w = __fma_rn(-f, r.w, v[k].w);
-                    }
-                    st_sector(P.T + (size_t)i * (size_t)P.ld + j, o);
-                    if (i == 0) {
-                        arg_consider(a, o.x, j, jend, P.eps_d);
-                        arg_consider(a, o.y, j + 1, jend, P.eps_d);
-                        arg_consider(a, o.z, j + 2, jend, P.eps_d);
-                        arg_consider(a, o.w, j + 3, jend, P.eps_d);
-                    }
-                }
-            }
+        if (j < P.ld) {
+            const sec4 r = ld_sector_cg(P.R + j);
+            const sec4 v = ld_sector_stream(P.T + j);
+            sec4 o;
+            o.x = __fma_rn(-f0, r.x, v.x);
+            o.y = __fma_rn(-f0, r.y, v.y);
+            o.z = __fma_rn(-f0, r.z, v.z);
+            o.w = __fma_rn(-f0, r.w, v.w);
+            st_sector(P.T + j, o);
+            st_sector(P.T + (size_t)p * (size_t)P.ld + j, r);
+            arg_consider(a, o.x, j, jend, P.eps_d);
+            arg_consider(a, o.y, j + 1, jend, P.eps_d);
+            arg_consider(a, o.z, j + 2, jend, P.eps_d);
+            arg_consider(a, o.w, j + 3, jend, P.eps_d);
         }
-        if (i0 == 0) {
-            a = warp_arg(a);
-            if (lane == 0) store_arg(P.cpart + s, a);
+        a = warp_arg(a);
+        if (lane == 0) store_arg(P.cpart + s, a);
+    }
+}
+
+// P4b: the rank-1 update of rows 1..m except p on the listed column groups:
+// T[i][j] = fma(-F[i], R[j], T[i][j]).  Work slots are (group of kRowsInFlight
+// rows, chunk of 32 listed column groups), numbered row-group-major, so that
+// consecutive slots stream along the same rows and the rows' F values stay in
+// registers while the row group is unchanged.  One listed column group per
+// lane.  Groups not listed have R == 0: their update is the identity.
+// One work slot: rows i0 .. i0+nrows-1 (row p excluded) of the column group
+// listed at entry c*32 + lane.
+__device__ __forceinline__ void update_slot(const Params& P, int p, unsigned nact, long long c, int i0,
+                                            int nrows, const double* f) {
+    const long long e = c * 32 + (threadIdx.x & 31);
+    if (e >= (long long)nact) return;
+    const size_t col = 4 * (size_t)__ldcg(P.act + e);
+    const sec4 r = ld_sector_cg(P.R + col);
+    sec4 v[kRowsInFlight];
+#pragma unroll
+    for (int k = 0; k < kRowsInFlight; ++k) {
+        const int i = i0 + k;
+        if (k < nrows && i != p) v[k] = ld_sector_stream(P.T + (size_t)i * (size_t)P.ld + col);
+    }
+#pragma unroll
+    for (int k = 0; k < kRowsInFlight; ++k) {
+        const int i = i0 + k;
+        if (k < nrows && i != p) {
+            sec4 o;
+            o.x = __fma_rn(-f[k], r.x, v[k].x);
+            o.y = __fma_rn(-f[k], r.y, v[k].y);
+            o.z = __fma_rn(-f[k], r.z, v[k].z);
+            o.w = __fma_rn(-f[k], r.w, v[k].w);
+            st_sector(P.T + (size_t)i * (size_t)P.ld + col, o);
         }
     }
+}
+
+__device__ void phase_update_bulk(const Params& P, int p, unsigned nact) {
+    const int lane = threadIdx.x & 31;
+    const long long nchunks = ((long long)nact + 31) / 32;
+    const long long ngroups = ((long long)P.m + kRowsInFlight - 1) / kRowsInFlight;
+    const long long total = nchunks * ngroups;
+    long long gcur = -1;
+    double f[kRowsInFlight];
+    int i0 = 1, nrows = 0;
+    // Slots are handed out TSX_GRAB at a time from a counter (a static split
+    // leaves the slowest blocks ~15% behind the mean); the next grab is
+    // requested before the current one is processed.
+    unsigned next = 0;
+    if (lane == 0) next = atomicAdd(&P.st->next_slot, (unsigned)TSX_GRAB);
+    next = __shfl_sync(0xffffffffu, next, 0);
+    while ((long long)next < total) {
+        const long long u0 = next;
+        const long long u1 = min(total, u0 + TSX_GRAB);
+        if (lane == 0) next = atomicAdd(&P.st->next_slot, (unsigned)TSX_GRAB);
+        next = __shfl_sync(0xffffffffu, next, 0);
+        for (long long u = u0; u < u1; ++u) {
+            const long long g = u / nchunks;
+            const long long c = u - g * nchunks;
+            if (g != gcur) {
+                gcur = g;
+                i0 = 1 + (int)g * kRowsInFlight;
+                nrows = min(kRowsInFlight, P.m + 1 - i0);
+#pragma unroll
+                for (int k = 0; k < kRowsInFlight; ++k) f[k] = k < nrows ? __ldcg(P.F + i0 + k) : 0.0;
+            }
+            update_slot(P, p, nact, c, i0, nrows, f);
+        }
+    }
+}
+
+__device__ void phase_update(const Params& P, int p) {
+    const unsigned nact = *(volatile const unsigned*)&P.st->nact;
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.st->active_sectors += nact;
+    phase_update_edge_rows(P, p);
+    phase_update_bulk(P, p, nact);
 }
 
 }  // namespace tsx

@@ -55,7 +55,7 @@ def _assert_same(gpu, ref):
 
 
 SHAPES = [(1, 1), (1, 7), (7, 1), (3, 4), (16, 16), (37, 53), (64, 64), (100, 300),
-          (300, 100), (129, 257), (256, 256)]
+          (300, 100), (129, 257), (256, 256), (1024, 1024), (512, 2048)]
 
 
 @pytest.mark.parametrize("m,n", SHAPES)
