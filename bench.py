@@ -151,7 +151,7 @@ def measured_peaks():
 def profile_traffic(m, n):
     """ncu DRAM bytes per pivot of the update kernel, if a summary for this
     exact kernel build and workload is committed under profiles/."""
-    path = os.path.join(ROOT, "profiles", "traffic.json")
+    path = os.path.join(ROOT, "profiles", "traffic_k_pivot_persistent.txt")
     try:
         with open(path) as fh:
             d = json.load(fh)
