@@ -53,6 +53,7 @@ typedef enum {
 
 enum { LP_RULE_DANTZIG = 0, LP_RULE_BLAND = 1 };
 enum { LP_PATH_AUTO = 0, LP_PATH_PERSISTENT = 1, LP_PATH_MULTILAUNCH = 2 };
+enum { LP_PREC_FP64 = 0, LP_PREC_FP32 = 1 };
 
 /* Solve options.  Initialise with lp_options_init() and change fields. */
 typedef struct {
@@ -83,6 +84,19 @@ typedef struct {
                                      0 = none                                   */
     void *stream;                 /* cudaStream_t to run on; NULL = the
                                      handle's own stream                        */
+    int precision;                /* LP_PREC_FP64 (default): double tableau,
+                                     results equal the FP64 method step by step.
+                                     LP_PREC_FP32: float tableau for every pivot
+                                     (half the bytes), then the final basis is
+                                     refactorised in FP64 on the GPU (x_B, y
+                                     solves, primal/dual/gap checks) and FP64
+                                     cleanup pivots run until the checks pass   */
+    double eps_d_fp32;            /* eps_d of the float pivots (default 1e-5)   */
+    double eps_p_fp32;            /* eps_p of the float pivots (default 1e-6)   */
+    double recover_tol;           /* FP64 feasibility tolerance of the checks
+                                     (default 1e-9, absolute)                   */
+    int cleanup_max;              /* cap on FP64 cleanup pivots (default 1000);
+                                     beyond it the solve ends LP_ERR_NUMERIC    */
 } lp_options;
 
 /* Per-solve measurements (device time from CUDA events on the solve stream). */
@@ -103,6 +117,14 @@ typedef struct {
                                      time of {ratio test (Steps 1-2), pivot-row
                                      staging, rank-1 update (Step 3)}, then the
                                      barrier wait after each of them            */
+    int precision;                /* precision of the solve                     */
+    int pivot_status;             /* status at the end of the pivot phase       */
+    int k;                        /* FP32 path: structural basic variables      */
+    int cleanup_pivots;           /* FP32 path: FP64 cleanup pivots             */
+    double recover_ms;            /* FP32 path: FP64 recovery time              */
+    double primal_violation;      /* FP32 path: max(0, -min basic value)        */
+    double dual_violation;        /* FP32 path: max(0, -min objective-row entry)*/
+    double gap;                   /* FP32 path: |c^T x - b^T y|                 */
 } lp_stats;
 
 /* Fill *opt with the defaults listed above.  NULL is ignored. */
@@ -137,13 +159,16 @@ lp_status lp_solve(lp_t h, const lp_options *opt);
  * objective-row entry of the slack column of constraint i (m entries, the dual
  * values); obj is the objective row's right-hand side; basis[i] is the 0-based
  * variable basic in constraint row i+1 (m entries); iters is the number of
- * pivots.  Every output is a HOST pointer and may be NULL.  Returns the status
- * of the last solve, or LP_ERR_STATE before any solve. */
+ * pivots.  After an LP_PREC_FP32 solve, x, y and obj are the FP64 recovery's
+ * values and basis lists the final basic variables in ascending order.  Every
+ * output is a HOST pointer and may be NULL.  Returns the status of the last
+ * solve, or LP_ERR_STATE before any solve. */
 lp_status lp_get_solution(lp_t h, double *x, double *y, double *obj, int *basis,
                           long long *iters);
 
 /* Copy the current tableau to HOST memory T ((m + 1) x (n + m + 1) row-major,
- * float64, without the padding).  Returns LP_ERR_STATE before any solve. */
+ * float64, without the padding; a float tableau is widened).  Returns
+ * LP_ERR_STATE before any solve. */
 lp_status lp_get_tableau(lp_t h, double *T);
 
 /* Copy the recorded (q, p) pairs of the last solve (q = entering column,

@@ -75,6 +75,19 @@ def _load():
         lib.orc_solve.restype = ctypes.c_int
         lib.orc_extract.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, dp, dp, dp]
         lib.orc_extract.restype = None
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.orc32_build.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, dp, fp, ip]
+        lib.orc32_build.restype = ctypes.c_int
+        lib.orc32_entering.argtypes = [ctypes.c_int, ctypes.c_int, fp, ctypes.c_int, ctypes.c_double]
+        lib.orc32_entering.restype = ctypes.c_int
+        lib.orc32_leaving.argtypes = [ctypes.c_int, ctypes.c_int, fp, ip, ctypes.c_int,
+                                      ctypes.c_int, ctypes.c_double, fp]
+        lib.orc32_leaving.restype = ctypes.c_int
+        lib.orc32_pivot.argtypes = [ctypes.c_int, ctypes.c_int, fp, ctypes.c_int, ctypes.c_int, fp, fp]
+        lib.orc32_pivot.restype = None
+        lib.orc32_solve.argtypes = [ctypes.c_int, ctypes.c_int, fp, ip, ctypes.POINTER(_Opts),
+                                    ctypes.POINTER(ctypes.c_long), ip, ip, ctypes.c_long]
+        lib.orc32_solve.restype = ctypes.c_int
         _lib = lib
     return _lib
 
@@ -184,3 +197,59 @@ def solve(A, b, c, opts: Options | None = None, log_cap: int = 1 << 20) -> Resul
     st, it, qlog, plog = solve_tableau(T, basis, m, n, opts, log_cap)
     x, y, obj = extract(T, basis, m, n)
     return Result(st, it, x, y, obj, basis, qlog, plog, T)
+
+
+# ---------------------------------------------------------------- float variant
+def _fp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_float))
+
+
+def build_tableau32(A, b, c):
+    """Initialization Step on a float tableau (inputs rounded to float)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    b = np.ascontiguousarray(b, dtype=np.float64)
+    c = np.ascontiguousarray(c, dtype=np.float64)
+    m, n = A.shape
+    T = np.empty((m + 1, n + m + 1), dtype=np.float32)
+    basis = np.empty(m, dtype=np.int32)
+    if _load().orc32_build(m, n, _dp(A), _dp(b), _dp(c), _fp(T), _ip(basis)) != 0:
+        raise ValueError("invalid LP (need m, n > 0 and finite b >= 0)")
+    return T, basis
+
+
+def entering32(T, m, n, bland=False, eps_d=1e-5) -> int:
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    return int(_load().orc32_entering(m, n, _fp(T), int(bland), eps_d))
+
+
+def leaving32(T, basis, m, n, q, bland=False, eps_p=1e-6):
+    T = np.ascontiguousarray(T, dtype=np.float32)
+    basis = np.ascontiguousarray(basis, dtype=np.int32)
+    ratio = ctypes.c_float(0.0)
+    p = _load().orc32_leaving(m, n, _fp(T), _ip(basis), q, int(bland), eps_p, ctypes.byref(ratio))
+    return int(p), ratio.value
+
+
+def pivot32(T, m, n, p, q):
+    assert T.flags.c_contiguous and T.dtype == np.float32
+    r = np.empty(T.shape[1], dtype=np.float32)
+    f = np.empty(T.shape[0], dtype=np.float32)
+    _load().orc32_pivot(m, n, _fp(T), p, q, _fp(r), _fp(f))
+
+
+def solve32(A, b, c, opts: Options | None = None, log_cap: int = 1 << 20):
+    """Steps 1-3 on a float tableau from the slack basis (default tolerances
+    eps_d = 1e-5, eps_p = 1e-6).  Returns (status, iters, qlog, plog, T, basis)."""
+    opts = opts or Options(eps_d=1e-5, eps_p=1e-6)
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    m, n = A.shape
+    T, basis = build_tableau32(A, b, c)
+    cap = int(log_cap)
+    qlog = np.full(cap, -1, dtype=np.int32)
+    plog = np.full(cap, -1, dtype=np.int32)
+    it = ctypes.c_long(0)
+    o = opts.c()
+    st = _load().orc32_solve(m, n, _fp(T), _ip(basis), ctypes.byref(o), ctypes.byref(it),
+                             _ip(qlog), _ip(plog), cap)
+    k = min(it.value, cap)
+    return int(st), int(it.value), qlog[:k].copy(), plog[:k].copy(), T, basis

@@ -262,3 +262,165 @@ void orc_extract(int m, int n, const double *T, const int *basis, double *x,
     if (obj)
         *obj = TAB(T, W, 0, W - 1);
 }
+
+/* ------------------------------------------------------------------------
+ * The same steps on a float tableau (the single-precision variant of the
+ * method): the tableau entries are the inputs rounded to float, r_j and the
+ * ratios are float divisions, the update is one fmaf per entry.  Comparisons
+ * against the tolerances are made in double on the float values.  Used to
+ * check a float pivot kernel step by step; the result of the method itself is
+ * checked against the double oracle above.
+ * ------------------------------------------------------------------------ */
+int orc32_build(int m, int n, const double *A, const double *b, const double *c,
+                float *T, int *basis)
+{
+    if (m <= 0 || n <= 0 || !A || !b || !c || !T || !basis)
+        return ORC_INVALID;
+    const int W = n + m + 1;
+    for (int i = 0; i < m; ++i)
+        if (!(b[i] >= 0.0) || !isfinite(b[i]))
+            return ORC_INVALID;
+    memset(T, 0, sizeof(float) * (size_t)(m + 1) * (size_t)W);
+    for (int j = 0; j < n; ++j)
+        TAB(T, W, 0, j) = (float)(-c[j]);
+    for (int i = 1; i <= m; ++i) {
+        for (int j = 0; j < n; ++j)
+            TAB(T, W, i, j) = (float)A[(size_t)(i - 1) * (size_t)n + (size_t)j];
+        TAB(T, W, i, n + i - 1) = 1.0f;
+        TAB(T, W, i, W - 1) = (float)b[i - 1];
+        basis[i - 1] = n + i - 1;
+    }
+    return ORC_OPTIMAL;
+}
+
+int orc32_entering(int m, int n, const float *T, int bland, double eps_d)
+{
+    const int W = n + m + 1;
+    int q = -1;
+    float best = 0.0f;
+    for (int j = 0; j < W - 1; ++j) {
+        float v = TAB(T, W, 0, j);
+        if ((double)v < -eps_d) {
+            if (bland)
+                return j;
+            if (q < 0 || v < best) {
+                q = j;
+                best = v;
+            }
+        }
+    }
+    return q;
+}
+
+int orc32_leaving(int m, int n, const float *T, const int *basis, int q,
+                  int bland, double eps_p, float *ratio_out)
+{
+    const int W = n + m + 1;
+    int p = -1;
+    float best = 0.0f;
+    for (int i = 1; i <= m; ++i) {
+        float a = TAB(T, W, i, q);
+        if ((double)a > eps_p) {
+            float r = TAB(T, W, i, W - 1) / a;
+            int take;
+            if (p < 0)
+                take = 1;
+            else if (r < best)
+                take = 1;
+            else if (r == best && bland)
+                take = basis[i - 1] < basis[p - 1];
+            else
+                take = 0;
+            if (take) {
+                p = i;
+                best = r;
+            }
+        }
+    }
+    if (ratio_out)
+        *ratio_out = best;
+    return p;
+}
+
+void orc32_pivot(int m, int n, float *T, int p, int q, float *r, float *f)
+{
+    const int W = n + m + 1;
+    const float piv = TAB(T, W, p, q);
+    for (int j = 0; j < W; ++j)
+        r[j] = TAB(T, W, p, j) / piv;
+    for (int i = 0; i <= m; ++i)
+        f[i] = TAB(T, W, i, q);
+    for (int i = 0; i <= m; ++i) {
+        if (i == p)
+            continue;
+        for (int j = 0; j < W; ++j)
+            TAB(T, W, i, j) = fmaf(-f[i], r[j], TAB(T, W, i, j));
+    }
+    for (int j = 0; j < W; ++j)
+        TAB(T, W, p, j) = r[j];
+}
+
+int orc32_solve(int m, int n, float *T, int *basis, const orc_options *opt,
+                long *iters_out, int *qlog, int *plog, long log_cap)
+{
+    if (m <= 0 || n <= 0 || !T || !basis || !opt)
+        return ORC_INVALID;
+    const int W = n + m + 1;
+    const long cap = opt->max_iters < 0 ? 50L * ((long)m + (long)n) : opt->max_iters;
+    float *r = (float *)malloc(sizeof(float) * (size_t)W);
+    float *f = (float *)malloc(sizeof(float) * (size_t)(m + 1));
+    if (!r || !f) {
+        free(r);
+        free(f);
+        return ORC_INVALID;
+    }
+    int bland = opt->rule == 1;
+    int degen_run = 0;
+    long it = 0;
+    int status;
+    for (;;) {
+        int q = orc32_entering(m, n, T, bland, opt->eps_d);
+        if (q < 0) {
+            status = ORC_OPTIMAL;
+            break;
+        }
+        if (it >= cap) {
+            status = ORC_ITER_LIMIT;
+            break;
+        }
+        float theta = 0.0f;
+        int p = orc32_leaving(m, n, T, basis, q, bland, opt->eps_p, &theta);
+        if (p < 0) {
+            status = ORC_UNBOUNDED;
+            break;
+        }
+        if (!isfinite(TAB(T, W, p, q)) || !isfinite(theta)) {
+            status = ORC_NUMERIC;
+            break;
+        }
+        if (it < log_cap) {
+            if (qlog)
+                qlog[it] = q;
+            if (plog)
+                plog[it] = p;
+        }
+        orc32_pivot(m, n, T, p, q, r, f);
+        basis[p - 1] = q;
+        ++it;
+        if (opt->rule == 0) {
+            if (theta <= 0.0f) {
+                ++degen_run;
+                if (opt->k_cyc > 0 && degen_run >= opt->k_cyc)
+                    bland = 1;
+            } else {
+                degen_run = 0;
+                bland = 0;
+            }
+        }
+    }
+    free(r);
+    free(f);
+    if (iters_out)
+        *iters_out = it;
+    return status;
+}

@@ -20,6 +20,7 @@ STATUS_NAMES = {0: "OPTIMAL", 1: "UNBOUNDED", 2: "ITER_LIMIT", 3: "NUMERIC", -1:
                 -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE"}
 LP_RULE_DANTZIG, LP_RULE_BLAND = 0, 1
 LP_PATH_AUTO, LP_PATH_PERSISTENT, LP_PATH_MULTILAUNCH = 0, 1, 2
+LP_PREC_FP64, LP_PREC_FP32 = 0, 1
 
 # every symbol include/tabsimplex.h declares
 EXPORTS = ("lp_options_init", "lp_create", "lp_create_device", "lp_solve", "lp_get_solution",
@@ -44,6 +45,11 @@ class lp_options(ctypes.Structure):
         ("blocks", ctypes.c_int),
         ("log_capacity", ctypes.c_longlong),
         ("stream", ctypes.c_void_p),
+        ("precision", ctypes.c_int),
+        ("eps_d_fp32", ctypes.c_double),
+        ("eps_p_fp32", ctypes.c_double),
+        ("recover_tol", ctypes.c_double),
+        ("cleanup_max", ctypes.c_int),
     ]
 
 
@@ -60,6 +66,14 @@ class lp_stats(ctypes.Structure):
         ("block", ctypes.c_int),
         ("ld", ctypes.c_int),
         ("phase_ms", ctypes.c_double * 6),
+        ("precision", ctypes.c_int),
+        ("pivot_status", ctypes.c_int),
+        ("k", ctypes.c_int),
+        ("cleanup_pivots", ctypes.c_int),
+        ("recover_ms", ctypes.c_double),
+        ("primal_violation", ctypes.c_double),
+        ("dual_violation", ctypes.c_double),
+        ("gap", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -1,12 +1,8 @@
-// Host side and kernels of the C ABI declared in include/tabsimplex.h: the
-// dense full-tableau simplex of arXiv 2211.10979 (Section III), one GPU.
-//
-// Kernels:
-//   k_validate       checks the device inputs (finite, b >= 0) before a build
-//   k_build          Initialization Step: tableau of Table I with the slack basis
-//   k_pivot_persistent  Steps 1-3 iterated inside one cooperative launch
-//   k_ml_*           the same phases, one launch each (fallback / profiling)
-//   k_extract_*      solution read-out (x, y, objective)
+// Host side of the C ABI declared in include/tabsimplex.h: the dense
+// full-tableau simplex of arXiv 2211.10979 (Section III) on one GPU, with a
+// double tableau (exact path) or a float tableau followed by an FP64 recovery
+// of the final basis.  Kernels live in tsx_kernels.cuh (pivoting) and
+// tsx_recover.cuh (FP64 recovery).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -16,9 +12,11 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "tabsimplex.h"
-#include "tsx_device.cuh"
+#include "tsx_kernels.cuh"
+#include "tsx_recover.cuh"
 
 using namespace tsx;
 
@@ -55,9 +53,48 @@ struct Block {
     size_t bytes = 0;
 };
 
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Sequential carving of one allocation into 256-byte aligned pieces.
+struct Carve {
+    size_t off = 0;
+    size_t take(size_t bytes) {
+        const size_t at = align_up(off, 256);
+        off = at + bytes;
+        return at;
+    }
+};
+
 // ---------------------------------------------------------------- handle
+struct Work {                        // pivot buffers for one precision
+    Block blk;
+    int elem = 0;                    // bytes per tableau entry (8 or 4), 0 = none
+    int ld = 0;
+    void* T = nullptr;
+    void* F = nullptr;
+    void* R = nullptr;
+    int* act = nullptr;
+    ArgPart* cpart = nullptr;
+    RatPart* rpart = nullptr;
+};
+
+struct RecBufs {                     // FP64 recovery buffers
+    Block vec;                       // m / n sized vectors
+    Block kb;                        // k-sized (capacity kcap)
+    int kcap = -1;
+    double *s = nullptr, *aZ = nullptr, *d = nullptr, *arow = nullptr;
+    int *isbasic = nullptr, *inR = nullptr;
+    DevState* rst = nullptr;
+    RecCheck* chk = nullptr;
+    RecChoice* choice = nullptr;
+    int* singular = nullptr;
+    double *M = nullptr, *inv = nullptr, *xS = nullptr, *yR = nullptr, *bR = nullptr, *cS = nullptr;
+    double *rp = nullptr, *rd = nullptr, *aS = nullptr, *rho = nullptr, *venter = nullptr;
+    int *pivrow = nullptr, *used = nullptr, *S = nullptr, *Rr = nullptr;
+};
+
 struct lp_handle {
-    int m = 0, n = 0, W = 0, ld = 0;
+    int m = 0, n = 0, W = 0;
     int device = 0;
     cudaStream_t stream = nullptr;   // handle stream
     bool own_stream = false;
@@ -68,21 +105,19 @@ struct lp_handle {
     void* alloc_ctx = nullptr;
     const double *A = nullptr, *b = nullptr, *c = nullptr;
     Block inputs;                    // owned copy of (A, b, c) for lp_create
-    Block work;                      // tableau + work buffers
-    double* T = nullptr;
-    double* F = nullptr;
-    double* R = nullptr;
-    int* act = nullptr;
-    ArgPart* cpart = nullptr;
-    RatPart* rpart = nullptr;
+    Block common;                    // state, basis, read-out
     DevState* st = nullptr;
     int* basis = nullptr;
     double* sol = nullptr;           // x (n), y (m), obj (1)
+    Work work;
+    RecBufs rec;
     Block logs;
     long long log_cap = 0;
     int max_grid = 0;                // rpart capacity
     bool solved = false;
     int last_status = LP_ERR_STATE;
+    bool sol_ready = false;          // sol already holds the read-out (float path)
+    std::vector<int> final_basis;    // float path: basic variables after the recovery
     long long iters = 0;
     lp_stats stats{};
 };
@@ -108,263 +143,20 @@ static void dev_free(lp_handle* h, Block& blk) {
     blk.bytes = 0;
 }
 
-static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
-
-// ---------------------------------------------------------------- kernels
-__global__ void k_reset_state(DevState* st) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) {
-        st->status = kRunning;
-        st->q = -1;
-        st->p = -1;
-        st->bland = 0;
-        st->degen_run = 0;
-        st->bad = 0;
-        st->iters = 0;
-        st->active_sectors = 0;
-        st->nact = 0;
-        st->next_slot = 0;
-        st->theta = 0.0;
-        st->bar_count = 0;
-        st->bar_gen = 0;
-        for (int k = 0; k < 6; ++k) st->phase_ns[k] = 0;
-    }
+static bool dev_alloc_block(lp_handle* h, Block& blk, size_t bytes) {
+    blk.ptr = dev_alloc(h, bytes);
+    blk.bytes = blk.ptr ? bytes : 0;
+    return blk.ptr != nullptr;
 }
 
-// Input check for device-created LPs: every entry finite, b >= 0.
-__global__ void k_validate(int m, int n, const double* __restrict__ A, const double* __restrict__ b,
-                           const double* __restrict__ c, DevState* st) {
-    const size_t mn = (size_t)m * (size_t)n;
-    const size_t total = mn + (size_t)m + (size_t)n;
-    int bad = 0;
-    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
-         k += (size_t)gridDim.x * blockDim.x) {
-        double v;
-        if (k < mn) {
-            v = A[k];
-            bad |= !isfinite(v);
-        } else if (k < mn + m) {
-            v = b[k - mn];
-            bad |= !isfinite(v) || !(v >= 0.0);
-        } else {
-            v = c[k - mn - m];
-            bad |= !isfinite(v);
-        }
-    }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->bad, 1);
-}
-
-// Initialization Step (Section III, Table I): row 0 = [-c, 0 | 0],
-// row i = [A_i, e_i | b_i]; padding columns [W, ld) are zero.  One thread per
-// 32-byte group of 4 columns.  Also seeds the slack basis.
-__global__ void k_build(int m, int n, int W, int ld, const double* __restrict__ A,
-                        const double* __restrict__ b, const double* __restrict__ c,
-                        double* __restrict__ T, int* __restrict__ basis) {
-    const size_t groups_per_row = (size_t)ld / 4;
-    const size_t total = (size_t)(m + 1) * groups_per_row;
-    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
-         g += (size_t)gridDim.x * blockDim.x) {
-        const int i = (int)(g / groups_per_row);
-        const int j0 = (int)(g - (size_t)i * groups_per_row) * 4;
-        double out[4];
-#pragma unroll
-        for (int e = 0; e < 4; ++e) {
-            const int j = j0 + e;
-            double v = 0.0;
-            if (i == 0) {
-                if (j < n) v = -c[j];
-            } else {
-                if (j < n)
-                    v = A[(size_t)(i - 1) * (size_t)n + j];
-                else if (j == n + i - 1)
-                    v = 1.0;
-                else if (j == W - 1)
-                    v = b[i - 1];
-            }
-            out[e] = v;
-        }
-        st_sector(T + (size_t)i * (size_t)ld + j0, make_sec4(out[0], out[1], out[2], out[3]));
-    }
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)m;
-         i += (size_t)gridDim.x * blockDim.x)
-        basis[i] = n + (int)i;
-}
-
-// Pivot bookkeeping shared by both paths (one thread): basis update, pivot log.
-__device__ __forceinline__ void record_pivot(const Params& P, long long it, int q, int p) {
-    P.basis[p - 1] = q;
-    if (it < P.log_cap) {
-        P.qlog[it] = q;
-        P.plog[it] = p;
-    }
-}
-
-// Cycling guard: a pivot with minimum ratio <= 0 does not move the objective;
-// k_cyc of them in a row switch to Bland's rule until a positive-ratio pivot.
-__device__ __forceinline__ void degeneracy_step(const Params& P, double theta, int& bland, int& degen) {
-    if (P.rule != 0) return;
-    if (theta <= 0.0) {
-        ++degen;
-        if (P.k_cyc > 0 && degen >= P.k_cyc) bland = 1;
-    } else {
-        degen = 0;
-        bland = 0;
-    }
-}
-
-__device__ __forceinline__ void finish(const Params& P, int status, long long it, int bland, int degen,
-                                       const long long* ph) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        atomicCAS(&P.st->status, kRunning, status);
-        P.st->iters = it;
-        P.st->bland = bland;
-        P.st->degen_run = degen;
-        for (int k = 0; k < 6; ++k) P.st->phase_ns[k] = ph[k];
-    }
-}
-
-// Phase timer of block 0, thread 0 (other threads keep it at zero).
-struct PhaseClock {
-    long long acc[6] = {0, 0, 0, 0, 0, 0};
-    long long t = 0;
-    bool on = false;
-    __device__ void start() {
-        on = blockIdx.x == 0 && threadIdx.x == 0;
-        if (on) t = global_ns();
-    }
-    __device__ void lap(int k) {   // closes interval k, opens the next one
-        if (on) {
-            const long long now = global_ns();
-            acc[k] += now - t;
-            t = now;
-        }
-    }
-};
-
-// Steps 1-3 iterated inside one cooperative launch; three grid barriers per
-// pivot (after P2, after P3, after P4).  Every block takes the same decisions
-// from the same reduced values, so all leave the loop together.
-template <int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) k_pivot_persistent(Params P) {
-    __shared__ BlockScratch s;
-    PhaseClock clk;
-    phase_init_argmin(P);
-    if (!grid_barrier(P.st, P.timeout_ns, s)) return;
-    long long it = 0;
-    int bland = P.rule == 1 ? 1 : 0;
-    int degen = 0;
-    clk.start();
-    for (;;) {
-        const ArgPart e = phase_entering(P, s);           // Step 1
-        const int q = bland ? e.jfirst : e.j;
-        if (q == INT_MAX) { finish(P, kOptimal, it, bland, degen, clk.acc); return; }
-        if (it >= P.max_iters) { finish(P, kIterLimit, it, bland, degen, clk.acc); return; }
-        phase_ratio(P, q, bland, s);                      // Step 2 (block partials)
-        clk.lap(0);
-        if (!grid_barrier(P.st, P.timeout_ns, s)) return;
-        clk.lap(3);
-        const RatPart l = phase_leaving(P, s);            // Step 2 (global)
-        if (l.i == INT_MAX) { finish(P, kUnbounded, it, bland, degen, clk.acc); return; }
-        const double piv = __ldcg(P.F + l.i);
-        if (!isfinite(piv) || !isfinite(l.r)) { finish(P, kNumeric, it, bland, degen, clk.acc); return; }
-        phase_stage_row(P, l.i, piv, s);                  // Step 3 (pivot row)
-        if (blockIdx.x == 0 && threadIdx.x == 0) record_pivot(P, it, q, l.i);
-        clk.lap(1);
-        if (!grid_barrier(P.st, P.timeout_ns, s)) return;
-        clk.lap(4);
-        phase_update(P, l.i);                             // Step 3 (rank-1 update)
-        ++it;
-        degeneracy_step(P, l.r, bland, degen);
-        clk.lap(2);
-        if (!grid_barrier(P.st, P.timeout_ns, s)) return;
-        clk.lap(5);
-    }
-}
-
-// ---- one launch per phase (same device functions; state in DevState)
-__global__ void k_ml_init(Params P) {
-    if (blockIdx.x == 0 && threadIdx.x == 0) P.st->bland = P.rule == 1 ? 1 : 0;
-    phase_init_argmin(P);
-}
-
-template <int NT>
-__global__ void __launch_bounds__(NT) k_ml_select(Params P) {
-    __shared__ BlockScratch s;
-    if (P.st->status != kRunning) return;
-    const int bland = P.st->bland;
-    const long long it = P.st->iters;
-    const ArgPart e = phase_entering(P, s);
-    const int q = bland ? e.jfirst : e.j;
-    if (q == INT_MAX || it >= P.max_iters) {
-        if (blockIdx.x == 0 && threadIdx.x == 0)
-            atomicCAS(&P.st->status, kRunning, q == INT_MAX ? kOptimal : kIterLimit);
-        return;
-    }
-    phase_ratio(P, q, bland, s);
-    if (blockIdx.x == 0 && threadIdx.x == 0) P.st->q = q;
-}
-
-template <int NT>
-__global__ void __launch_bounds__(NT) k_ml_stage(Params P) {
-    __shared__ BlockScratch s;
-    if (P.st->status != kRunning) return;
-    const RatPart l = phase_leaving(P, s);
-    if (l.i == INT_MAX) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&P.st->status, kRunning, kUnbounded);
-        return;
-    }
-    const double piv = __ldcg(P.F + l.i);
-    if (!isfinite(piv) || !isfinite(l.r)) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&P.st->status, kRunning, kNumeric);
-        return;
-    }
-    phase_stage_row(P, l.i, piv, s);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        record_pivot(P, P.st->iters, P.st->q, l.i);
-        P.st->p = l.i;
-        P.st->theta = l.r;
-    }
-}
-
-template <int NT>
-__global__ void __launch_bounds__(NT, 512 / NT) k_ml_update(Params P) {
-    if (P.st->status != kRunning) return;
-    const int p = P.st->p;
-    phase_update(P, p);
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-        int bland = P.st->bland, degen = P.st->degen_run;
-        degeneracy_step(P, P.st->theta, bland, degen);
-        P.st->bland = bland;
-        P.st->degen_run = degen;
-        P.st->iters += 1;
-    }
-}
-
-// Solution read-out (Table I layout): y_i = T[0][n+i], obj = T[0][W-1],
-// x zeroed, then x[basis[i]] = T[i+1][W-1] for structural basics.
-__global__ void k_extract_dense(int m, int n, int W, int ld, const double* __restrict__ T,
-                                double* __restrict__ sol) {
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n + m + 1; k += gridDim.x * blockDim.x) {
-        if (k < n)
-            sol[k] = 0.0;
-        else if (k < n + m)
-            sol[k] = T[n + (k - n)];
-        else
-            sol[k] = T[W - 1];
-    }
-}
-
-__global__ void k_extract_x(int m, int n, int W, int ld, const double* __restrict__ T,
-                            const int* __restrict__ basis, double* __restrict__ sol) {
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
-        const int v = basis[i];
-        if (v < n) sol[v] = T[(size_t)(i + 1) * (size_t)ld + (W - 1)];
-    }
+static int grid_for(long long work, int nt, int cap) {
+    return (int)std::max<long long>(1, std::min<long long>((work + nt - 1) / nt, cap));
 }
 
 // ------------------------------------------------------------------- API
 // (C linkage comes from the declarations in tabsimplex.h)
 
-const char* lp_version(void) { return "tabsimplex 0.1 (sm_103a)"; }
+const char* lp_version(void) { return "tabsimplex 0.2 (sm_103a)"; }
 
 const char* lp_last_error(void) { return g_last_error.c_str(); }
 
@@ -395,6 +187,11 @@ void lp_options_init(lp_options* o) {
     o->blocks = 0;
     o->log_capacity = 0;
     o->stream = nullptr;
+    o->precision = LP_PREC_FP64;
+    o->eps_d_fp32 = 1e-5;
+    o->eps_p_fp32 = 1e-6;
+    o->recover_tol = 1e-9;
+    o->cleanup_max = 1000;
 }
 
 static void destroy_impl(lp_handle* h) {
@@ -402,7 +199,10 @@ static void destroy_impl(lp_handle* h) {
     cudaSetDevice(h->device);
     if (h->stream) cudaStreamSynchronize(h->stream);
     dev_free(h, h->logs);
-    dev_free(h, h->work);
+    dev_free(h, h->work.blk);
+    dev_free(h, h->rec.vec);
+    dev_free(h, h->rec.kb);
+    dev_free(h, h->common);
     dev_free(h, h->inputs);
     if (h->stream) cudaStreamSynchronize(h->stream);
     for (auto& e : h->ev)
@@ -414,7 +214,7 @@ static void destroy_impl(lp_handle* h) {
 
 void lp_destroy(lp_t h) { destroy_impl(h); }
 
-// Common part of the two create calls: sizes, stream, events, work buffers.
+// Common part of the two create calls: sizes, stream, events, state block.
 static lp_handle* create_common(int m, int n, cudaStream_t stream, bool own_stream) {
     if (m <= 0 || n <= 0) {
         set_error("lp_create: need m > 0 and n > 0 (got m=%d, n=%d)", m, n);
@@ -428,7 +228,6 @@ static lp_handle* create_common(int m, int n, cudaStream_t stream, bool own_stre
     h->m = m;
     h->n = n;
     h->W = n + m + 1;
-    h->ld = (int)align_up((size_t)h->W, 16);
     cudaGetDevice(&h->device);
     {
         std::lock_guard<std::mutex> lk(g_alloc_mu);
@@ -456,35 +255,19 @@ static lp_handle* create_common(int m, int n, cudaStream_t stream, bool own_stre
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
     h->max_grid = std::max(1, nsm) * 32;   // rpart capacity (>= any co-resident grid)
-    const int nstrips = (h->ld + kStripCols - 1) / kStripCols;
-    // one allocation: T | F | R | act | cpart | rpart | st | basis | sol
-    const size_t sz_T = (size_t)(m + 1) * (size_t)h->ld * sizeof(double);
-    const size_t off_F = align_up(sz_T, 256);
-    const size_t off_R = align_up(off_F + (size_t)(m + 1) * sizeof(double), 256);
-    const size_t off_act = align_up(off_R + (size_t)h->ld * sizeof(double), 256);
-    const size_t off_cp = align_up(off_act + (size_t)(h->ld / 4) * sizeof(int), 256);
-    const size_t off_rp = align_up(off_cp + (size_t)nstrips * sizeof(ArgPart), 256);
-    const size_t off_st = align_up(off_rp + (size_t)h->max_grid * sizeof(RatPart), 256);
-    const size_t off_bs = align_up(off_st + sizeof(DevState), 256);
-    const size_t off_sol = align_up(off_bs + (size_t)m * sizeof(int), 256);
-    const size_t total = align_up(off_sol + (size_t)(n + m + 1) * sizeof(double), 256);
-    h->work.ptr = dev_alloc(h, total);
-    if (!h->work.ptr) {
-        set_error("lp_create: device allocation of %zu bytes failed", total);
+    Carve cv;
+    const size_t o_st = cv.take(sizeof(DevState));
+    const size_t o_bs = cv.take((size_t)m * sizeof(int));
+    const size_t o_sol = cv.take((size_t)(n + m + 1) * sizeof(double));
+    if (!dev_alloc_block(h, h->common, align_up(cv.off, 256))) {
+        set_error("lp_create: device allocation of %zu bytes failed", cv.off);
         destroy_impl(h);
         return nullptr;
     }
-    h->work.bytes = total;
-    char* base = (char*)h->work.ptr;
-    h->T = (double*)base;
-    h->F = (double*)(base + off_F);
-    h->R = (double*)(base + off_R);
-    h->act = (int*)(base + off_act);
-    h->cpart = (ArgPart*)(base + off_cp);
-    h->rpart = (RatPart*)(base + off_rp);
-    h->st = (DevState*)(base + off_st);
-    h->basis = (int*)(base + off_bs);
-    h->sol = (double*)(base + off_sol);
+    char* base = (char*)h->common.ptr;
+    h->st = (DevState*)(base + o_st);
+    h->basis = (int*)(base + o_bs);
+    h->sol = (double*)(base + o_sol);
     return h;
 }
 
@@ -515,20 +298,19 @@ lp_t lp_create(int m, int n, const double* A, const double* b, const double* c) 
     lp_handle* h = create_common(m, n, nullptr, true);
     if (!h) return nullptr;
     const size_t mn = (size_t)m * (size_t)n;
-    const size_t off_b = align_up(mn * sizeof(double), 256);
-    const size_t off_c = align_up(off_b + (size_t)m * sizeof(double), 256);
-    const size_t total = align_up(off_c + (size_t)n * sizeof(double), 256);
-    h->inputs.ptr = dev_alloc(h, total);
-    if (!h->inputs.ptr) {
-        set_error("lp_create: device allocation of %zu input bytes failed", total);
+    Carve cv;
+    const size_t o_A = cv.take(mn * sizeof(double));
+    const size_t o_b = cv.take((size_t)m * sizeof(double));
+    const size_t o_c = cv.take((size_t)n * sizeof(double));
+    if (!dev_alloc_block(h, h->inputs, align_up(cv.off, 256))) {
+        set_error("lp_create: device allocation of %zu input bytes failed", cv.off);
         destroy_impl(h);
         return nullptr;
     }
-    h->inputs.bytes = total;
     char* base = (char*)h->inputs.ptr;
-    h->A = (const double*)base;
-    h->b = (const double*)(base + off_b);
-    h->c = (const double*)(base + off_c);
+    h->A = (const double*)(base + o_A);
+    h->b = (const double*)(base + o_b);
+    h->c = (const double*)(base + o_c);
     if (cudaMemcpyAsync((void*)h->A, A, mn * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaMemcpyAsync((void*)h->b, b, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaMemcpyAsync((void*)h->c, c, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
@@ -562,35 +344,69 @@ lp_t lp_create_device(int m, int n, const double* dA, const double* db, const do
     return h;
 }
 
-template <int NT>
-static cudaError_t launch_persistent(const Params& P, int grid, cudaStream_t s) {
-    void* args[] = {(void*)&P};
-    return cudaLaunchCooperativeKernel((const void*)k_pivot_persistent<NT>, grid, NT, args, 0, s);
+// Leading dimension of a tableau of `elem`-byte entries: 128-byte rows.
+static int tableau_ld(int W, int elem) { return (int)align_up((size_t)W, 128 / elem); }
+
+// (Re)allocates the pivot buffers for a tableau of `elem`-byte entries.
+static lp_status ensure_work(lp_handle* h, int elem) {
+    if (h->work.elem == elem && h->work.blk.ptr) return LP_OPTIMAL;
+    dev_free(h, h->work.blk);
+    h->work = Work{};
+    const int ld = tableau_ld(h->W, elem);
+    const int E = 32 / elem;
+    const int nstrips = (ld + 32 * E - 1) / (32 * E);
+    Carve cv;
+    const size_t o_T = cv.take((size_t)(h->m + 1) * (size_t)ld * elem);
+    const size_t o_F = cv.take((size_t)(h->m + 1) * elem);
+    const size_t o_R = cv.take((size_t)ld * elem);
+    const size_t o_act = cv.take((size_t)(ld / E) * sizeof(int));
+    const size_t o_cp = cv.take((size_t)nstrips * sizeof(ArgPart));
+    const size_t o_rp = cv.take((size_t)h->max_grid * sizeof(RatPart));
+    if (!dev_alloc_block(h, h->work.blk, align_up(cv.off, 256))) {
+        set_error("lp_solve: device allocation of %zu bytes for the tableau failed", cv.off);
+        return LP_ERR_NOMEM;
+    }
+    char* base = (char*)h->work.blk.ptr;
+    h->work.elem = elem;
+    h->work.ld = ld;
+    h->work.T = base + o_T;
+    h->work.F = base + o_F;
+    h->work.R = base + o_R;
+    h->work.act = (int*)(base + o_act);
+    h->work.cpart = (ArgPart*)(base + o_cp);
+    h->work.rpart = (RatPart*)(base + o_rp);
+    return LP_OPTIMAL;
 }
 
-template <int NT>
+template <int NT, typename V>
+static cudaError_t launch_persistent(const Params<V>& P, int grid, cudaStream_t s) {
+    void* args[] = {(void*)&P};
+    return cudaLaunchCooperativeKernel((const void*)k_pivot_persistent<NT, V>, grid, NT, args, 0, s);
+}
+
+template <int NT, typename V>
 static int max_coresident(int device) {
     int nsm = 0, per = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pivot_persistent<NT>, NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pivot_persistent<NT, V>, NT, 0);
     return nsm * per;
 }
 
-template <int NT>
-static lp_status run_multilaunch(lp_handle* h, const Params& P, int grid, cudaStream_t s, long long& launches) {
-    k_ml_init<<<grid, NT, 0, s>>>(P);
+template <int NT, typename V>
+static lp_status run_multilaunch(const Params<V>& P, int grid, cudaStream_t s, long long& launches) {
+    k_ml_init<V><<<grid, NT, 0, s>>>(P);
     ++launches;
     int status = kRunning;
     int batch = 4;
     for (;;) {
         for (int k = 0; k < batch; ++k) {
-            k_ml_select<NT><<<grid, NT, 0, s>>>(P);
-            k_ml_stage<NT><<<grid, NT, 0, s>>>(P);
-            k_ml_update<NT><<<grid, NT, 0, s>>>(P);
+            k_ml_select<NT, V><<<grid, NT, 0, s>>>(P);
+            k_ml_stage<NT, V><<<grid, NT, 0, s>>>(P);
+            k_ml_update<NT, V><<<grid, NT, 0, s>>>(P);
             launches += 3;
         }
         CUDA_TRY(cudaGetLastError(), LP_ERR_CUDA);
-        CUDA_TRY(cudaMemcpyAsync(&status, &h->st->status, sizeof(int), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+        CUDA_TRY(cudaMemcpyAsync(&status, &P.st->status, sizeof(int), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
         CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
         if (status != kRunning) break;
         batch = std::min(batch * 2, 64);
@@ -598,58 +414,63 @@ static lp_status run_multilaunch(lp_handle* h, const Params& P, int grid, cudaSt
     return (lp_status)status;
 }
 
-template <int NT>
-static lp_status solve_nt(lp_handle* h, const lp_options& o, cudaStream_t s) {
-    const int m = h->m, n = h->n;
-    Params P{};
-    P.T = h->T;
-    P.ld = h->ld;
+// Pivot-kernel parameters over a tableau of V with the given buffers.
+template <typename V>
+static Params<V> make_params(int m, int n, int ld, V* T, V* F, V* R, int* act, ArgPart* cpart, RatPart* rpart,
+                             DevState* st, int* basis, const lp_options& o, double eps_d, double eps_p) {
+    constexpr int E = Lanes<V>::E;
+    Params<V> P{};
+    P.T = T;
+    P.ld = ld;
     P.m = m;
     P.n = n;
-    P.W = h->W;
-    P.basis = h->basis;
-    P.F = h->F;
-    P.R = h->R;
-    P.act = h->act;
-    P.cpart = h->cpart;
-    P.rpart = h->rpart;
-    P.st = h->st;
-    P.eps_d = o.eps_d;
-    P.eps_p = o.eps_p;
+    P.W = n + m + 1;
+    P.basis = basis;
+    P.F = F;
+    P.R = R;
+    P.act = act;
+    P.cpart = cpart;
+    P.rpart = rpart;
+    P.st = st;
+    P.eps_d = eps_d;
+    P.eps_p = eps_p;
     P.max_iters = o.max_iters < 0 ? 50LL * ((long long)m + n) : o.max_iters;
     P.k_cyc = o.k_cyc;
     P.rule = o.rule;
     P.timeout_ns = std::max(0LL, o.barrier_timeout_ns);
-    P.nstrips = (h->ld + kStripCols - 1) / kStripCols;
-    P.nrc = (m + 1 + kUnitRows - 1) / kUnitRows;
-    P.nunits = (long long)P.nstrips * P.nrc;
+    P.nstrips = (ld + 32 * E - 1) / (32 * E);
     P.skip_zero = o.skip_zero_columns ? 1 : 0;
+    return P;
+}
 
-    // pivot log buffers
-    if (o.log_capacity > 0 && o.log_capacity != h->log_cap) {
-        dev_free(h, h->logs);
-        h->log_cap = 0;
-        const size_t bytes = (size_t)o.log_capacity * 2 * sizeof(int);
-        h->logs.ptr = dev_alloc(h, bytes);
-        if (!h->logs.ptr) {
-            set_error("lp_solve: allocation of the pivot log failed");
-            return LP_ERR_NOMEM;
-        }
-        h->logs.bytes = bytes;
-        h->log_cap = o.log_capacity;
-    }
+// Grid of the pivot kernels: enough warps for the update slots, at most the
+// co-resident blocks.
+template <int NT, typename V>
+static int pivot_grid(int device, int m, int ld, int max_grid, int user_blocks, int& coresident) {
+    constexpr int E = Lanes<V>::E;
+    const long long slots = (long long)((ld / E + 31) / 32) * (((long long)m + kRowsInFlight - 1) / kRowsInFlight);
+    const long long want = (slots + NT / 32 - 1) / (NT / 32);
+    coresident = max_coresident<NT, V>(device);
+    int grid = (int)std::min<long long>(std::max<long long>(1, want), std::max(1, coresident));
+    grid = std::min(grid, max_grid);
+    if (user_blocks > 0) grid = std::min(grid, user_blocks);
+    return grid;
+}
+
+// Runs the pivot phase (build + Steps 1-3) on the handle's tableau of V.
+template <int NT, typename V>
+static lp_status pivot_phase(lp_handle* h, const lp_options& o, cudaStream_t s, double eps_d, double eps_p,
+                             DevState& hs, long long& launches, int& path_used, int& grid_used) {
+    const int m = h->m, n = h->n;
+    const int ld = h->work.ld;
+    Params<V> P = make_params<V>(m, n, ld, (V*)h->work.T, (V*)h->work.F, (V*)h->work.R, h->work.act,
+                                 h->work.cpart, h->work.rpart, h->st, h->basis, o, eps_d, eps_p);
     P.log_cap = o.log_capacity > 0 ? h->log_cap : 0;
     P.qlog = P.log_cap ? (int*)h->logs.ptr : nullptr;
     P.plog = P.log_cap ? (int*)h->logs.ptr + P.log_cap : nullptr;
 
-    // grid: enough warps for the units, at most the co-resident blocks
-    const int warps = NT / 32;
-    const long long want = (P.nunits + warps - 1) / warps;
-    int coresident = max_coresident<NT>(h->device);
-    int grid = (int)std::min<long long>(std::max<long long>(1, want), std::max(1, coresident));
-    grid = std::min(grid, h->max_grid);
-    if (o.blocks > 0) grid = std::min(grid, o.blocks);
-
+    int coresident = 0;
+    const int grid = pivot_grid<NT, V>(h->device, m, ld, h->max_grid, o.blocks, coresident);
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
     int path = o.path;
@@ -663,17 +484,17 @@ static lp_status solve_nt(lp_handle* h, const lp_options& o, cudaStream_t s) {
     cudaEventRecord(h->ev[0], s);
     k_reset_state<<<1, 32, 0, s>>>(h->st);
     {
-        const size_t groups = (size_t)(m + 1) * (size_t)(h->ld / 4);
+        constexpr int E = Lanes<V>::E;
+        const size_t groups = (size_t)(m + 1) * (size_t)(ld / E);
         int g = (int)std::min<size_t>((groups + 255) / 256, 152 * 16);
-        k_build<<<g, 256, 0, s>>>(m, n, h->W, h->ld, h->A, h->b, h->c, h->T, h->basis);
+        k_build<V><<<g, 256, 0, s>>>(m, n, h->W, ld, h->A, h->b, h->c, (V*)h->work.T, h->basis);
     }
     CUDA_TRY(cudaGetLastError(), LP_ERR_CUDA);
     cudaEventRecord(h->ev[1], s);
+    launches += 2;
 
-    long long launches = 2;
-    lp_status st;
     if (path == LP_PATH_PERSISTENT) {
-        cudaError_t e = launch_persistent<NT>(P, grid, s);
+        cudaError_t e = launch_persistent<NT, V>(P, grid, s);
         if (e != cudaSuccess) {
             if (o.path == LP_PATH_AUTO) {   // co-residency refused: fall back
                 cudaGetLastError();
@@ -687,48 +508,336 @@ static lp_status solve_nt(lp_handle* h, const lp_options& o, cudaStream_t s) {
         }
     }
     if (path == LP_PATH_MULTILAUNCH) {
-        if (run_multilaunch<NT>(h, P, grid, s, launches) == LP_ERR_CUDA) return LP_ERR_CUDA;
+        if (run_multilaunch<NT, V>(P, grid, s, launches) == LP_ERR_CUDA) return LP_ERR_CUDA;
     }
     cudaEventRecord(h->ev[2], s);
-    DevState hs{};
     CUDA_TRY(cudaMemcpyAsync(&hs, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
     CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
-    cudaEventRecord(h->ready, s);
+    path_used = path;
+    grid_used = grid;
+    if (hs.status == kRunning) {
+        set_error("lp_solve: kernel ended without a status");
+        return LP_ERR_CUDA;
+    }
+    if (hs.status == kTimeout) set_error("lp_solve: a grid barrier wait exceeded %lld ns", (long long)P.timeout_ns);
+    return (lp_status)hs.status;
+}
+
+// ------------------------------------------------------------ FP64 recovery
+static lp_status ensure_recovery(lp_handle* h, int k) {
+    RecBufs& r = h->rec;
+    const int m = h->m, n = h->n;
+    if (!r.vec.ptr) {
+        Carve cv;
+        const size_t o_s = cv.take((size_t)m * 8), o_aZ = cv.take((size_t)m * 8);
+        const size_t o_d = cv.take((size_t)n * 8), o_ar = cv.take((size_t)n * 8);
+        const size_t o_ib = cv.take((size_t)(n + m) * 4), o_ir = cv.take((size_t)m * 4);
+        const size_t o_rst = cv.take(sizeof(DevState)), o_chk = cv.take(sizeof(RecCheck));
+        const size_t o_ch = cv.take(sizeof(RecChoice)), o_sg = cv.take(sizeof(int));
+        if (!dev_alloc_block(h, r.vec, align_up(cv.off, 256))) {
+            set_error("lp_solve: allocation of the recovery vectors failed");
+            return LP_ERR_NOMEM;
+        }
+        char* b = (char*)r.vec.ptr;
+        r.s = (double*)(b + o_s);
+        r.aZ = (double*)(b + o_aZ);
+        r.d = (double*)(b + o_d);
+        r.arow = (double*)(b + o_ar);
+        r.isbasic = (int*)(b + o_ib);
+        r.inR = (int*)(b + o_ir);
+        r.rst = (DevState*)(b + o_rst);
+        r.chk = (RecCheck*)(b + o_chk);
+        r.choice = (RecChoice*)(b + o_ch);
+        r.singular = (int*)(b + o_sg);
+    }
+    if (k > r.kcap) {
+        dev_free(h, r.kb);
+        const int kc = std::max(std::max(k, 2 * std::max(r.kcap, 0)), 16);
+        const size_t K = (size_t)kc;
+        Carve cv;
+        const size_t o_M = cv.take(K * 2 * K * 8), o_inv = cv.take(K * K * 8);
+        size_t o_v[9];
+        for (auto& o : o_v) o = cv.take(K * 8);
+        size_t o_i[4];
+        for (auto& o : o_i) o = cv.take(K * 4);
+        if (!dev_alloc_block(h, r.kb, align_up(cv.off, 256))) {
+            set_error("lp_solve: allocation of the recovery matrices (k = %d) failed", k);
+            r.kcap = -1;
+            return LP_ERR_NOMEM;
+        }
+        char* b = (char*)r.kb.ptr;
+        r.M = (double*)(b + o_M);
+        r.inv = (double*)(b + o_inv);
+        double** vs[9] = {&r.xS, &r.yR, &r.bR, &r.cS, &r.rp, &r.rd, &r.aS, &r.rho, &r.venter};
+        for (int t = 0; t < 9; ++t) *vs[t] = (double*)(b + o_v[t]);
+        int** is[4] = {&r.pivrow, &r.used, &r.S, &r.Rr};
+        for (int t = 0; t < 4; ++t) *is[t] = (int*)(b + o_i[t]);
+        r.kcap = kc;
+    }
+    return LP_OPTIMAL;
+}
+
+// Refactorises A_RS for the sets (S, R), solves x_S and y_R (one refinement
+// step), computes the slacks and the objective-row entries, and runs the
+// checks.  Fills `chk`.  Returns LP_ERR_NUMERIC if A_RS is singular.
+static lp_status recover_factor(lp_handle* h, const lp_options& o, cudaStream_t s, const std::vector<int>& S,
+                                const std::vector<int>& R, RecCheck& chk, long long& launches) {
+    RecBufs& r = h->rec;
+    const int m = h->m, n = h->n, k = (int)S.size();
+    lp_status st = ensure_recovery(h, k);
+    if (st != LP_OPTIMAL) return st;
+    if (k > 0) {
+        CUDA_TRY(cudaMemcpyAsync(r.S, S.data(), (size_t)k * 4, cudaMemcpyHostToDevice, s), LP_ERR_CUDA);
+        CUDA_TRY(cudaMemcpyAsync(r.Rr, R.data(), (size_t)k * 4, cudaMemcpyHostToDevice, s), LP_ERR_CUDA);
+    }
+    k_rec_flags<<<grid_for(n + m, 256, 4096), 256, 0, s>>>(m, n, r.S, r.Rr, k, r.isbasic, r.inR);
+    k_rec_flags2<<<grid_for(k, 256, 4096), 256, 0, s>>>(m, n, r.S, r.Rr, k, r.isbasic, r.inR);
+    launches += 2;
+    int singular = 0;
+    if (k > 0) {
+        const size_t kk = (size_t)k;
+        k_rec_gather<<<grid_for((long long)(2 * kk * kk), 256, 152 * 16), 256, 0, s>>>(n, h->A, r.S, r.Rr, k, r.M);
+        CUDA_TRY(cudaMemsetAsync(r.used, 0, kk * 4, s), LP_ERR_CUDA);
+        CUDA_TRY(cudaMemsetAsync(r.singular, 0, 4, s), LP_ERR_CUDA);
+        k_reset_state<<<1, 32, 0, s>>>(r.rst);
+        int nsm = 0, per = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rec_gauss_jordan<256>, 256, 0);
+        const int g = std::max(1, std::min(nsm * std::max(per, 1), grid_for((long long)(2 * kk * kk), 256, 1 << 20)));
+        int* sg = r.singular;
+        int* pv = r.pivrow;
+        int* us = r.used;
+        double* Mx = r.M;
+        DevState* rs = r.rst;
+        long long to = std::max(0LL, o.barrier_timeout_ns);
+        int kv = k;
+        void* args[] = {&Mx, &kv, &pv, &us, &sg, &rs, &to};
+        CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_rec_gauss_jordan<256>, g, 256, args, 0, s), LP_ERR_CUDA);
+        k_rec_finish<<<grid_for((long long)(kk * kk), 256, 152 * 16), 256, 0, s>>>(r.M, k, r.pivrow, r.inv);
+        k_rec_gather_rhs<<<grid_for(k, 256, 1024), 256, 0, s>>>(h->b, h->c, r.S, r.Rr, k, r.bR, r.cS);
+        const int gw = grid_for(32LL * k, 256, 4096);
+        k_rec_matvec<<<gw, 256, 0, s>>>(r.inv, k, r.bR, 0, nullptr, r.xS);
+        k_rec_matvec<<<grid_for(k, 256, 1024), 256, 0, s>>>(r.inv, k, r.cS, 1, nullptr, r.yR);
+        // one step of iterative refinement in FP64
+        k_rec_residual<<<grid_for(64LL * k, 256, 4096), 256, 0, s>>>(n, h->A, r.S, r.Rr, k, r.bR, r.cS, r.xS, r.yR,
+                                                                       r.rp, r.rd);
+        k_rec_matvec<<<gw, 256, 0, s>>>(r.inv, k, r.rp, 0, r.xS, r.xS);
+        k_rec_matvec<<<grid_for(k, 256, 1024), 256, 0, s>>>(r.inv, k, r.rd, 1, r.yR, r.yR);
+        k_rec_residual<<<grid_for(64LL * k, 256, 4096), 256, 0, s>>>(n, h->A, r.S, r.Rr, k, r.bR, r.cS, r.xS, r.yR,
+                                                                       r.rp, r.rd);
+        launches += 11;
+    }
+    // slacks s = b - A_:S x_S (every row), objective row d = A_R:^T y_R - c
+    k_rec_rows_dot<<<grid_for(32LL * m, 256, 8192), 256, 0, s>>>(m, n, h->A, r.S, k, h->b, -1, r.xS, r.s);
+    k_rec_cols_dot<<<grid_for(n, 256, 8192), 256, 0, s>>>(n, h->A, r.Rr, k, r.yR, -1, h->c, r.d);
+    k_rec_check<256><<<1, 256, 0, s>>>(m, n, r.S, r.Rr, k, r.xS, r.s, r.d, r.yR, r.isbasic, r.inR, h->b, h->c,
+                                       r.rp, r.rd, r.chk);
+    launches += 3;
+    CUDA_TRY(cudaGetLastError(), LP_ERR_CUDA);
+    CUDA_TRY(cudaMemcpyAsync(&chk, r.chk, sizeof(RecCheck), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+    CUDA_TRY(cudaMemcpyAsync(&singular, r.singular, sizeof(int), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+    int rstatus = kRunning;
+    CUDA_TRY(cudaMemcpyAsync(&rstatus, &r.rst->status, sizeof(int), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+    CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
+    if (k > 0 && rstatus == kTimeout) {
+        set_error("lp_solve: a grid barrier wait of the FP64 refactorisation exceeded its limit");
+        return LP_ERR_TIMEOUT;
+    }
+    if (k > 0 && singular) {
+        set_error("lp_solve: the final basis is singular in FP64 (k = %d)", k);
+        return LP_ERR_NUMERIC;
+    }
+    return LP_OPTIMAL;
+}
+
+// FP64 recovery of the float phase's final basis: refactorise, check, and
+// clean up with revised-form pivots until the checks pass.  Writes the read-out
+// into h->sol and the final basic set into h->final_basis.
+static lp_status recover(lp_handle* h, const lp_options& o, cudaStream_t s, long long& launches) {
+    const int m = h->m, n = h->n;
+    std::vector<int> basis(m);
+    CUDA_TRY(cudaMemcpyAsync(basis.data(), h->basis, (size_t)m * 4, cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+    CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
+    std::vector<int> S, R;
+    std::vector<char> slack_basic(m, 0);
+    for (int v : basis) {
+        if (v < n)
+            S.push_back(v);
+        else
+            slack_basic[v - n] = 1;
+    }
+    std::sort(S.begin(), S.end());
+    for (int i = 0; i < m; ++i)
+        if (!slack_basic[i]) R.push_back(i);
+    if (S.size() != R.size()) {
+        set_error("lp_solve: the float phase left an inconsistent basis");
+        return LP_ERR_NUMERIC;
+    }
+    const double tol = o.recover_tol;
+    RecBufs& r = h->rec;
+    int cleanup = 0;
+    RecCheck chk{};
+    lp_status st = LP_OPTIMAL;
+    for (;;) {
+        st = recover_factor(h, o, s, S, R, chk, launches);
+        if (st != LP_OPTIMAL) return st;
+        const double pmin = std::min(chk.min_x, chk.min_s);
+        const double dmin = std::min(chk.min_d, chk.min_y);
+        if (pmin >= -tol && dmin >= -tol) break;                       // optimal in FP64
+        if (cleanup >= o.cleanup_max) {
+            set_error("lp_solve: FP64 cleanup did not converge in %d pivots", cleanup);
+            st = LP_ERR_NUMERIC;
+            break;
+        }
+        const int k = (int)S.size();
+        int e_kind, e_at, l_kind, l_at;
+        RecChoice ch{};
+        if (pmin < -tol) {
+            // dual step: the most negative basic value leaves
+            const bool structural = chk.min_x <= chk.min_s;
+            l_kind = structural ? 0 : 1;
+            l_at = structural ? chk.min_x_at : chk.min_s_at;
+            k_rec_rho<<<grid_for(k, 256, 1024), 256, 0, s>>>(n, h->A, r.S, k, r.inv, l_kind, l_at, r.rho);
+            k_rec_cols_dot<<<grid_for(n, 256, 8192), 256, 0, s>>>(n, h->A, r.Rr, k, r.rho, l_kind == 1 ? l_at : -1,
+                                                                  nullptr, r.arow);
+            k_rec_dual_ratio<256><<<1, 256, 0, s>>>(n, r.Rr, k, r.arow, r.d, r.isbasic, r.rho, r.yR, 1e-9, r.choice);
+            launches += 3;
+            CUDA_TRY(cudaMemcpyAsync(&ch, r.choice, sizeof ch, cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+            CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
+            if (ch.kind < 0) {
+                set_error("lp_solve: FP64 dual cleanup found no entering column");
+                st = LP_ERR_NUMERIC;
+                break;
+            }
+            e_kind = ch.kind;
+            e_at = ch.at;
+        } else {
+            // primal step: the most negative objective-row entry enters
+            const bool structural = chk.min_d <= chk.min_y;
+            e_kind = structural ? 0 : 1;
+            e_at = structural ? chk.min_d_at : chk.min_y_at;
+            k_rec_enter_col<<<grid_for(k, 256, 1024), 256, 0, s>>>(n, h->A, r.Rr, k, e_kind, e_at, r.venter);
+            k_rec_matvec<<<grid_for(32LL * k, 256, 4096), 256, 0, s>>>(r.inv, k, r.venter, 0, nullptr, r.aS);
+            k_rec_rows_dot<<<grid_for(32LL * m, 256, 8192), 256, 0, s>>>(m, n, h->A, r.S, k, nullptr,
+                                                                         e_kind == 0 ? e_at : -1, r.aS, r.aZ);
+            k_rec_primal_ratio<256><<<1, 256, 0, s>>>(m, n, r.S, k, r.xS, r.aS, r.s, r.aZ, r.inR, 1e-9, r.choice);
+            launches += 4;
+            CUDA_TRY(cudaMemcpyAsync(&ch, r.choice, sizeof ch, cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+            CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
+            if (ch.kind < 0) {
+                st = LP_UNBOUNDED;
+                break;
+            }
+            l_kind = ch.kind;
+            l_at = ch.at;
+        }
+        // basis exchange in the (S, R) form
+        if (e_kind == 0 && l_kind == 0) {
+            S[l_at] = e_at;
+        } else if (e_kind == 0 && l_kind == 1) {
+            S.push_back(e_at);
+            R.push_back(l_at);
+        } else if (e_kind == 1 && l_kind == 0) {
+            S.erase(S.begin() + l_at);
+            R.erase(R.begin() + e_at);
+        } else {
+            R[e_at] = l_at;
+        }
+        ++cleanup;
+    }
+    h->stats.cleanup_pivots = cleanup;
+    h->stats.k = (int)S.size();
+    h->stats.primal_violation = std::max(0.0, -std::min(chk.min_x, chk.min_s));
+    h->stats.dual_violation = std::max(0.0, -std::min(chk.min_d, chk.min_y));
+    h->stats.gap = std::fabs(chk.cx - chk.by);
+    // read-out: x, y, objective in FP64
+    const int k = (int)S.size();
+    CUDA_TRY(cudaMemsetAsync(h->sol, 0, (size_t)(n + m + 1) * sizeof(double), s), LP_ERR_CUDA);
+    k_rec_output<<<grid_for(std::max(k, 1), 256, 1024), 256, 0, s>>>(m, n, r.S, r.Rr, k, r.xS, r.yR, r.chk, h->sol);
+    ++launches;
+    std::vector<char> slack_nb(m, 0);
+    for (int i : R) slack_nb[i] = 1;
+    h->final_basis = S;
+    for (int i = 0; i < m; ++i)
+        if (!slack_nb[i]) h->final_basis.push_back(n + i);
+    std::sort(h->final_basis.begin(), h->final_basis.end());
+    return st;
+}
+
+template <int NT>
+static lp_status solve_nt(lp_handle* h, const lp_options& o, cudaStream_t s) {
+    const int m = h->m;
+    // pivot log buffers
+    if (o.log_capacity > 0 && o.log_capacity != h->log_cap) {
+        dev_free(h, h->logs);
+        h->log_cap = 0;
+        if (!dev_alloc_block(h, h->logs, (size_t)o.log_capacity * 2 * sizeof(int))) {
+            set_error("lp_solve: allocation of the pivot log failed");
+            return LP_ERR_NOMEM;
+        }
+        h->log_cap = o.log_capacity;
+    }
+    const bool fp32 = o.precision == LP_PREC_FP32;
+    lp_status st = ensure_work(h, fp32 ? 4 : 8);
+    if (st != LP_OPTIMAL) return st;
+
+    h->stats = lp_stats{};
+    h->sol_ready = false;
+    h->final_basis.clear();
+    DevState hs{};
+    long long launches = 0;
+    int path = 0, grid = 0;
+    if (fp32)
+        st = pivot_phase<NT, float>(h, o, s, o.eps_d_fp32, o.eps_p_fp32, hs, launches, path, grid);
+    else
+        st = pivot_phase<NT, double>(h, o, s, o.eps_d, o.eps_p, hs, launches, path, grid);
+    if (st == LP_ERR_CUDA) return st;
 
     float ms_build = 0.f, ms_pivot = 0.f;
     cudaEventElapsedTime(&ms_build, h->ev[0], h->ev[1]);
     cudaEventElapsedTime(&ms_pivot, h->ev[1], h->ev[2]);
-    h->stats = lp_stats{};
+    const int ld = h->work.ld, elem = h->work.elem, E = 32 / elem;
     h->stats.iters = hs.iters;
     h->stats.build_ms = ms_build;
     h->stats.pivot_ms = ms_pivot;
-    h->stats.kernel_launches = launches;
-    h->stats.dense_update_bytes = 2.0 * (double)(m + 1) * (double)h->W * sizeof(double) * (double)hs.iters;
+    h->stats.dense_update_bytes = 2.0 * (double)(m + 1) * (double)h->W * elem * (double)hs.iters;
     // bytes Step 3 moves: read + write of every listed 32-B group in rows
     // 1..m except p, read + write of the objective row and write of row p over
     // all groups; plus the side traffic of Steps 1-2 and the staging: column q
     // and right-hand-side sectors (m + 1 rows), pivot row read, R write + read.
     {
-        const double nsec = (double)(h->ld / 4);
+        const double nsec = (double)(ld / E);
         const double upd = 64.0 * (double)(m - 1) * (double)hs.active_sectors + 96.0 * nsec * (double)hs.iters;
-        const double side = (64.0 * (double)(m + 1) + 24.0 * (double)h->ld) * (double)hs.iters;
+        const double side = (64.0 * (double)(m + 1) + 3.0 * elem * (double)ld) * (double)hs.iters;
         h->stats.update_bytes = upd + side;
     }
     h->stats.path = path;
     h->stats.grid = grid;
     h->stats.block = NT;
-    h->stats.ld = h->ld;
+    h->stats.ld = ld;
+    h->stats.precision = o.precision;
+    h->stats.pivot_status = (int)st;
     for (int k = 0; k < 6; ++k) h->stats.phase_ms[k] = 1e-6 * (double)hs.phase_ns[k];
-
     h->iters = hs.iters;
-    h->solved = true;
-    st = (lp_status)hs.status;
-    if (hs.status == kRunning) {
-        set_error("lp_solve: kernel ended without a status");
-        st = LP_ERR_CUDA;
-    } else if (hs.status == kTimeout) {
-        set_error("lp_solve: a grid barrier wait exceeded %lld ns", (long long)P.timeout_ns);
+
+    if (fp32 && (st == LP_OPTIMAL || st == LP_ITER_LIMIT || st == LP_UNBOUNDED)) {
+        cudaEventRecord(h->ev[3], s);
+        long long rl = 0;
+        lp_status rs = recover(h, o, s, rl);
+        if (rs == LP_ERR_CUDA) return rs;
+        cudaEventRecord(h->ev[2], s);
+        CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
+        float ms_rec = 0.f;
+        cudaEventElapsedTime(&ms_rec, h->ev[3], h->ev[2]);
+        h->stats.recover_ms = ms_rec;
+        launches += rl;
+        // a float phase stopped by the iteration cap is finished by the cleanup
+        st = rs;
+        h->sol_ready = rs == LP_OPTIMAL;
     }
+    h->stats.kernel_launches = launches;
+    cudaEventRecord(h->ready, s);
+    h->solved = true;
     h->last_status = st;
     return st;
 }
@@ -744,7 +853,8 @@ lp_status lp_solve(lp_t h, const lp_options* opt) {
     else
         lp_options_init(&o);
     if (!(o.eps_d >= 0.0) || !(o.eps_p >= 0.0) || o.rule < 0 || o.rule > 1 || o.path < 0 || o.path > 2 ||
-        o.log_capacity < 0) {
+        o.log_capacity < 0 || o.precision < 0 || o.precision > 1 || !(o.eps_d_fp32 >= 0.0) ||
+        !(o.eps_p_fp32 >= 0.0) || !(o.recover_tol >= 0.0) || o.cleanup_max < 0) {
         set_error("lp_solve: invalid options");
         return LP_ERR_INVALID;
     }
@@ -775,16 +885,28 @@ lp_status lp_get_solution(lp_t h, double* x, double* y, double* obj, int* basis,
     cudaStream_t s = h->stream;
     CUDA_TRY(cudaStreamWaitEvent(s, h->ready, 0), LP_ERR_CUDA);
     const int m = h->m, n = h->n;
-    if (x || y || obj) {
+    if ((x || y || obj) && !h->sol_ready) {
+        const int ld = h->work.ld;
         int g = std::min((n + m + 1 + 255) / 256, 1024);
-        k_extract_dense<<<g, 256, 0, s>>>(m, n, h->W, h->ld, h->T, h->sol);
-        if (x) k_extract_x<<<std::min((m + 255) / 256, 1024), 256, 0, s>>>(m, n, h->W, h->ld, h->T, h->basis, h->sol);
+        int gx = std::min((m + 255) / 256, 1024);
+        if (h->work.elem == 8) {
+            k_extract_dense<double><<<g, 256, 0, s>>>(m, n, h->W, ld, (const double*)h->work.T, h->sol);
+            k_extract_x<double><<<gx, 256, 0, s>>>(m, n, h->W, ld, (const double*)h->work.T, h->basis, h->sol);
+        } else {
+            k_extract_dense<float><<<g, 256, 0, s>>>(m, n, h->W, ld, (const float*)h->work.T, h->sol);
+            k_extract_x<float><<<gx, 256, 0, s>>>(m, n, h->W, ld, (const float*)h->work.T, h->basis, h->sol);
+        }
         CUDA_TRY(cudaGetLastError(), LP_ERR_CUDA);
-        if (x) CUDA_TRY(cudaMemcpyAsync(x, h->sol, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
-        if (y) CUDA_TRY(cudaMemcpyAsync(y, h->sol + n, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
-        if (obj) CUDA_TRY(cudaMemcpyAsync(obj, h->sol + n + m, sizeof(double), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
     }
-    if (basis) CUDA_TRY(cudaMemcpyAsync(basis, h->basis, (size_t)m * sizeof(int), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+    if (x) CUDA_TRY(cudaMemcpyAsync(x, h->sol, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+    if (y) CUDA_TRY(cudaMemcpyAsync(y, h->sol + n, (size_t)m * sizeof(double), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+    if (obj) CUDA_TRY(cudaMemcpyAsync(obj, h->sol + n + m, sizeof(double), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+    if (basis) {
+        if (!h->final_basis.empty())
+            memcpy(basis, h->final_basis.data(), (size_t)m * sizeof(int));
+        else
+            CUDA_TRY(cudaMemcpyAsync(basis, h->basis, (size_t)m * sizeof(int), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+    }
     CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
     if (iters) *iters = h->iters;
     return (lp_status)h->last_status;
@@ -800,11 +922,27 @@ lp_status lp_get_tableau(lp_t h, double* T) {
         return LP_ERR_STATE;
     }
     CUDA_TRY(cudaSetDevice(h->device), LP_ERR_CUDA);
-    CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ready, 0), LP_ERR_CUDA);
-    CUDA_TRY(cudaMemcpy2DAsync(T, (size_t)h->W * sizeof(double), h->T, (size_t)h->ld * sizeof(double),
-                               (size_t)h->W * sizeof(double), (size_t)h->m + 1, cudaMemcpyDeviceToHost, h->stream),
-             LP_ERR_CUDA);
-    CUDA_TRY(cudaStreamSynchronize(h->stream), LP_ERR_CUDA);
+    cudaStream_t s = h->stream;
+    CUDA_TRY(cudaStreamWaitEvent(s, h->ready, 0), LP_ERR_CUDA);
+    const size_t rows = (size_t)h->m + 1, W = (size_t)h->W;
+    if (h->work.elem == 8) {
+        CUDA_TRY(cudaMemcpy2DAsync(T, W * sizeof(double), h->work.T, (size_t)h->work.ld * sizeof(double),
+                                   W * sizeof(double), rows, cudaMemcpyDeviceToHost, s),
+                 LP_ERR_CUDA);
+    } else {
+        // float tableau: widened to double on the device, then copied
+        Block tmp;
+        if (!dev_alloc_block(h, tmp, rows * W * sizeof(double))) {
+            set_error("lp_get_tableau: allocation of the widened copy failed");
+            return LP_ERR_NOMEM;
+        }
+        k_widen<float><<<grid_for((long long)(rows * W), 256, 152 * 16), 256, 0, s>>>(
+            (int)rows, (int)W, h->work.ld, (const float*)h->work.T, (double*)tmp.ptr);
+        CUDA_TRY(cudaMemcpyAsync(T, tmp.ptr, rows * W * sizeof(double), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+        CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
+        dev_free(h, tmp);
+    }
+    CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
     return LP_OPTIMAL;
 }
 
@@ -881,53 +1019,28 @@ static lp_status noalloc_nt(int m, int n, const double* dA, const double* db, co
     cudaStream_t s = (cudaStream_t)o.stream;
     int device = 0;
     CUDA_TRY(cudaGetDevice(&device), LP_ERR_CUDA);
-    Params P{};
-    P.T = dT;
-    P.ld = ld;
-    P.m = m;
-    P.n = n;
-    P.W = n + m + 1;
-    P.basis = dbasis;
-    P.F = (double*)base;
-    P.R = (double*)(base + off_R);
-    P.act = (int*)(base + off_act);
-    P.cpart = (ArgPart*)(base + off_cp);
-    P.rpart = (RatPart*)(base + off_rp);
-    P.st = (DevState*)(base + off_st);
-    P.qlog = nullptr;
-    P.plog = nullptr;
-    P.log_cap = 0;
-    P.eps_d = o.eps_d;
-    P.eps_p = o.eps_p;
-    P.max_iters = o.max_iters < 0 ? 50LL * ((long long)m + n) : o.max_iters;
-    P.k_cyc = o.k_cyc;
-    P.rule = o.rule;
-    P.timeout_ns = std::max(0LL, o.barrier_timeout_ns);
-    P.nstrips = (ld + kStripCols - 1) / kStripCols;
-    P.nrc = (m + 1 + kUnitRows - 1) / kUnitRows;
-    P.nunits = (long long)P.nstrips * P.nrc;
-    P.skip_zero = o.skip_zero_columns ? 1 : 0;
+    DevState* st = (DevState*)(base + off_st);
+    Params<double> P = make_params<double>(m, n, ld, dT, (double*)base, (double*)(base + off_R),
+                                           (int*)(base + off_act), (ArgPart*)(base + off_cp),
+                                           (RatPart*)(base + off_rp), st, dbasis, o, o.eps_d, o.eps_p);
 
     // validate the inputs: the state word starts from zero on every call
-    k_reset_state<<<1, 32, 0, s>>>(P.st);
+    k_reset_state<<<1, 32, 0, s>>>(st);
     {
         const size_t total = (size_t)m * n + m + n;
         int g = (int)std::min<size_t>((total + 255) / 256, 4096);
-        k_validate<<<g, 256, 0, s>>>(m, n, dA, db, dc, P.st);
+        k_validate<<<g, 256, 0, s>>>(m, n, dA, db, dc, st);
     }
     int bad = 0;
-    CUDA_TRY(cudaMemcpyAsync(&bad, &P.st->bad, sizeof(int), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+    CUDA_TRY(cudaMemcpyAsync(&bad, &st->bad, sizeof(int), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
     CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
     if (bad) {
         set_error("lp_solve_noalloc: inputs must be finite with b >= 0");
         return LP_ERR_INVALID;
     }
 
-    const long long want = (P.nunits + NT / 32 - 1) / (NT / 32);
-    int coresident = max_coresident<NT>(device);
-    int grid = (int)std::min<long long>(std::max<long long>(1, want), std::max(1, coresident));
-    grid = std::min(grid, kNoAllocMaxGrid);
-    if (o.blocks > 0) grid = std::min(grid, o.blocks);
+    int coresident = 0;
+    const int grid = pivot_grid<NT, double>(device, m, ld, kNoAllocMaxGrid, o.blocks, coresident);
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, device);
     int path = o.path;
@@ -937,15 +1050,15 @@ static lp_status noalloc_nt(int m, int n, const double* dA, const double* db, co
         return LP_ERR_CUDA;
     }
 
-    k_reset_state<<<1, 32, 0, s>>>(P.st);
+    k_reset_state<<<1, 32, 0, s>>>(st);
     {
         const size_t groups = (size_t)(m + 1) * (size_t)(ld / 4);
         int g = (int)std::min<size_t>((groups + 255) / 256, 152 * 16);
-        k_build<<<g, 256, 0, s>>>(m, n, n + m + 1, ld, dA, db, dc, dT, dbasis);
+        k_build<double><<<g, 256, 0, s>>>(m, n, n + m + 1, ld, dA, db, dc, dT, dbasis);
     }
     CUDA_TRY(cudaGetLastError(), LP_ERR_CUDA);
     if (path == LP_PATH_PERSISTENT) {
-        cudaError_t e = launch_persistent<NT>(P, grid, s);
+        cudaError_t e = launch_persistent<NT, double>(P, grid, s);
         if (e != cudaSuccess) {
             if (o.path != LP_PATH_AUTO) {
                 set_error("lp_solve_noalloc: cooperative launch failed: %s", cudaGetErrorString(e));
@@ -956,24 +1069,11 @@ static lp_status noalloc_nt(int m, int n, const double* dA, const double* db, co
         }
     }
     if (path == LP_PATH_MULTILAUNCH) {
-        k_ml_init<<<grid, NT, 0, s>>>(P);
-        int status = kRunning;
-        int batch = 4;
-        for (;;) {
-            for (int k = 0; k < batch; ++k) {
-                k_ml_select<NT><<<grid, NT, 0, s>>>(P);
-                k_ml_stage<NT><<<grid, NT, 0, s>>>(P);
-                k_ml_update<NT><<<grid, NT, 0, s>>>(P);
-            }
-            CUDA_TRY(cudaGetLastError(), LP_ERR_CUDA);
-            CUDA_TRY(cudaMemcpyAsync(&status, &P.st->status, sizeof(int), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
-            CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
-            if (status != kRunning) break;
-            batch = std::min(batch * 2, 64);
-        }
+        long long launches = 0;
+        if (run_multilaunch<NT, double>(P, grid, s, launches) == LP_ERR_CUDA) return LP_ERR_CUDA;
     }
     DevState hs{};
-    CUDA_TRY(cudaMemcpyAsync(&hs, P.st, sizeof(DevState), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+    CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(DevState), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
     CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
     if (iters_out) *iters_out = hs.iters;
     if (hs.status == kRunning) {
@@ -1010,12 +1110,13 @@ lp_status lp_solve_noalloc(int m, int n, const double* dA, const double* db, con
     else
         lp_options_init(&o);
     if (!(o.eps_d >= 0.0) || !(o.eps_p >= 0.0) || o.rule < 0 || o.rule > 1 || o.path < 0 || o.path > 2 ||
-        o.log_capacity != 0 || o.blocks < 0 || o.blocks > kNoAllocMaxGrid) {
-        set_error("lp_solve_noalloc: invalid options (log_capacity must be 0, blocks <= %d)", kNoAllocMaxGrid);
+        o.log_capacity != 0 || o.blocks < 0 || o.blocks > kNoAllocMaxGrid || o.precision != LP_PREC_FP64) {
+        set_error("lp_solve_noalloc: invalid options (FP64 only, log_capacity must be 0, blocks <= %d)",
+                  kNoAllocMaxGrid);
         return LP_ERR_INVALID;
     }
     // layout of the array: F | R | act | cpart | rpart | state
-    const size_t nstrips = ((size_t)ld + kStripCols - 1) / kStripCols;
+    const size_t nstrips = ((size_t)ld + 127) / 128;
     const size_t off_R = align_up((size_t)(m + 1) * sizeof(double), 256);
     const size_t off_act = align_up(off_R + (size_t)ld * sizeof(double), 256);
     const size_t off_cp = align_up(off_act + (size_t)(ld / 4) * sizeof(int), 256);

@@ -1,8 +1,9 @@
 // Device side of the dense full-tableau simplex pivot (arXiv 2211.10979,
 // Section III Steps 1-3; Section IV Steps 1-4 for one GPU).
 //
-// One pivot is four phases over the row-major tableau T ((m+1) x ld doubles,
-// W = n + m + 1 logical columns, the last one the right-hand side):
+// One pivot is four phases over the row-major tableau T ((m+1) x ld entries of
+// type V = double or float, W = n + m + 1 logical columns, the last one the
+// right-hand side):
 //   P1  entering column q: reduce the per-strip (value, index) partials of the
 //       objective row left by the previous P4 (Section III Step 1, Dantzig's
 //       most negative coefficient; Section IV Step 1's local-then-global
@@ -11,12 +12,13 @@
 //       every block scans a share of the rows, copies column q into F and keeps
 //       its best (ratio, key, row) -> one partial per block.
 //   P3  leaving row p = reduce of the P2 partials; pivot-row staging
-//       R[j] = T[p][j] / T[p][q] (Section III Step 3's pivot row).
+//       R[j] = T[p][j] / T[p][q] (Section III Step 3's pivot row) and the list
+//       of 32-byte column groups of row p holding a nonzero entry.
 //   P4  rank-1 update T[i][j] = fma(-F[i], R[j], T[i][j]) for i != p and
 //       T[p][j] = R[j] (Section III Step 3, Section IV Step 4), streamed with
-//       256-bit accesses, one warp per strip of 128 columns; the warp holding the
-//       objective row of a strip also emits that strip's argmin partial of the
-//       new objective row (the next P1's input).
+//       256-bit accesses; the objective row is updated first, one warp per strip,
+//       each emitting that strip's argmin partial of the new objective row (the
+//       next P1's input).
 // Between phases every block of the grid passes a device-wide barrier whose
 // wait is bounded in time (the paper's per-iteration synchronisation,
 // Section IV Iterate/Finalization).
@@ -30,8 +32,6 @@
 namespace tsx {
 
 constexpr int kRunning = 100;      // status while the iteration is in progress
-constexpr int kStripCols = 128;    // columns of one warp strip (32 lanes x 4)
-constexpr int kUnitRows = 32;      // rows of one work unit (one strip)
 #ifndef TSX_ROWS_IN_FLIGHT
 #define TSX_ROWS_IN_FLIGHT 8
 #endif
@@ -75,13 +75,19 @@ struct DevState {
                                        // barrier wait after each of them
 };
 
+// Entries of type V per 32-byte sector (one lane's share of a warp access).
+template <typename V> struct Lanes;
+template <> struct Lanes<double> { static constexpr int E = 4; };
+template <> struct Lanes<float> { static constexpr int E = 8; };
+
+template <typename V>
 struct Params {
-    double* T;           // tableau, (m+1) x ld
+    V* T;                // tableau, (m+1) x ld
     int ld, m, n, W;
     int* basis;          // m: variable basic in row i+1
-    double* F;           // m+1: column q of the tableau before the update
-    double* R;           // ld: scaled pivot row
-    int* act;            // ld/4: indices of the 32-B column groups Step 3 updates
+    V* F;                // m+1: column q of the tableau before the update
+    V* R;                // ld: scaled pivot row
+    int* act;            // ld/E: indices of the 32-B column groups Step 3 updates
     ArgPart* cpart;      // nstrips: objective-row argmin partial per strip
     RatPart* rpart;      // grid blocks: ratio-test partial per block
     DevState* st;
@@ -92,26 +98,16 @@ struct Params {
     long long max_iters;
     int k_cyc, rule;
     long long timeout_ns;
-    int nstrips;         // ceil(ld / kStripCols)
-    int nrc;             // ceil((m+1) / kUnitRows)
-    long long nunits;    // nstrips * nrc
+    int nstrips;         // ceil(ld / (32 E)): warp strips of the objective row
     int skip_zero;       // leave column groups whose R entries are all zero
 };
 
 // ------------------------------------------------------------------ helpers
-// One 32-byte sector of the tableau: four consecutive doubles.
-struct __align__(32) sec4 {
-    double x, y, z, w;
+// One 32-byte sector of the tableau: E consecutive entries.
+template <typename V>
+struct __align__(32) Sector {
+    V v[Lanes<V>::E];
 };
-
-__device__ __forceinline__ sec4 make_sec4(double x, double y, double z, double w) {
-    sec4 v;
-    v.x = x;
-    v.y = y;
-    v.z = z;
-    v.w = w;
-    return v;
-}
 
 __device__ __forceinline__ long long global_ns() {
     unsigned long long t;
@@ -142,24 +138,57 @@ __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
     return old;
 }
 
-// 256-bit accesses of one 32-byte sector (4 doubles); addresses 32-B aligned.
-__device__ __forceinline__ sec4 ld_sector_stream(const double* p) {
-    sec4 v;
+// 256-bit accesses of one 32-byte sector; addresses 32-byte aligned.
+// "stream": the bulk update's loads (no L1 allocation); "cg": L2 loads of data
+// another block wrote before the last barrier.
+__device__ __forceinline__ Sector<double> ld_sector_stream(const double* p) {
+    Sector<double> s;
     asm volatile("ld.global.L1::no_allocate.v4.f64 {%0,%1,%2,%3}, [%4];"
-                 : "=d"(v.x), "=d"(v.y), "=d"(v.z), "=d"(v.w) : "l"(p));
-    return v;
+                 : "=d"(s.v[0]), "=d"(s.v[1]), "=d"(s.v[2]), "=d"(s.v[3]) : "l"(p));
+    return s;
 }
-
-__device__ __forceinline__ sec4 ld_sector_cg(const double* p) {
-    sec4 v;
+__device__ __forceinline__ Sector<double> ld_sector_cg(const double* p) {
+    Sector<double> s;
     asm volatile("ld.global.cg.v4.f64 {%0,%1,%2,%3}, [%4];"
-                 : "=d"(v.x), "=d"(v.y), "=d"(v.z), "=d"(v.w) : "l"(p));
-    return v;
+                 : "=d"(s.v[0]), "=d"(s.v[1]), "=d"(s.v[2]), "=d"(s.v[3]) : "l"(p));
+    return s;
+}
+__device__ __forceinline__ void st_sector(double* p, const Sector<double>& s) {
+    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};"
+                 ::"l"(p), "d"(s.v[0]), "d"(s.v[1]), "d"(s.v[2]), "d"(s.v[3]) : "memory");
+}
+__device__ __forceinline__ Sector<float> ld_sector_stream(const float* p) {
+    Sector<float> s;
+    asm volatile("ld.global.L1::no_allocate.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(s.v[0]), "=f"(s.v[1]), "=f"(s.v[2]), "=f"(s.v[3]),
+                   "=f"(s.v[4]), "=f"(s.v[5]), "=f"(s.v[6]), "=f"(s.v[7]) : "l"(p));
+    return s;
+}
+__device__ __forceinline__ Sector<float> ld_sector_cg(const float* p) {
+    Sector<float> s;
+    asm volatile("ld.global.cg.v8.f32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=f"(s.v[0]), "=f"(s.v[1]), "=f"(s.v[2]), "=f"(s.v[3]),
+                   "=f"(s.v[4]), "=f"(s.v[5]), "=f"(s.v[6]), "=f"(s.v[7]) : "l"(p));
+    return s;
+}
+__device__ __forceinline__ void st_sector(float* p, const Sector<float>& s) {
+    asm volatile("st.global.v8.f32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};"
+                 ::"l"(p), "f"(s.v[0]), "f"(s.v[1]), "f"(s.v[2]), "f"(s.v[3]),
+                   "f"(s.v[4]), "f"(s.v[5]), "f"(s.v[6]), "f"(s.v[7]) : "memory");
 }
 
-__device__ __forceinline__ void st_sector(double* p, sec4 v) {
-    asm volatile("st.global.v4.f64 [%0], {%1,%2,%3,%4};"
-                 ::"l"(p), "d"(v.x), "d"(v.y), "d"(v.z), "d"(v.w) : "memory");
+// One rounding per operation, in the tableau's own precision.
+__device__ __forceinline__ double fma_rn(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ float fma_rn(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double div_rn(double a, double b) { return __ddiv_rn(a, b); }
+__device__ __forceinline__ float div_rn(float a, float b) { return __fdiv_rn(a, b); }
+
+template <typename V>
+__device__ __forceinline__ bool sector_nonzero(const Sector<V>& s) {
+    bool nz = false;
+#pragma unroll
+    for (int e = 0; e < Lanes<V>::E; ++e) nz |= s.v[e] != V(0);
+    return nz;
 }
 
 __device__ __forceinline__ ArgPart arg_none() { return ArgPart{__longlong_as_double(0x7ff0000000000000LL), INT_MAX, INT_MAX}; }
@@ -176,6 +205,12 @@ __device__ __forceinline__ void arg_consider(ArgPart& a, double v, int j, int je
         if (v < a.v || (v == a.v && j < a.j)) { a.v = v; a.j = j; }
         a.jfirst = min(a.jfirst, j);
     }
+}
+
+template <typename V>
+__device__ __forceinline__ void arg_consider_sector(ArgPart& a, const Sector<V>& s, int j, int jend, double eps_d) {
+#pragma unroll
+    for (int e = 0; e < Lanes<V>::E; ++e) arg_consider(a, (double)s.v[e], j + e, jend, eps_d);
 }
 
 // (r, key) lexicographic minimum: smallest ratio, lowest key on ties.
@@ -230,10 +265,8 @@ __device__ __forceinline__ RatPart load_rat(const RatPart* src) {
 struct BlockScratch {
     ArgPart arg[kMaxWarps];
     RatPart rat[kMaxWarps];
-    unsigned long long cnt[kMaxWarps];
     ArgPart arg_out;
     RatPart rat_out;
-    unsigned long long cnt_out;
     int ok;
 };
 
@@ -266,23 +299,6 @@ __device__ RatPart block_rat(RatPart a, BlockScratch& s) {
     }
     __syncthreads();
     return s.rat_out;
-}
-
-__device__ unsigned long long block_sum(unsigned long long v, BlockScratch& s) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if (lane == 0) s.cnt[w] = v;
-    __syncthreads();
-    if (w == 0) {
-        unsigned long long b = lane < nw ? s.cnt[lane] : 0ull;
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) b += __shfl_xor_sync(0xffffffffu, b, o);
-        if (lane == 0) s.cnt_out = b;
-    }
-    __syncthreads();
-    return s.cnt_out;
 }
 
 // ------------------------------------------------------------- grid barrier
@@ -330,35 +346,33 @@ __device__ bool grid_barrier(DevState* st, long long timeout_ns, BlockScratch& s
 
 // ------------------------------------------------------------------ phases
 // Initial objective-row argmin (before the first pivot): one warp per strip.
-__device__ void phase_init_argmin(const Params& P) {
+template <typename V>
+__device__ void phase_init_argmin(const Params<V>& P) {
+    constexpr int E = Lanes<V>::E;
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     for (long long s = gw; s < P.nstrips; s += nw) {
-        const int j = (int)s * kStripCols + lane * 4;
+        const int j = (int)s * 32 * E + lane * E;
         ArgPart a = arg_none();
-        if (j < P.ld) {
-            sec4 v = ld_sector_cg(P.T + j);
-            arg_consider(a, v.x, j, P.W - 1, P.eps_d);
-            arg_consider(a, v.y, j + 1, P.W - 1, P.eps_d);
-            arg_consider(a, v.z, j + 2, P.W - 1, P.eps_d);
-            arg_consider(a, v.w, j + 3, P.W - 1, P.eps_d);
-        }
+        if (j < P.ld) arg_consider_sector(a, ld_sector_cg(P.T + j), j, P.W - 1, P.eps_d);
         a = warp_arg(a);
         if (lane == 0) store_arg(P.cpart + s, a);
     }
 }
 
 // P1: global entering candidate from the strip partials (every block).
-__device__ ArgPart phase_entering(const Params& P, BlockScratch& s) {
+template <typename V>
+__device__ ArgPart phase_entering(const Params<V>& P, BlockScratch& s) {
     ArgPart a = arg_none();
     for (int k = threadIdx.x; k < P.nstrips; k += blockDim.x) arg_merge(a, load_arg(P.cpart + k));
     return block_arg(a, s);
 }
 
 // P2: ratio test on column q and copy of column q into F; one partial per block.
-// Row i goes to block i mod G, so the FP64 divisions spread over every SM.
-__device__ void phase_ratio(const Params& P, int q, int bland, BlockScratch& s) {
+// Row i goes to block i mod G, so the divisions spread over every SM.
+template <typename V>
+__device__ void phase_ratio(const Params<V>& P, int q, int bland, BlockScratch& s) {
     RatPart best = rat_none();
     const long long nth = (long long)gridDim.x * blockDim.x;
     if (blockIdx.x == 0 && threadIdx.x == 0) {   // counted again in P3 / P4
@@ -366,12 +380,12 @@ __device__ void phase_ratio(const Params& P, int q, int bland, BlockScratch& s) 
         P.st->next_slot = 0;
     }
     for (long long i = (long long)threadIdx.x * gridDim.x + blockIdx.x; i <= P.m; i += nth) {
-        const double* row = P.T + (size_t)i * (size_t)P.ld;
-        const double a = __ldcg(row + q);
+        const V* row = P.T + (size_t)i * (size_t)P.ld;
+        const V a = __ldcg(row + q);
         __stcg(P.F + i, a);
-        if (i >= 1 && a > P.eps_p) {
+        if (i >= 1 && (double)a > P.eps_p) {
             RatPart c;
-            c.r = __ldcg(row + (P.W - 1)) / a;
+            c.r = (double)div_rn(__ldcg(row + (P.W - 1)), a);
             c.i = (int)i;
             c.key = bland ? __ldcg(P.basis + (i - 1)) : (int)i;
             rat_merge(best, c);
@@ -382,7 +396,8 @@ __device__ void phase_ratio(const Params& P, int q, int bland, BlockScratch& s) 
 }
 
 // P3a: global leaving candidate from the block partials (every block).
-__device__ RatPart phase_leaving(const Params& P, BlockScratch& s) {
+template <typename V>
+__device__ RatPart phase_leaving(const Params<V>& P, BlockScratch& s) {
     RatPart a = rat_none();
     for (int k = threadIdx.x; k < (int)gridDim.x; k += blockDim.x) rat_merge(a, load_rat(P.rpart + k));
     return block_rat(a, s);
@@ -394,23 +409,18 @@ __device__ RatPart phase_leaving(const Params& P, BlockScratch& s) {
 // list does not matter, every group is updated independently).  With
 // skip_zero == 0 every group is listed.  (2) R[j] = T[p][j] / piv over the
 // padded row, element j on block j mod G so the divisions spread over all SMs.
-__device__ void phase_stage_row(const Params& P, int p, double piv, BlockScratch& s) {
-    const double* row = P.T + (size_t)p * (size_t)P.ld;
+template <typename V>
+__device__ void phase_stage_row(const Params<V>& P, int p, V piv) {
+    constexpr int E = Lanes<V>::E;
+    const V* row = P.T + (size_t)p * (size_t)P.ld;
     const int lane = threadIdx.x & 31;
-    const long long nsec = P.ld / 4;
+    const long long nsec = P.ld / E;
     const long long wi = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     const long long nwi = (long long)(blockDim.x >> 5) * gridDim.x;
     for (long long base = wi * 32; base < nsec; base += nwi * 32) {
         const long long k = base + lane;
         bool nz = false;
-        if (k < nsec) {
-            if (P.skip_zero) {
-                const sec4 v = ld_sector_cg(row + 4 * k);
-                nz = v.x != 0.0 || v.y != 0.0 || v.z != 0.0 || v.w != 0.0;
-            } else {
-                nz = true;
-            }
-        }
+        if (k < nsec) nz = P.skip_zero ? sector_nonzero(ld_sector_cg(row + E * k)) : true;
         const unsigned mask = __ballot_sync(0xffffffffu, nz);
         if (mask) {
             unsigned off = 0;
@@ -421,57 +431,48 @@ __device__ void phase_stage_row(const Params& P, int p, double piv, BlockScratch
     }
     const long long nth = (long long)gridDim.x * blockDim.x;
     for (long long e = (long long)threadIdx.x * gridDim.x + blockIdx.x; e < P.ld; e += nth)
-        __stcg(P.R + e, __ldcg(row + e) / piv);
+        __stcg(P.R + e, div_rn(__ldcg(row + e), piv));
 }
 
 // P4a: the objective row and the pivot row, every column group.  One warp per
-// strip of 128 columns: T[0][j] = fma(-F[0], R[j], T[0][j]) with the strip's
-// argmin partial of the new objective row (the next Step 1's input), and
-// T[p][j] = R[j].
-__device__ void phase_update_edge_rows(const Params& P, int p) {
+// strip: T[0][j] = fma(-F[0], R[j], T[0][j]) with the strip's argmin partial of
+// the new objective row (the next Step 1's input), and T[p][j] = R[j].
+template <typename V>
+__device__ void phase_update_edge_rows(const Params<V>& P, int p) {
+    constexpr int E = Lanes<V>::E;
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-    const double f0 = __ldcg(P.F);
+    const V f0 = __ldcg(P.F);
     const int jend = P.W - 1;
     for (long long s = gw; s < P.nstrips; s += nw) {
-        const int j = (int)s * kStripCols + lane * 4;
+        const int j = (int)s * 32 * E + lane * E;
         ArgPart a = arg_none();
         if (j < P.ld) {
-            const sec4 r = ld_sector_cg(P.R + j);
-            const sec4 v = ld_sector_stream(P.T + j);
-            sec4 o;
-            o.x = __fma_rn(-f0, r.x, v.x);
-            o.y = __fma_rn(-f0, r.y, v.y);
-            o.z = __fma_rn(-f0, r.z, v.z);
-            o.w = __fma_rn(-f0, r.w, v.w);
+            const Sector<V> r = ld_sector_cg(P.R + j);
+            Sector<V> o = ld_sector_stream(P.T + j);
+#pragma unroll
+            for (int e = 0; e < E; ++e) o.v[e] = fma_rn(-f0, r.v[e], o.v[e]);
             st_sector(P.T + j, o);
             st_sector(P.T + (size_t)p * (size_t)P.ld + j, r);
-            arg_consider(a, o.x, j, jend, P.eps_d);
-            arg_consider(a, o.y, j + 1, jend, P.eps_d);
-            arg_consider(a, o.z, j + 2, jend, P.eps_d);
-            arg_consider(a, o.w, j + 3, jend, P.eps_d);
+            arg_consider_sector(a, o, j, jend, P.eps_d);
         }
         a = warp_arg(a);
         if (lane == 0) store_arg(P.cpart + s, a);
     }
 }
 
-// P4b: the rank-1 update of rows 1..m except p on the listed column groups:
-// T[i][j] = fma(-F[i], R[j], T[i][j]).  Work slots are (group of kRowsInFlight
-// rows, chunk of 32 listed column groups), numbered row-group-major, so that
-// consecutive slots stream along the same rows and the rows' F values stay in
-// registers while the row group is unchanged.  One listed column group per
-// lane.  Groups not listed have R == 0: their update is the identity.
 // One work slot: rows i0 .. i0+nrows-1 (row p excluded) of the column group
 // listed at entry c*32 + lane.
-__device__ __forceinline__ void update_slot(const Params& P, int p, unsigned nact, long long c, int i0,
-                                            int nrows, const double* f) {
+template <typename V>
+__device__ __forceinline__ void update_slot(const Params<V>& P, int p, unsigned nact, long long c, int i0,
+                                            int nrows, const V* f) {
+    constexpr int E = Lanes<V>::E;
     const long long e = c * 32 + (threadIdx.x & 31);
     if (e >= (long long)nact) return;
-    const size_t col = 4 * (size_t)__ldcg(P.act + e);
-    const sec4 r = ld_sector_cg(P.R + col);
-    sec4 v[kRowsInFlight];
+    const size_t col = (size_t)E * (size_t)__ldcg(P.act + e);
+    const Sector<V> r = ld_sector_cg(P.R + col);
+    Sector<V> v[kRowsInFlight];
 #pragma unroll
     for (int k = 0; k < kRowsInFlight; ++k) {
         const int i = i0 + k;
@@ -481,23 +482,27 @@ __device__ __forceinline__ void update_slot(const Params& P, int p, unsigned nac
     for (int k = 0; k < kRowsInFlight; ++k) {
         const int i = i0 + k;
         if (k < nrows && i != p) {
-            sec4 o;
-            o.x = __fma_rn(-f[k], r.x, v[k].x);
-            o.y = __fma_rn(-f[k], r.y, v[k].y);
-            o.z = __fma_rn(-f[k], r.z, v[k].z);
-            o.w = __fma_rn(-f[k], r.w, v[k].w);
-            st_sector(P.T + (size_t)i * (size_t)P.ld + col, o);
+#pragma unroll
+            for (int e2 = 0; e2 < E; ++e2) v[k].v[e2] = fma_rn(-f[k], r.v[e2], v[k].v[e2]);
+            st_sector(P.T + (size_t)i * (size_t)P.ld + col, v[k]);
         }
     }
 }
 
-__device__ void phase_update_bulk(const Params& P, int p, unsigned nact) {
+// P4b: the rank-1 update of rows 1..m except p on the listed column groups:
+// T[i][j] = fma(-F[i], R[j], T[i][j]).  Work slots are (group of kRowsInFlight
+// rows, chunk of 32 listed column groups), numbered row-group-major, so that
+// consecutive slots stream along the same rows and the rows' F values stay in
+// registers while the row group is unchanged.  One listed column group per
+// lane.  Groups not listed have R == 0: their update is the identity.
+template <typename V>
+__device__ void phase_update_bulk(const Params<V>& P, int p, unsigned nact) {
     const int lane = threadIdx.x & 31;
     const long long nchunks = ((long long)nact + 31) / 32;
     const long long ngroups = ((long long)P.m + kRowsInFlight - 1) / kRowsInFlight;
     const long long total = nchunks * ngroups;
     long long gcur = -1;
-    double f[kRowsInFlight];
+    V f[kRowsInFlight];
     int i0 = 1, nrows = 0;
     // Slots are handed out TSX_GRAB at a time from a counter (a static split
     // leaves the slowest blocks ~15% behind the mean); the next grab is
@@ -518,14 +523,15 @@ __device__ void phase_update_bulk(const Params& P, int p, unsigned nact) {
                 i0 = 1 + (int)g * kRowsInFlight;
                 nrows = min(kRowsInFlight, P.m + 1 - i0);
 #pragma unroll
-                for (int k = 0; k < kRowsInFlight; ++k) f[k] = k < nrows ? __ldcg(P.F + i0 + k) : 0.0;
+                for (int k = 0; k < kRowsInFlight; ++k) f[k] = k < nrows ? __ldcg(P.F + i0 + k) : V(0);
             }
             update_slot(P, p, nact, c, i0, nrows, f);
         }
     }
 }
 
-__device__ void phase_update(const Params& P, int p) {
+template <typename V>
+__device__ void phase_update(const Params<V>& P, int p) {
     const unsigned nact = *(volatile const unsigned*)&P.st->nact;
     if (blockIdx.x == 0 && threadIdx.x == 0) P.st->active_sectors += nact;
     phase_update_edge_rows(P, p);

@@ -1,0 +1,284 @@
+// Kernels of the full-tableau simplex (arXiv 2211.10979, Section III), for a
+// tableau of doubles or floats (V):
+//   k_reset_state         zero the per-solve state word block
+//   k_validate            inputs finite, b >= 0 (create)
+//   k_build<V>            Initialization Step: Table I tableau, slack basis
+//   k_pivot_persistent    Steps 1-3 iterated inside one cooperative launch
+//   k_ml_*                the same phases, one launch each (fallback, profiling)
+//   k_extract_*<V>        read-out of x, y, objective from the tableau
+#pragma once
+
+#include "tsx_device.cuh"
+
+namespace tsx {
+
+__global__ void k_reset_state(DevState* st) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        st->status = kRunning;
+        st->q = -1;
+        st->p = -1;
+        st->bland = 0;
+        st->degen_run = 0;
+        st->bad = 0;
+        st->iters = 0;
+        st->active_sectors = 0;
+        st->theta = 0.0;
+        st->bar_count = 0;
+        st->bar_gen = 0;
+        st->nact = 0;
+        st->next_slot = 0;
+        for (int k = 0; k < 6; ++k) st->phase_ns[k] = 0;
+    }
+}
+
+// Input check: every entry finite, b >= 0.
+__global__ void k_validate(int m, int n, const double* __restrict__ A, const double* __restrict__ b,
+                           const double* __restrict__ c, DevState* st) {
+    const size_t mn = (size_t)m * (size_t)n;
+    const size_t total = mn + (size_t)m + (size_t)n;
+    int bad = 0;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (size_t)gridDim.x * blockDim.x) {
+        double v;
+        if (k < mn) {
+            v = A[k];
+            bad |= !isfinite(v);
+        } else if (k < mn + m) {
+            v = b[k - mn];
+            bad |= !isfinite(v) || !(v >= 0.0);
+        } else {
+            v = c[k - mn - m];
+            bad |= !isfinite(v);
+        }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->bad, 1);
+}
+
+// Initialization Step (Section III, Table I): row 0 = [-c, 0 | 0],
+// row i = [A_i, e_i | b_i]; padding columns [W, ld) are zero.  One thread per
+// 32-byte sector; the float tableau takes the inputs rounded to nearest.
+// Also seeds the slack basis.
+template <typename V>
+__global__ void k_build(int m, int n, int W, int ld, const double* __restrict__ A,
+                        const double* __restrict__ b, const double* __restrict__ c,
+                        V* __restrict__ T, int* __restrict__ basis) {
+    constexpr int E = Lanes<V>::E;
+    const size_t per_row = (size_t)ld / E;
+    const size_t total = (size_t)(m + 1) * per_row;
+    for (size_t g = (size_t)blockIdx.x * blockDim.x + threadIdx.x; g < total;
+         g += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(g / per_row);
+        const int j0 = (int)(g - (size_t)i * per_row) * E;
+        Sector<V> out;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int j = j0 + e;
+            double v = 0.0;
+            if (i == 0) {
+                if (j < n) v = -c[j];
+            } else {
+                if (j < n)
+                    v = A[(size_t)(i - 1) * (size_t)n + j];
+                else if (j == n + i - 1)
+                    v = 1.0;
+                else if (j == W - 1)
+                    v = b[i - 1];
+            }
+            out.v[e] = (V)v;
+        }
+        st_sector(T + (size_t)i * (size_t)ld + j0, out);
+    }
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)m;
+         i += (size_t)gridDim.x * blockDim.x)
+        basis[i] = n + (int)i;
+}
+
+// Pivot bookkeeping shared by both paths (one thread): basis update, pivot log.
+template <typename V>
+__device__ __forceinline__ void record_pivot(const Params<V>& P, long long it, int q, int p) {
+    P.basis[p - 1] = q;
+    if (it < P.log_cap) {
+        P.qlog[it] = q;
+        P.plog[it] = p;
+    }
+}
+
+// Cycling guard: a pivot with minimum ratio <= 0 does not move the objective;
+// k_cyc of them in a row switch to Bland's rule until a positive-ratio pivot.
+template <typename V>
+__device__ __forceinline__ void degeneracy_step(const Params<V>& P, double theta, int& bland, int& degen) {
+    if (P.rule != 0) return;
+    if (theta <= 0.0) {
+        ++degen;
+        if (P.k_cyc > 0 && degen >= P.k_cyc) bland = 1;
+    } else {
+        degen = 0;
+        bland = 0;
+    }
+}
+
+template <typename V>
+__device__ __forceinline__ void finish(const Params<V>& P, int status, long long it, int bland, int degen,
+                                       const long long* ph) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        atomicCAS(&P.st->status, kRunning, status);
+        P.st->iters = it;
+        P.st->bland = bland;
+        P.st->degen_run = degen;
+        for (int k = 0; k < 6; ++k) P.st->phase_ns[k] = ph[k];
+    }
+}
+
+// Phase timer of block 0, thread 0 (other threads keep it at zero).
+struct PhaseClock {
+    long long acc[6] = {0, 0, 0, 0, 0, 0};
+    long long t = 0;
+    bool on = false;
+    __device__ void start() {
+        on = blockIdx.x == 0 && threadIdx.x == 0;
+        if (on) t = global_ns();
+    }
+    __device__ void lap(int k) {   // closes interval k, opens the next one
+        if (on) {
+            const long long now = global_ns();
+            acc[k] += now - t;
+            t = now;
+        }
+    }
+};
+
+// Steps 1-3 iterated inside one cooperative launch; three grid barriers per
+// pivot (after P2, after P3, after P4).  Every block takes the same decisions
+// from the same reduced values, so all leave the loop together.
+template <int NT, typename V>
+__global__ void __launch_bounds__(NT, 512 / NT) k_pivot_persistent(Params<V> P) {
+    __shared__ BlockScratch s;
+    PhaseClock clk;
+    phase_init_argmin(P);
+    if (!grid_barrier(P.st, P.timeout_ns, s)) return;
+    long long it = 0;
+    int bland = P.rule == 1 ? 1 : 0;
+    int degen = 0;
+    clk.start();
+    for (;;) {
+        const ArgPart e = phase_entering(P, s);           // Step 1
+        const int q = bland ? e.jfirst : e.j;
+        if (q == INT_MAX) { finish(P, kOptimal, it, bland, degen, clk.acc); return; }
+        if (it >= P.max_iters) { finish(P, kIterLimit, it, bland, degen, clk.acc); return; }
+        phase_ratio(P, q, bland, s);                      // Step 2 (block partials)
+        clk.lap(0);
+        if (!grid_barrier(P.st, P.timeout_ns, s)) return;
+        clk.lap(3);
+        const RatPart l = phase_leaving(P, s);            // Step 2 (global)
+        if (l.i == INT_MAX) { finish(P, kUnbounded, it, bland, degen, clk.acc); return; }
+        const V piv = __ldcg(P.F + l.i);
+        if (!isfinite((double)piv) || !isfinite(l.r)) { finish(P, kNumeric, it, bland, degen, clk.acc); return; }
+        phase_stage_row(P, l.i, piv);                     // Step 3 (pivot row)
+        if (blockIdx.x == 0 && threadIdx.x == 0) record_pivot(P, it, q, l.i);
+        clk.lap(1);
+        if (!grid_barrier(P.st, P.timeout_ns, s)) return;
+        clk.lap(4);
+        phase_update(P, l.i);                             // Step 3 (rank-1 update)
+        ++it;
+        degeneracy_step(P, l.r, bland, degen);
+        clk.lap(2);
+        if (!grid_barrier(P.st, P.timeout_ns, s)) return;
+        clk.lap(5);
+    }
+}
+
+// ---- one launch per phase (same device functions; state in DevState)
+template <typename V>
+__global__ void k_ml_init(Params<V> P) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.st->bland = P.rule == 1 ? 1 : 0;
+    phase_init_argmin(P);
+}
+
+template <int NT, typename V>
+__global__ void __launch_bounds__(NT) k_ml_select(Params<V> P) {
+    __shared__ BlockScratch s;
+    if (P.st->status != kRunning) return;
+    const int bland = P.st->bland;
+    const long long it = P.st->iters;
+    const ArgPart e = phase_entering(P, s);
+    const int q = bland ? e.jfirst : e.j;
+    if (q == INT_MAX || it >= P.max_iters) {
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            atomicCAS(&P.st->status, kRunning, q == INT_MAX ? kOptimal : kIterLimit);
+        return;
+    }
+    phase_ratio(P, q, bland, s);
+    if (blockIdx.x == 0 && threadIdx.x == 0) P.st->q = q;
+}
+
+template <int NT, typename V>
+__global__ void __launch_bounds__(NT) k_ml_stage(Params<V> P) {
+    __shared__ BlockScratch s;
+    if (P.st->status != kRunning) return;
+    const RatPart l = phase_leaving(P, s);
+    if (l.i == INT_MAX) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&P.st->status, kRunning, kUnbounded);
+        return;
+    }
+    const V piv = __ldcg(P.F + l.i);
+    if (!isfinite((double)piv) || !isfinite(l.r)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&P.st->status, kRunning, kNumeric);
+        return;
+    }
+    phase_stage_row(P, l.i, piv);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        record_pivot(P, P.st->iters, P.st->q, l.i);
+        P.st->p = l.i;
+        P.st->theta = l.r;
+    }
+}
+
+template <int NT, typename V>
+__global__ void __launch_bounds__(NT, 512 / NT) k_ml_update(Params<V> P) {
+    if (P.st->status != kRunning) return;
+    const int p = P.st->p;
+    phase_update(P, p);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        int bland = P.st->bland, degen = P.st->degen_run;
+        degeneracy_step(P, P.st->theta, bland, degen);
+        P.st->bland = bland;
+        P.st->degen_run = degen;
+        P.st->iters += 1;
+    }
+}
+
+// Solution read-out (Table I layout), widened to double: y_i = T[0][n+i],
+// obj = T[0][W-1], x zeroed, then x[basis[i]] = T[i+1][W-1] for structural
+// basics.
+template <typename V>
+__global__ void k_extract_dense(int m, int n, int W, int ld, const V* __restrict__ T, double* __restrict__ sol) {
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n + m + 1; k += gridDim.x * blockDim.x) {
+        if (k < n)
+            sol[k] = 0.0;
+        else if (k < n + m)
+            sol[k] = (double)T[n + (k - n)];
+        else
+            sol[k] = (double)T[W - 1];
+    }
+}
+
+template <typename V>
+__global__ void k_extract_x(int m, int n, int W, int ld, const V* __restrict__ T, const int* __restrict__ basis,
+                            double* __restrict__ sol) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+        const int v = basis[i];
+        if (v < n) sol[v] = (double)T[(size_t)(i + 1) * (size_t)ld + (W - 1)];
+    }
+}
+
+// Tableau copy-out widened to double (row-major, W columns).
+template <typename V>
+__global__ void k_widen(int rows, int W, int ld, const V* __restrict__ T, double* __restrict__ out) {
+    const size_t total = (size_t)rows * (size_t)W;
+    for (size_t k = (size_t)blockIdx.x * blockDim.x + threadIdx.x; k < total; k += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = k / (size_t)W, j = k - i * (size_t)W;
+        out[k] = (double)T[i * (size_t)ld + j];
+    }
+}
+
+}  // namespace tsx

@@ -44,6 +44,8 @@ def test_options_defaults_roundtrip(lib):
     assert o.k_cyc == 50 and o.barrier_timeout_ns == 2_000_000_000 and o.path == 0
     assert o.skip_zero_columns == 1 and o.threads == 0 and o.blocks == 0
     assert o.log_capacity == 0 and o.stream is None
+    assert o.precision == tsx.LP_PREC_FP64 and o.eps_d_fp32 == 1e-5 and o.eps_p_fp32 == 1e-6
+    assert o.recover_tol == 1e-9 and o.cleanup_max == 1000
     assert "sm_103a" in tsx.lp_version()
 
 

@@ -1,0 +1,156 @@
+"""The FP32 path (float tableau for every pivot, FP64 recovery on the GPU).
+
+Two bars:
+  - the float pivots equal the float variant of the oracle step by step
+    (tableau entries and (q, p) pairs identical: same operations, same order);
+  - the recovered result equals the FP64 oracle's: objective within 1e-9
+    relative, x and y within 1e-9 relative to their scale, and primal/dual
+    feasibility violations at most 1e-9 (times 1 + |b| or 1 + |c|).
+"""
+import numpy as np
+import pytest
+
+import lpgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tsx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_10979_gb300 import build
+    build.build()
+    import paper_2211_10979_gb300 as mod
+    mod.use_torch_allocator()
+    return mod
+
+
+def _run(tsx, A, b, c, **kw):
+    kw.setdefault("log_capacity", 100000)
+    kw.setdefault("precision", tsx.LP_PREC_FP32)
+    with tsx.Problem(A, b, c) as pr:
+        st = pr.solve(tsx.options(**kw))
+        sol = pr.solution()
+        T = pr.tableau()
+        q, p = pr.pivot_log(kw["log_capacity"])
+        return st, sol, T, q, p, pr.stats()
+
+
+def _violations(A, b, c, x, y):
+    pv = max(0.0, float(np.max((A @ x - b) / (1.0 + np.abs(b)))), float(-x.min()))
+    dv = max(0.0, float(np.max((c - A.T @ y) / (1.0 + np.abs(c)))), float(-y.min()))
+    return pv, dv
+
+
+def _assert_matches_fp64(A, b, c, sol, ref, tol=1e-9):
+    assert abs(sol.obj - ref.obj) <= tol * abs(ref.obj)
+    scale_x = max(1.0, float(np.abs(ref.x).max()))
+    scale_y = max(1.0, float(np.abs(ref.y).max()))
+    assert np.abs(sol.x - ref.x).max() <= tol * scale_x
+    assert np.abs(sol.y - ref.y).max() <= tol * scale_y
+    pv, dv = _violations(A, b, c, sol.x, sol.y)
+    assert pv <= tol and dv <= tol
+    assert abs(c @ sol.x - b @ sol.y) <= tol * abs(ref.obj)
+
+
+@pytest.mark.parametrize("m,n", [(1, 5), (7, 3), (37, 53), (100, 300), (256, 256), (300, 100)])
+def test_float_pivots_equal_float_oracle(tsx, m, n):
+    A, b, c = lpgen.dense_lp(m, n, 100 + m + n)
+    st32, it32, qref, pref, Tref, bref = oracle.solve32(A, b, c)
+    st, sol, T, q, p, stats = _run(tsx, A, b, c)
+    assert stats["pivot_status"] == st32 and stats["iters"] == it32
+    np.testing.assert_array_equal(q, qref)
+    np.testing.assert_array_equal(p, pref)
+    np.testing.assert_array_equal(T, Tref.astype(np.float64))
+
+
+@pytest.mark.parametrize("k", [1, 3, 11])
+def test_float_tableau_after_k_pivots(tsx, k):
+    A, b, c = lpgen.dense_lp(200, 150, 21)
+    st32, it32, qref, pref, Tref, bref = oracle.solve32(A, b, c, oracle.Options(eps_d=1e-5, eps_p=1e-6,
+                                                                                 max_iters=k))
+    st, sol, T, q, p, stats = _run(tsx, A, b, c, max_iters=k)
+    assert stats["pivot_status"] == oracle.ITER_LIMIT == st32
+    np.testing.assert_array_equal(T, Tref.astype(np.float64))
+
+
+@pytest.mark.parametrize("m,n,seed", [(16, 16, 1), (64, 64, 2), (256, 256, 1), (256, 256, 3),
+                                      (1024, 1024, 1), (512, 2048, 2), (2048, 512, 3)])
+def test_recovered_result_equals_fp64_oracle(tsx, m, n, seed):
+    A, b, c = lpgen.dense_lp(m, n, seed)
+    ref = oracle.solve(A, b, c)
+    st, sol, T, q, p, stats = _run(tsx, A, b, c)
+    assert st == tsx.LP_OPTIMAL == ref.status
+    _assert_matches_fp64(A, b, c, sol, ref)
+    assert stats["k"] == int((ref.basis < n).sum())
+    assert sorted(sol.basis.tolist()) == sorted(ref.basis.tolist())
+    assert stats["primal_violation"] <= 1e-9 and stats["dual_violation"] <= 1e-9
+    assert stats["recover_ms"] > 0
+
+
+@pytest.mark.parametrize("k", [0, 2, 7])
+def test_primal_cleanup_finishes_a_stopped_float_phase(tsx, k):
+    # the float phase stops after k pivots; FP64 cleanup pivots (revised form)
+    # must carry the basis to the optimum
+    A, b, c = lpgen.dense_lp(120, 90, 7)
+    ref = oracle.solve(A, b, c)
+    st, sol, T, q, p, stats = _run(tsx, A, b, c, max_iters=k)
+    assert stats["pivot_status"] == tsx.LP_ITER_LIMIT
+    assert st == tsx.LP_OPTIMAL
+    assert stats["cleanup_pivots"] > 0
+    _assert_matches_fp64(A, b, c, sol, ref)
+
+
+def test_dual_cleanup_repairs_an_infeasible_basis(tsx):
+    # a float ratio test that ignores entries below 3 picks wrong leaving rows,
+    # so the float basis is primal infeasible; dual cleanup pivots repair it
+    A, b, c = lpgen.dense_lp(80, 60, 9)
+    ref = oracle.solve(A, b, c)
+    st, sol, T, q, p, stats = _run(tsx, A, b, c, eps_p_fp32=3.0)
+    assert st == tsx.LP_OPTIMAL
+    assert stats["cleanup_pivots"] > 0
+    _assert_matches_fp64(A, b, c, sol, ref)
+
+
+def test_golden_traces_and_special_cases(tsx, golden_dir):
+    import json
+    import os
+    for name in ("two_pivots_dyadic.json", "one_pivot.json", "unbounded_after_one.json"):
+        g = json.load(open(os.path.join(golden_dir, name)))
+        A = np.array(g["A"], dtype=np.float64)
+        b = np.array(g["b"], dtype=np.float64)
+        c = np.array(g["c"], dtype=np.float64)
+        st, sol, T, q, p, stats = _run(tsx, A, b, c)
+        assert tsx.STATUS_NAMES[st] == g["status"]
+        if g["status"] == "OPTIMAL":
+            assert sol.obj == g["obj"]
+            np.testing.assert_array_equal(sol.x, np.array(g["x"], dtype=np.float64))
+    # nothing to improve: x = 0 from the start
+    A, b, _ = lpgen.dense_lp(6, 4, 2)
+    st, sol, T, q, p, stats = _run(tsx, A, b, -np.ones(4))
+    assert st == tsx.LP_OPTIMAL and sol.obj == 0.0 and stats["k"] == 0
+    assert not sol.x.any() and not sol.y.any()
+
+
+def test_fp32_full_size_16384(tsx):
+    # the precision workload: m = n = 16384, float tableau (2.1 GB) for every
+    # pivot, FP64 recovery; checked by certificates and against the FP64 path
+    import torch
+    m = n = 16384
+    A, b, c = lpgen.dense_lp(m, n, 1)
+    dA, db, dc = (torch.from_numpy(v).cuda() for v in (A, b, c))
+    s = torch.cuda.current_stream().cuda_stream
+    with tsx.Problem(dA, db, dc, device=True, stream=s) as pr:
+        assert pr.solve(tsx.options(stream=s, precision=tsx.LP_PREC_FP32)) == tsx.LP_OPTIMAL
+        sol32 = pr.solution()
+        st32 = pr.stats()
+        assert pr.solve(tsx.options(stream=s)) == tsx.LP_OPTIMAL
+        sol64 = pr.solution()
+    assert abs(sol32.obj - sol64.obj) <= 1e-9 * abs(sol64.obj)
+    pv, dv = _violations(A, b, c, sol32.x, sol32.y)
+    assert pv <= 1e-9 and dv <= 1e-9
+    assert abs(c @ sol32.x - b @ sol32.y) <= 1e-9 * abs(sol64.obj)
+    assert st32["primal_violation"] <= 1e-9 and st32["dual_violation"] <= 1e-9

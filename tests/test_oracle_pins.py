@@ -271,3 +271,52 @@ def test_degenerate_duplicate_rows():
     r = oracle.solve(A, b, c)
     best, _ = _vertex_max(A, b, c)
     assert r.status == oracle.OPTIMAL and abs(r.obj - best) <= 1e-9 * best
+
+
+# ------------------------------------------------------------- float variant
+@pytest.mark.parametrize("name", ["two_pivots_dyadic.json", "one_pivot.json",
+                                  "unbounded_after_one.json"])
+def test_float_variant_hand_derived_trace_is_exact(golden_dir, name):
+    # every value of these traces is a float as well: the float steps must
+    # reproduce them exactly
+    g = _load_golden(golden_dir, name)
+    A = np.array(g["A"], dtype=np.float64)
+    b = np.array(g["b"], dtype=np.float64)
+    c = np.array(g["c"], dtype=np.float64)
+    m, n = A.shape
+    T, basis = oracle.build_tableau32(A, b, c)
+    np.testing.assert_array_equal(T, np.array(g["T0"], dtype=np.float32))
+    for st in g["steps"]:
+        q = oracle.entering32(T, m, n)
+        assert q == st["q"]
+        p, ratio = oracle.leaving32(T, basis, m, n, q)
+        assert p == st["p"] and ratio == st["ratio"]
+        oracle.pivot32(T, m, n, p, q)
+        basis[p - 1] = q
+        np.testing.assert_array_equal(T, np.array(st["T"], dtype=np.float32))
+    status, iters, qlog, plog, T, basis = oracle.solve32(A, b, c)
+    assert oracle.STATUS_NAMES[status] == g["status"]
+    assert qlog.tolist() == [s["q"] for s in g["steps"]]
+
+
+def test_float_variant_brute_force_objective():
+    rng = np.random.default_rng(31)
+    for _ in range(60):
+        m, n = int(rng.integers(1, 6)), int(rng.integers(1, 6))
+        A, b, c = _small_lp(rng, m, n, False)
+        status, iters, qlog, plog, T, basis = oracle.solve32(A, b, c)
+        assert status == oracle.OPTIMAL
+        best, _ = _vertex_max(A, b, c)
+        best = max(best, 0.0)
+        assert abs(float(T[0, -1]) - best) <= 2e-5 * max(1.0, abs(best))
+
+
+def test_float_variant_follows_double_run_on_generated_lp():
+    # both precisions choose the same pivots here (gaps between candidates are
+    # far above float rounding); the objectives agree to float accuracy
+    A, b, c = lpgen.dense_lp(96, 80, 4)
+    ref = oracle.solve(A, b, c)
+    status, iters, qlog, plog, T, basis = oracle.solve32(A, b, c)
+    assert status == oracle.OPTIMAL and iters == ref.iters
+    assert qlog.tolist() == ref.qlog.tolist()
+    assert abs(float(T[0, -1]) - ref.obj) <= 1e-5 * abs(ref.obj)
