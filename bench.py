@@ -52,6 +52,13 @@ def parse_args(argv=None):
     ap.add_argument("--path", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--blocks", type=int, default=0)
+    ap.add_argument("--workload", choices=["single", "batch"], default="single",
+                    help="batch: 4096 small LPs (m, n uniform in [16, 128]) per step")
+    ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--plain-sample", type=int, default=256,
+                    help="LPs of the batch solved one at a time for the plain-path figure")
+    ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
+                    help="fp32: float tableau for every pivot + FP64 recovery on the GPU")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args(argv)
@@ -239,8 +246,9 @@ def run_gpu(args, rank, world, local):
     resident = {s: tuple(torch.from_numpy(v).to(dev) for v in host[s]) for s in seeds}
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
+    prec = tsx.LP_PREC_FP32 if args.precision == "fp32" else tsx.LP_PREC_FP64
     opts = tsx.options(stream=sptr, skip_zero_columns=args.skip_zero, path=args.path,
-                       threads=args.threads, blocks=args.blocks)
+                       threads=args.threads, blocks=args.blocks, precision=prec)
 
     x = np.empty(n)
     y = np.empty(m)
@@ -296,7 +304,8 @@ def run_gpu(args, rank, world, local):
         h = tsx.lp_create(m, n, A, b, c)
         try:
             st = tsx.lp_solve(h, tsx.options(skip_zero_columns=args.skip_zero, path=args.path,
-                                             threads=args.threads, blocks=args.blocks))
+                                             threads=args.threads, blocks=args.blocks,
+                                             precision=prec))
             if st != tsx.LP_OPTIMAL:
                 raise RuntimeError(f"solve ended {tsx.STATUS_NAMES.get(st, st)}")
             _, it = tsx.lp_get_solution(h, xo, yo, oo, bo)
@@ -313,6 +322,34 @@ def run_gpu(args, rank, world, local):
         e2e_piv = sum(e2e_step(seeds[k % len(seeds)]) for k in range(args.e2e_steps))
         torch.cuda.synchronize(dev)
         e2e_secs = time.perf_counter() - t0
+
+    # FP32 path: objective error of each timed seed against the FP64 path
+    # (untimed), which equals the FP64 oracle step by step
+    prec_info = None
+    if args.precision == "fp32":
+        errs = []
+        for sd in seeds:
+            dA, db, dc = resident[sd]
+            h = tsx.lp_create_device(m, n, dA, db, dc, sptr)
+            try:
+                tsx.lp_solve(h, tsx.options(stream=sptr, precision=tsx.LP_PREC_FP32))
+                o32 = np.empty(1)
+                tsx.lp_get_solution(h, None, None, o32, None)
+                s32 = tsx.lp_get_stats(h).as_dict()
+                tsx.lp_solve(h, tsx.options(stream=sptr))
+                o64 = np.empty(1)
+                tsx.lp_get_solution(h, None, None, o64, None)
+                errs.append((abs(o32[0] - o64[0]) / abs(o64[0]), s32))
+            finally:
+                tsx.lp_destroy(h)
+        prec_info = {
+            "objective_rel_err_vs_fp64_max": max(e for e, _ in errs),
+            "cleanup_pivots": [st_["cleanup_pivots"] for _, st_ in errs],
+            "k": [st_["k"] for _, st_ in errs],
+            "recover_ms": [round(st_["recover_ms"], 3) for _, st_ in errs],
+            "primal_violation_max": max(st_["primal_violation"] for _, st_ in errs),
+            "dual_violation_max": max(st_["dual_violation"] for _, st_ in errs),
+        }
 
     per_rank = [(pivots, secs, e2e_piv, e2e_secs)]
     if dist:
@@ -340,9 +377,11 @@ def run_gpu(args, rank, world, local):
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000.0 * tmax / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64" if args.precision == "fp64" else "f32 tableau + f64 recovery",
+            "data": "synthetic",
             "config": {
-                "workload": f"dense LP m={m} n={n} FP64, full solve per step (seeded "
+                "workload": f"dense LP m={m} n={n} {args.precision.upper()}, full solve per step (seeded "
                             "A~U[1,10), b~U[100,1000), c~U[1,10); slack basis; Dantzig)",
                 "m": m, "n": n, "seeds_per_rank": len(seeds),
                 "pivots_per_step": pivots / args.steps,
@@ -371,6 +410,170 @@ def run_gpu(args, rank, world, local):
         }
         if cpu:
             line["cpu_baseline"] = cpu
+        if prec_info:
+            line["precision"] = prec_info
+            line["roofline"]["traffic"] = None
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+FP64_PEAK_TFLOPS = 1.25   # GB300 nominal FP64 (one DFMA = 2 flops)
+
+
+def batch_problems(count, seed):
+    """The batching workload: LP k has m, n uniform in [16, 128] and the dense
+    generator's data with seed 10_000 + k (per-rank offsets by `seed`)."""
+    shapes = lpgen.batch_shapes(count, 16, 128, seed)
+    return [lpgen.dense_lp(mm, nn, 10_000 * seed + k) for k, (mm, nn) in enumerate(shapes)]
+
+
+def oracle_batch_sample(problems, budget_s):
+    import oracle
+    t0 = time.perf_counter()
+    done = 0
+    for A, b, c in problems:
+        oracle.solve(A, b, c, log_cap=1)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    secs = time.perf_counter() - t0
+    return {"value": done / secs, "unit": "LPs/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {done} LPs of the batch, solved one by one (single-threaded C, FP64)"}
+
+
+def run_batch(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2211_10979_gb300 as tsx
+    from paper_2211_10979_gb300 import build as tsx_build
+    tsx_build.build()
+    tsx.use_torch_allocator()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    count = args.batch_count
+    problems = batch_problems(count, 1 + rank)
+    m = np.array([p[0].shape[0] for p in problems], dtype=np.int32)
+    n = np.array([p[0].shape[1] for p in problems], dtype=np.int32)
+    A = np.concatenate([p[0].ravel() for p in problems])
+    b = np.concatenate([p[1] for p in problems])
+    c = np.concatenate([p[2] for p in problems])
+    dA, db, dc = (torch.from_numpy(v).to(dev) for v in (A, b, c))
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    status = np.empty(count, dtype=np.int32)
+    iters = np.empty(count, dtype=np.int64)
+    obj = np.empty(count)
+    x = np.empty(int(n.sum()))
+    y = np.empty(int(m.sum()))
+    h = tsx.lp_batch_create_device(count, m, n, dA, db, dc, sptr)
+    opts = tsx.batch_options(stream=sptr)
+    try:
+        for _ in range(args.warmup):   # the first solve autotunes and captures the graph
+            tsx.lp_batch_solve(h, opts)
+            tsx.lp_batch_get(h, status, iters, obj, x, y)
+        torch.cuda.synchronize(dev)
+        clocks = ClockSampler(local) if rank == 0 else None
+        if clocks:
+            clocks.start()
+        if dist:
+            dist.barrier()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        kernel_ms = 0.0
+        for _ in range(args.steps):
+            if tsx.lp_batch_solve(h, opts) != 0:
+                raise RuntimeError(tsx.lp_last_error())
+            tsx.lp_batch_get(h, status, iters, obj, x, y)
+            kernel_ms += tsx.lp_batch_get_stats(h).solve_ms
+        ev1.record(stream)
+        torch.cuda.synchronize(dev)
+        if dist:
+            dist.barrier()
+        clk = clocks.stop() if clocks else None
+        secs = ev0.elapsed_time(ev1) / 1000.0
+        bstats = tsx.lp_batch_get_stats(h).as_dict()
+    finally:
+        tsx.lp_batch_destroy(h)
+    assert (status == 0).all(), "every LP of the workload is solved to optimality"
+    pivots = int(iters.sum())
+    flops = float(np.sum(2.0 * (m + 1.0) * (n + 1.0) * iters))   # one FMA per condensed entry
+
+    # plain path: the same resident LPs one at a time through lp_create_device / lp_solve
+    k_plain = min(args.plain_sample, count)
+    offs_a = np.concatenate([[0], np.cumsum(m.astype(np.int64) * n)])
+    offs_b = np.concatenate([[0], np.cumsum(m)])
+    offs_c = np.concatenate([[0], np.cumsum(n)])
+    xo = np.empty(int(n.max()))
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for k in range(k_plain):
+        hk = tsx.lp_create_device(int(m[k]), int(n[k]), dA[offs_a[k]:offs_a[k + 1]], db[offs_b[k]:offs_b[k + 1]],
+                                  dc[offs_c[k]:offs_c[k + 1]], sptr)
+        try:
+            tsx.lp_solve(hk, tsx.options(stream=sptr))
+            tsx.lp_get_solution(hk, xo[:n[k]], None, None, None)
+        finally:
+            tsx.lp_destroy(hk)
+    plain_secs = time.perf_counter() - t0
+
+    # e2e: packed inputs from pinned host memory, copies inside the timed region
+    pA, pb, pc = (torch.from_numpy(v).pin_memory() for v in (A, b, c))
+    e2e_steps = max(1, args.e2e_steps)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        he = tsx.lp_batch_create(count, m, n, pA, pb, pc)
+        try:
+            tsx.lp_batch_solve(he, tsx.batch_options())   # reuses the device's tuned threads
+            tsx.lp_batch_get(he, status, iters, obj, x, y)
+        finally:
+            tsx.lp_batch_destroy(he)
+    e2e_secs = time.perf_counter() - t0
+
+    per_rank = [(count * args.steps, secs, count * e2e_steps, e2e_secs)]
+    if dist:
+        t = torch.tensor(per_rank[0], dtype=torch.float64, device=dev)
+        allt = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(allt, t)
+        per_rank = [tuple(v.tolist()) for v in allt]
+    value, tmax = combine_ranks([(p, s_) for p, s_, _, _ in per_rank])
+    e2e_value, _ = combine_ranks([(p, s_) for _, _, p, s_ in per_rank])
+    if rank == 0:
+        kernel_s = kernel_ms / 1000.0 / args.steps
+        achieved = flops / kernel_s / 1e12
+        line = {
+            "metric": "LPs/s", "value": value, "unit": "LPs/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * tmax / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": f"batch of {count} dense LPs, m and n uniform in [16, 128], FP64, "
+                                   "one solve of the whole batch per step (results copied to the host)",
+                       "pivots_per_step": pivots, "classes": bstats["lps_per_class"],
+                       "threads_per_lp": bstats["threads"], "graph": bstats["graph"],
+                       "l2": f"inputs {A.nbytes / 1e6:.0f} MB; tableaux in shared memory"},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP64_PEAK_TFLOPS,
+                         "peak_source": "nominal GB300 FP64 rate (1.25 TFLOP/s)",
+                         "traffic": None, "kernel": "k_batch_solve",
+                         "flops_per_launch": flops, "kernel_ms_per_launch": 1000.0 * kernel_s,
+                         "pivots_per_s": pivots / kernel_s},
+            "plain": {"value": k_plain / plain_secs, "unit": "LPs/s",
+                      "sample": f"first {k_plain} LPs of the batch, lp_create_device + lp_solve + "
+                                "lp_get_solution one at a time",
+                      "speedup_of_batch": value / (k_plain / plain_secs)},
+            "e2e": {"value": e2e_value, "unit": "LPs/s", "h2d_bytes_per_step": int(A.nbytes + b.nbytes + c.nbytes),
+                    "d2h_bytes_per_step": int(status.nbytes + iters.nbytes + obj.nbytes + x.nbytes + y.nbytes)},
+            "gpu_launches": int(bstats["kernel_launches"]) * args.steps * world,
+            "clocks": clk,
+        }
+        if not args.no_cpu_baseline:
+            line["cpu_baseline"] = oracle_batch_sample(problems, args.cpu_seconds)
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -385,6 +588,8 @@ def main(argv=None):
         print(f"warning: --gpus {args.gpus} but WORLD_SIZE={world}", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.workload == "batch":
+        return run_batch(args, rank, world, local)
     return run_gpu(args, rank, world, local)
 
 

@@ -196,6 +196,83 @@ int lp_set_allocator(lp_alloc_fn alloc_fn, lp_free_fn free_fn, void *ctx);
 /* Version string of the library. */
 const char *lp_version(void);
 
+/* ------------------------------------------------------------------------
+ * Batched solve: many small LPs in one persistent launch (one thread block per
+ * LP, the LP's tableau in shared memory).  Every LP is the problem of
+ * lp_create and is solved by the same method (Section III, Table I start,
+ * Steps 1-3 with the same tie rules), FP64.  Results equal lp_solve's entry
+ * for entry.  The block keeps the condensed tableau (the nonbasic columns and
+ * the right-hand side; the basic columns of the full tableau are unit
+ * vectors), which must fit in shared memory: 8 ((m+1) ldc + m + 1 + ldc) +
+ * 4 (m + n) bytes <= the device's opt-in block limit (227 KB on GB300;
+ * ldc = n + 1 or n + 2, odd), e.g. m = n = 128 needs 134 KB.
+ * ------------------------------------------------------------------------ */
+typedef struct lp_batch *lp_batch_t;
+
+typedef struct {
+    int threads;                  /* threads per LP (32, 64, 128, 256);
+                                     0 = autotune: each shared-memory size class
+                                     times the candidates once per device; the
+                                     choice is reused by later solves and
+                                     batches on that device                     */
+    int rule;                     /* as lp_options                              */
+    double eps_d, eps_p;          /* as lp_options (defaults 1e-9)              */
+    long long max_iters;          /* per LP; < 0: 50 (m + n)                    */
+    int k_cyc;                    /* as lp_options (default 50)                 */
+    int use_graph;                /* 1 (default): the launches of a solve are
+                                     captured once in a CUDA graph and replayed */
+    int keep_tableaux;            /* 1: keep every LP's final tableau for
+                                     lp_batch_get_tableau (default 0)           */
+    void *stream;                 /* cudaStream_t; NULL = the batch's stream    */
+} lp_batch_options;
+
+typedef struct {
+    double solve_ms;              /* device time of the last solve              */
+    long long total_pivots;       /* pivots of all LPs                          */
+    long long kernel_launches;    /* kernels of the last solve (graph nodes)    */
+    int buckets;                  /* shared-memory size classes used            */
+    int threads[4];               /* threads per LP chosen for each class       */
+    int lps_per_class[4];
+    double tune_ms;               /* time spent autotuning (first solve)        */
+    int graph;                    /* 1 if the solve replayed a CUDA graph       */
+} lp_batch_stats;
+
+void lp_batch_options_init(lp_batch_options *opt);
+
+/* Create a batch from HOST arrays: LP k has m[k] constraints and n[k]
+ * variables; A holds the LPs' constraint matrices back to back (each m[k] x
+ * n[k] row-major), b the right-hand sides back to back (sum of m[k]) and c the
+ * price vectors back to back (sum of n[k]).  Copied to the device.  Each LP
+ * must satisfy lp_create's conditions and fit in shared memory (see above);
+ * otherwise NULL (lp_last_error names the LP).  Per-LP input errors found on
+ * the device (non-finite data, b < 0) are reported as that LP's status. */
+lp_batch_t lp_batch_create(int count, const int *m, const int *n, const double *A,
+                           const double *b, const double *c);
+
+/* Same with DEVICE arrays (m, n stay host arrays); the arrays are referenced
+ * and must stay valid until lp_batch_destroy; `stream` as lp_create_device. */
+lp_batch_t lp_batch_create_device(int count, const int *m, const int *n, const double *dA,
+                                  const double *db, const double *dc, void *stream);
+
+/* Solve every LP of the batch (from the slack basis).  Blocks until done.
+ * Returns LP_OPTIMAL if the launch succeeded (per-LP outcomes come from
+ * lp_batch_get), or an error. */
+lp_status lp_batch_solve(lp_batch_t h, const lp_batch_options *opt);
+
+/* Per-LP results to HOST arrays (any may be NULL): status[count], iters[count],
+ * obj[count], x packed like c (sum of n[k]), y packed like b (sum of m[k]). */
+lp_status lp_batch_get(lp_batch_t h, int *status, long long *iters, double *obj, double *x,
+                       double *y);
+
+/* Full final tableau of LP `index` ((m+1) x (n+m+1) row-major, HOST), rebuilt
+ * from the kept condensed tableau; needs a solve with keep_tableaux = 1. */
+lp_status lp_batch_get_tableau(lp_batch_t h, int index, double *T);
+
+lp_status lp_batch_get_stats(lp_batch_t h, lp_batch_stats *stats);
+
+/* Free the batch (NULL is ignored). */
+void lp_batch_destroy(lp_batch_t h);
+
 /* Solve without allocating any device memory.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory
  * themselves or let the library do it -- for example a plugin running inside

@@ -18,10 +18,14 @@ from .abi import (LP_ERR_CUDA, LP_ERR_INVALID, LP_ERR_NOMEM, LP_ERR_NUMERIC, LP_
                   LP_PATH_PERSISTENT, LP_PREC_FP32, LP_PREC_FP64, LP_RULE_BLAND, LP_RULE_DANTZIG, LP_UNBOUNDED, STATUS_NAMES,
                   lp_create, lp_create_device, lp_destroy, lp_get_pivot_log, lp_get_solution,
                   lp_get_stats, lp_get_tableau, lp_last_error, lp_options, lp_options_init,
-                  lp_set_allocator, lp_solve, lp_solve_noalloc, lp_stats, lp_version)
+                  lp_set_allocator, lp_solve, lp_solve_noalloc, lp_stats, lp_version,
+                  lp_batch_options, lp_batch_options_init, lp_batch_create, lp_batch_create_device,
+                  lp_batch_solve, lp_batch_get, lp_batch_get_tableau, lp_batch_get_stats,
+                  lp_batch_destroy)
 
 __all__ = [n for n in dir(abi) if n.startswith(("lp_", "LP_"))] + [
-    "STATUS_NAMES", "Solution", "Problem", "solve", "use_torch_allocator", "options"]
+    "STATUS_NAMES", "Solution", "Problem", "solve", "use_torch_allocator", "options",
+    "Batch", "BatchSolution", "batch_options"]
 
 _torch_hooks = None
 
@@ -121,6 +125,93 @@ class Problem:
     def close(self):
         if getattr(self, "h", None):
             lp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:   # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def batch_options(**kw) -> lp_batch_options:
+    """lp_batch_options with the library defaults, then the given fields."""
+    o = lp_batch_options_init()
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(f"lp_batch_options has no field {k!r}")
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class BatchSolution:
+    status: np.ndarray
+    iters: np.ndarray
+    obj: np.ndarray
+    x: list          # per LP, views into the packed array
+    y: list
+    stats: dict
+
+
+class Batch:
+    """Owns one lp_batch_t: many LPs solved together (one block per LP)."""
+
+    def __init__(self, problems=None, *, m=None, n=None, A=None, b=None, c=None, device=False,
+                 stream=None):
+        if problems is not None:
+            m = np.array([p[0].shape[0] for p in problems], dtype=np.int32)
+            n = np.array([p[0].shape[1] for p in problems], dtype=np.int32)
+            A = np.concatenate([np.ascontiguousarray(p[0], dtype=np.float64).ravel() for p in problems])
+            b = np.concatenate([np.asarray(p[1], dtype=np.float64) for p in problems])
+            c = np.concatenate([np.asarray(p[2], dtype=np.float64) for p in problems])
+        self.m = np.ascontiguousarray(m, dtype=np.int32)
+        self.n = np.ascontiguousarray(n, dtype=np.int32)
+        self.count = len(self.m)
+        self.x_off = np.concatenate([[0], np.cumsum(self.n)]).astype(np.int64)
+        self.y_off = np.concatenate([[0], np.cumsum(self.m)]).astype(np.int64)
+        if device:
+            self._keep = (A, b, c)
+            self.h = lp_batch_create_device(self.count, self.m, self.n, A, b, c, stream)
+        else:
+            self._keep = (np.ascontiguousarray(A, dtype=np.float64),
+                          np.ascontiguousarray(b, dtype=np.float64),
+                          np.ascontiguousarray(c, dtype=np.float64))
+            self.h = lp_batch_create(self.count, self.m, self.n, *self._keep)
+
+    def solve(self, opts: lp_batch_options | None = None) -> None:
+        st = lp_batch_solve(self.h, opts)
+        if st != 0:
+            raise RuntimeError(f"lp_batch_solve failed ({STATUS_NAMES.get(st, st)}): {lp_last_error()}")
+
+    def results(self) -> BatchSolution:
+        status = np.empty(self.count, dtype=np.int32)
+        iters = np.empty(self.count, dtype=np.int64)
+        obj = np.empty(self.count, dtype=np.float64)
+        x = np.empty(int(self.x_off[-1]), dtype=np.float64)
+        y = np.empty(int(self.y_off[-1]), dtype=np.float64)
+        if lp_batch_get(self.h, status, iters, obj, x, y) != 0:
+            raise RuntimeError(lp_last_error())
+        xs = [x[self.x_off[k]:self.x_off[k + 1]] for k in range(self.count)]
+        ys = [y[self.y_off[k]:self.y_off[k + 1]] for k in range(self.count)]
+        return BatchSolution(status, iters, obj, xs, ys, lp_batch_get_stats(self.h).as_dict())
+
+    def tableau(self, k: int) -> np.ndarray:
+        m, n = int(self.m[k]), int(self.n[k])
+        T = np.empty((m + 1, n + m + 1), dtype=np.float64)
+        if lp_batch_get_tableau(self.h, k, T) != 0:
+            raise RuntimeError(lp_last_error())
+        return T
+
+    def close(self):
+        if getattr(self, "h", None):
+            lp_batch_destroy(self.h)
             self.h = None
 
     def __del__(self):

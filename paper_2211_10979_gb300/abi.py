@@ -25,7 +25,9 @@ LP_PREC_FP64, LP_PREC_FP32 = 0, 1
 # every symbol include/tabsimplex.h declares
 EXPORTS = ("lp_options_init", "lp_create", "lp_create_device", "lp_solve", "lp_get_solution",
            "lp_get_tableau", "lp_get_pivot_log", "lp_get_stats", "lp_destroy", "lp_last_error",
-           "lp_set_allocator", "lp_version", "lp_solve_noalloc")
+           "lp_set_allocator", "lp_version", "lp_solve_noalloc", "lp_batch_options_init",
+           "lp_batch_create", "lp_batch_create_device", "lp_batch_solve", "lp_batch_get",
+           "lp_batch_get_tableau", "lp_batch_get_stats", "lp_batch_destroy")
 
 # capacity of the library's fixed work-buffer array used by lp_solve_noalloc
 LP_NOALLOC_SCRATCH_BYTES = 2 * 1024 * 1024
@@ -82,6 +84,39 @@ class lp_stats(ctypes.Structure):
         return d
 
 
+class lp_batch_options(ctypes.Structure):
+    _fields_ = [
+        ("threads", ctypes.c_int),
+        ("rule", ctypes.c_int),
+        ("eps_d", ctypes.c_double),
+        ("eps_p", ctypes.c_double),
+        ("max_iters", ctypes.c_longlong),
+        ("k_cyc", ctypes.c_int),
+        ("use_graph", ctypes.c_int),
+        ("keep_tableaux", ctypes.c_int),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class lp_batch_stats(ctypes.Structure):
+    _fields_ = [
+        ("solve_ms", ctypes.c_double),
+        ("total_pivots", ctypes.c_longlong),
+        ("kernel_launches", ctypes.c_longlong),
+        ("buckets", ctypes.c_int),
+        ("threads", ctypes.c_int * 4),
+        ("lps_per_class", ctypes.c_int * 4),
+        ("tune_ms", ctypes.c_double),
+        ("graph", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["threads"] = list(self.threads)
+        d["lps_per_class"] = list(self.lps_per_class)
+        return d
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -118,6 +153,14 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "lp_solve_noalloc": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp,
                                                 ctypes.c_longlong, vp, ctypes.POINTER(lp_options),
                                                 llp]),
+            "lp_batch_options_init": (None, [ctypes.POINTER(lp_batch_options)]),
+            "lp_batch_create": (vp, [ctypes.c_int, vp, vp, vp, vp, vp]),
+            "lp_batch_create_device": (vp, [ctypes.c_int, vp, vp, vp, vp, vp, vp]),
+            "lp_batch_solve": (ctypes.c_int, [vp, ctypes.POINTER(lp_batch_options)]),
+            "lp_batch_get": (ctypes.c_int, [vp, vp, vp, vp, vp, vp]),
+            "lp_batch_get_tableau": (ctypes.c_int, [vp, ctypes.c_int, vp]),
+            "lp_batch_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(lp_batch_stats)]),
+            "lp_batch_destroy": (None, [vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -221,3 +264,49 @@ def lp_solve_noalloc(m: int, n: int, dA, db, dc, dT, ld: int, dbasis,
 
 def lp_set_allocator(alloc_fn, free_fn, ctx=None) -> int:
     return int(load().lp_set_allocator(alloc_fn, free_fn, ctx))
+
+
+# ------------------------------------------------------------- batched solve
+def lp_batch_options_init() -> lp_batch_options:
+    o = lp_batch_options()
+    load().lp_batch_options_init(ctypes.byref(o))
+    return o
+
+
+def lp_batch_create(count: int, m, n, A, b, c) -> int:
+    """m, n: int32 host arrays; A, b, c: packed float64 host arrays."""
+    h = load().lp_batch_create(int(count), _ptr(m), _ptr(n), _ptr(A), _ptr(b), _ptr(c))
+    if not h:
+        raise ValueError(lp_last_error())
+    return h
+
+
+def lp_batch_create_device(count: int, m, n, dA, db, dc, stream=None) -> int:
+    h = load().lp_batch_create_device(int(count), _ptr(m), _ptr(n), _ptr(dA), _ptr(db), _ptr(dc), stream)
+    if not h:
+        raise ValueError(lp_last_error())
+    return h
+
+
+def lp_batch_solve(h: int, opts: lp_batch_options | None = None) -> int:
+    return int(load().lp_batch_solve(h, ctypes.byref(opts) if opts is not None else None))
+
+
+def lp_batch_get(h: int, status=None, iters=None, obj=None, x=None, y=None) -> int:
+    return int(load().lp_batch_get(h, _ptr(status), _ptr(iters), _ptr(obj), _ptr(x), _ptr(y)))
+
+
+def lp_batch_get_tableau(h: int, index: int, T) -> int:
+    return int(load().lp_batch_get_tableau(h, int(index), _ptr(T)))
+
+
+def lp_batch_get_stats(h: int) -> lp_batch_stats:
+    s = lp_batch_stats()
+    if load().lp_batch_get_stats(h, ctypes.byref(s)) != 0:
+        raise RuntimeError(lp_last_error())
+    return s
+
+
+def lp_batch_destroy(h: int) -> None:
+    if h:
+        load().lp_batch_destroy(h)

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libtabsimplex.so")
-SOURCES = ["tabsimplex.cu"]
+SOURCES = ["tabsimplex.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=default", "-shared"]
@@ -62,14 +62,31 @@ def build(force: bool = False, verbose: bool = False, defines=(), out: str | Non
     target = out or LIB
     if not force and not defines and out is None and up_to_date():
         return LIB
-    tmp = target + f".tmp{os.getpid()}"
-    cmd = [nvcc(), *ARCH, *FLAGS, *[f"-D{d}" for d in defines], "-I", INCLUDE, "-I", CSRC,
-           "-o", tmp, *[os.path.join(CSRC, s) for s in SOURCES]]
-    if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), flush=True)
-    subprocess.run(cmd, check=True)
-    os.replace(tmp, target)
+    tag = f"{os.getpid()}"
+    objdir = os.path.join(PKG, "_build")
+    os.makedirs(objdir, exist_ok=True)
+    compile_flags = [f for f in FLAGS if f != "-shared"]
+    procs, objs = [], []
+    for src in SOURCES:   # translation units compiled in parallel
+        obj = os.path.join(objdir, f"{os.path.splitext(src)[0]}.{tag}.o")
+        cmd = [nvcc(), *ARCH, *compile_flags, *[f"-D{d}" for d in defines], "-I", INCLUDE, "-I", CSRC,
+               "-c", "-o", obj, os.path.join(CSRC, src)]
+        if verbose:
+            cmd.insert(1, "-Xptxas=-v")
+            print(" ".join(cmd), flush=True)
+        procs.append(subprocess.Popen(cmd))
+        objs.append(obj)
+    try:
+        codes = [p.wait() for p in procs]
+        if any(codes):
+            raise subprocess.CalledProcessError(max(codes), "nvcc")
+        tmp = target + f".tmp{tag}"
+        subprocess.run([nvcc(), *ARCH, "-shared", "-Xcompiler", "-fPIC", "-o", tmp, *objs], check=True)
+        os.replace(tmp, target)
+    finally:
+        for obj in objs:
+            if os.path.exists(obj):
+                os.remove(obj)
     return target
 
 

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "tabsimplex.h"
+#include "tsx_host.h"
 #include "tsx_kernels.cuh"
 #include "tsx_recover.cuh"
 
@@ -23,7 +24,7 @@ using namespace tsx;
 // ---------------------------------------------------------------- errors
 static thread_local std::string g_last_error;
 
-static void set_error(const char* fmt, ...) {
+void tsx::set_error(const char* fmt, ...) {
     char buf[512];
     va_list ap;
     va_start(ap, fmt);
@@ -47,6 +48,13 @@ static std::mutex g_alloc_mu;
 static lp_alloc_fn g_alloc = nullptr;
 static lp_free_fn g_free = nullptr;
 static void* g_alloc_ctx = nullptr;
+
+void tsx::current_allocator(lp_alloc_fn* alloc_fn, lp_free_fn* free_fn, void** ctx) {
+    std::lock_guard<std::mutex> lk(g_alloc_mu);
+    *alloc_fn = g_alloc;
+    *free_fn = g_free;
+    *ctx = g_alloc_ctx;
+}
 
 struct Block {
     void* ptr = nullptr;

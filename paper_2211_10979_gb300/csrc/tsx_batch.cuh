@@ -1,0 +1,291 @@
+// Batched solve of many small LPs (the full-tableau simplex of arXiv 2211.10979,
+// Section III, one LP per block, the whole LP in shared memory).
+//
+// Each block keeps the CONDENSED tableau of its LP: the objective row and the m
+// constraint rows over the n nonbasic columns plus the right-hand side, with
+// var[j] = the variable held by column slot j.  The full tableau's basic
+// columns are exact unit vectors (the pivot column becomes e_p exactly, and a
+// basic column's pivot-row entry is zero so later pivots leave it unchanged),
+// so dropping them changes no stored value: at a pivot on (p, slot q) the
+// leaving variable takes slot q, whose new entries are what the full tableau
+// computes for the leaving variable's unit column e_p:
+//     row p:  1 / piv;     row i != p:  fma(-T[i][q], 1 / piv, 0),
+// and every other slot follows Step 3 unchanged.  Ties are broken by the
+// original variable index, so pivots and values equal the full-tableau run.
+// The largest LP of m = n = 128 needs (m+1) x (n+1) doubles = 133 KB.
+#pragma once
+
+#include "tsx_device.cuh"
+
+namespace tsx {
+
+struct BatchLP {              // one LP of the batch
+    int m, n;
+    int ldc;                  // padded row length of the condensed tableau (odd)
+    int bucket;
+    long long a_off;          // offset of A (m x n row-major) in the packed A
+    long long b_off;          // offset of b (and of y) in the packed b / y
+    long long c_off;          // offset of c (and of x) in the packed c / x
+    long long t_off;          // offset of the kept condensed tableau ((m+1) x ldc)
+};
+
+struct BatchParams {
+    const BatchLP* lps;
+    const double* A;
+    const double* b;
+    const double* c;
+    int* status;              // per LP
+    long long* iters;         // per LP
+    double* obj;              // per LP
+    double* x;                // packed like c
+    double* y;                // packed like b
+    double* keepT;            // kept condensed tableaux (null: not kept)
+    int* keepvar;             // kept var maps (packed like c) (null: not kept)
+    int* keepbasis;           // kept basis (packed like b)
+    unsigned long long* total_pivots;
+    double eps_d, eps_p;
+    long long max_iters;      // < 0: 50 (m + n)
+    int k_cyc, rule;
+};
+
+// Shared-memory bytes of one LP's block.
+__host__ __device__ inline size_t batch_smem_bytes(int m, int n, int ldc) {
+    size_t bytes = (size_t)(m + 1) * ldc * 8      // tableau
+                 + (size_t)(m + 1) * 8             // F (pivot column)
+                 + (size_t)ldc * 8                 // R (scaled pivot row)
+                 + (size_t)n * 4 + (size_t)m * 4;  // var, basis
+    return (bytes + 15) / 16 * 16;
+}
+
+struct BArg {                 // entering candidate
+    double v;                 // objective-row entry
+    int var;                  // its variable (tie-break), INT_MAX if none
+    int slot;
+    int fvar;                 // Bland: lowest candidate variable
+    int fslot;
+};
+
+__device__ __forceinline__ void barg_merge(BArg& a, const BArg& b) {
+    if (b.v < a.v || (b.v == a.v && b.var < a.var)) { a.v = b.v; a.var = b.var; a.slot = b.slot; }
+    if (b.fvar < a.fvar) { a.fvar = b.fvar; a.fslot = b.fslot; }
+}
+
+struct BatchScratch {
+    BArg arg[kMaxWarps];
+    RatPart rat[kMaxWarps];
+    BArg arg_out;
+    RatPart rat_out;
+    int lp;
+};
+
+template <int NT>
+__device__ BArg batch_block_arg(BArg a, BatchScratch& s) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        BArg b;
+        b.v = __shfl_xor_sync(0xffffffffu, a.v, o);
+        b.var = __shfl_xor_sync(0xffffffffu, a.var, o);
+        b.slot = __shfl_xor_sync(0xffffffffu, a.slot, o);
+        b.fvar = __shfl_xor_sync(0xffffffffu, a.fvar, o);
+        b.fslot = __shfl_xor_sync(0xffffffffu, a.fslot, o);
+        barg_merge(a, b);
+    }
+    if (NT == 32) return a;
+    __syncthreads();
+    if (lane == 0) s.arg[w] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        BArg r = s.arg[0];
+        for (int k = 1; k < NT / 32; ++k) barg_merge(r, s.arg[k]);
+        s.arg_out = r;
+    }
+    __syncthreads();
+    return s.arg_out;
+}
+
+template <int NT>
+__device__ RatPart batch_block_rat(RatPart a, BatchScratch& s) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    a = warp_rat(a);
+    if (NT == 32) return a;
+    __syncthreads();
+    if (lane == 0) s.rat[w] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        RatPart r = s.rat[0];
+        for (int k = 1; k < NT / 32; ++k) rat_merge(r, s.rat[k]);
+        s.rat_out = r;
+    }
+    __syncthreads();
+    return s.rat_out;
+}
+
+// Solves LP `k` of the batch in shared memory (NT threads).
+template <int NT>
+__device__ void batch_solve_one(const BatchParams& P, int k, unsigned char* smem, BatchScratch& sc) {
+    const BatchLP L = P.lps[k];
+    const int m = L.m, n = L.n, ldc = L.ldc;
+    double* T = reinterpret_cast<double*>(smem);
+    double* F = T + (size_t)(m + 1) * ldc;
+    double* R = F + (m + 1);
+    int* var = reinterpret_cast<int*>(R + ldc);
+    int* basis = var + n;
+    const double* A = P.A + L.a_off;
+    const double* b = P.b + L.b_off;
+    const double* c = P.c + L.c_off;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = NT / 32;
+
+    // Initialization Step: condensed Table I (slack basis), plus input checks
+    int bad = 0;
+    for (int t = tid; t < (m + 1) * ldc; t += NT) {
+        const int i = t / ldc, j = t - i * ldc;
+        double v = 0.0;
+        if (j < n)
+            v = i == 0 ? -c[j] : A[(size_t)(i - 1) * n + j];
+        else if (j == n && i > 0)
+            v = b[i - 1];
+        if (j <= n) bad |= !isfinite(v) || (j == n && i > 0 && !(v >= 0.0));
+        T[t] = v;
+    }
+    for (int j = tid; j < n; j += NT) var[j] = j;
+    for (int i = tid; i < m; i += NT) basis[i] = n + i;
+    bad = __syncthreads_or(bad);
+    const long long cap = P.max_iters < 0 ? 50LL * (m + n) : P.max_iters;
+    int status = kRunning;
+    if (bad) status = -1;   // LP_ERR_INVALID
+    long long it = 0;
+    int bland = P.rule == 1, degen = 0;
+    while (status == kRunning) {
+        // Step 1: entering slot (most negative objective-row entry; ties and
+        // Bland's rule by variable index)
+        BArg a{__longlong_as_double(0x7ff0000000000000LL), INT_MAX, -1, INT_MAX, -1};
+        for (int j = tid; j < n; j += NT) {
+            const double v = T[j];
+            if (v < -P.eps_d) {
+                const int vj = var[j];
+                if (v < a.v || (v == a.v && vj < a.var)) { a.v = v; a.var = vj; a.slot = j; }
+                if (vj < a.fvar) { a.fvar = vj; a.fslot = j; }
+            }
+        }
+        a = batch_block_arg<NT>(a, sc);
+        const int qs = bland ? a.fslot : a.slot;
+        if (qs < 0) { status = kOptimal; break; }
+        if (it >= cap) { status = kIterLimit; break; }
+        // Step 2: minimum ratio on slot qs (ties: row, or basic variable in Bland mode)
+        RatPart best = rat_none();
+        for (int i = 1 + tid; i <= m; i += NT) {
+            const double av = T[(size_t)i * ldc + qs];
+            if (av > P.eps_p) {
+                RatPart cnd;
+                cnd.r = __ddiv_rn(T[(size_t)i * ldc + n], av);
+                cnd.i = i;
+                cnd.key = bland ? basis[i - 1] : i;
+                rat_merge(best, cnd);
+            }
+        }
+        best = batch_block_rat<NT>(best, sc);
+        if (best.i == INT_MAX) { status = kUnbounded; break; }
+        const int p = best.i;
+        const double piv = T[(size_t)p * ldc + qs];
+        if (!isfinite(piv) || !isfinite(best.r)) { status = kNumeric; break; }
+        // Step 3: pivot column and scaled pivot row staged first
+        for (int i = tid; i <= m; i += NT) F[i] = T[(size_t)i * ldc + qs];
+        for (int j = tid; j <= n; j += NT) R[j] = j == qs ? __ddiv_rn(1.0, piv) : __ddiv_rn(T[(size_t)p * ldc + j], piv);
+        __syncthreads();
+        for (int i = warp; i <= m; i += NW) {
+            double* row = T + (size_t)i * ldc;
+            if (i == p) {
+                for (int j = lane; j <= n; j += 32) row[j] = R[j];
+            } else {
+                const double f = F[i];
+                for (int j = lane; j <= n; j += 32) row[j] = __fma_rn(-f, R[j], j == qs ? 0.0 : row[j]);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            const int leaving = basis[p - 1];
+            basis[p - 1] = var[qs];
+            var[qs] = leaving;
+        }
+        ++it;
+        if (P.rule == 0) {
+            if (best.r <= 0.0) {
+                ++degen;
+                if (P.k_cyc > 0 && degen >= P.k_cyc) bland = 1;
+            } else {
+                degen = 0;
+                bland = 0;
+            }
+        }
+        __syncthreads();
+    }
+    // read-out (Table I layout): x from the basis, y from the objective row
+    double* x = P.x + L.c_off;
+    double* y = P.y + L.b_off;
+    for (int j = tid; j < n; j += NT) x[j] = 0.0;
+    for (int i = tid; i < m; i += NT) y[i] = 0.0;
+    __syncthreads();
+    if (status != -1) {
+        for (int i = tid; i < m; i += NT)
+            if (basis[i] < n) x[basis[i]] = T[(size_t)(i + 1) * ldc + n];
+        for (int j = tid; j < n; j += NT)
+            if (var[j] >= n) y[var[j] - n] = T[j];
+    }
+    if (tid == 0) {
+        P.status[k] = status;
+        P.iters[k] = it;
+        P.obj[k] = status == -1 ? 0.0 : T[n];
+        if (it) atomicAdd(P.total_pivots, (unsigned long long)it);
+    }
+    if (P.keepT) {
+        double* kt = P.keepT + L.t_off;
+        for (int t = tid; t < (m + 1) * ldc; t += NT) kt[t] = T[t];
+        for (int j = tid; j < n; j += NT) P.keepvar[L.c_off + j] = var[j];
+        for (int i = tid; i < m; i += NT) P.keepbasis[L.b_off + i] = basis[i];
+    }
+    __syncthreads();
+}
+
+// One bucket: persistent blocks take LPs of `list` from a counter until none is left.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_batch_solve(BatchParams P, const int* __restrict__ list, int count,
+                                                   unsigned* __restrict__ queue) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ BatchScratch sc;
+    for (;;) {
+        if (threadIdx.x == 0) sc.lp = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int t = sc.lp;
+        __syncthreads();
+        if (t >= count) return;
+        batch_solve_one<NT>(P, list[t], smem, sc);
+    }
+}
+
+// Full (m+1) x (n+m+1) tableau of one LP from its kept condensed tableau: the
+// nonbasic columns where var[] puts them, unit columns for the basic variables,
+// the right-hand side last.
+__global__ void k_batch_expand(const BatchLP* lps, int k, const double* keepT, const int* keepvar,
+                               const int* keepbasis, double* out) {
+    const BatchLP L = lps[k];
+    const int m = L.m, n = L.n, W = n + m + 1;
+    const double* T = keepT + L.t_off;
+    const int* var = keepvar + L.c_off;
+    const int* basis = keepbasis + L.b_off;
+    const size_t total = (size_t)(m + 1) * W;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x)
+        out[t] = 0.0;
+    __syncthreads();
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < (size_t)(m + 1) * (n + 1);
+         t += (size_t)gridDim.x * blockDim.x) {
+        const int i = (int)(t / (n + 1)), j = (int)(t - (size_t)i * (n + 1));
+        const int col = j < n ? var[j] : W - 1;
+        out[(size_t)i * W + col] = T[(size_t)i * L.ldc + j];
+    }
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+        out[(size_t)(i + 1) * W + basis[i]] = 1.0;
+}
+
+}  // namespace tsx

@@ -271,7 +271,7 @@ struct BlockScratch {
 };
 
 // Block-wide reductions; every thread returns the block result.
-__device__ ArgPart block_arg(ArgPart a, BlockScratch& s) {
+__device__ inline ArgPart block_arg(ArgPart a, BlockScratch& s) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     a = warp_arg(a);
     __syncthreads();
@@ -286,7 +286,7 @@ __device__ ArgPart block_arg(ArgPart a, BlockScratch& s) {
     return s.arg_out;
 }
 
-__device__ RatPart block_rat(RatPart a, BlockScratch& s) {
+__device__ inline RatPart block_rat(RatPart a, BlockScratch& s) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     a = warp_rat(a);
     __syncthreads();
@@ -309,7 +309,7 @@ __device__ RatPart block_rat(RatPart a, BlockScratch& s) {
 // limit, the block marks the solve LP_ERR_TIMEOUT and returns false; a block
 // that sees a negative status while waiting returns false as well, so every
 // block of a failed solve exits without waiting for the others.
-__device__ bool grid_barrier(DevState* st, long long timeout_ns, BlockScratch& s) {
+__device__ inline bool grid_barrier(DevState* st, long long timeout_ns, BlockScratch& s) {
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {

@@ -1,0 +1,28 @@
+// Host-side helpers shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+
+#include "tabsimplex.h"
+
+namespace tsx {
+
+// Records the thread's last error message (read by lp_last_error).
+void set_error(const char* fmt, ...);
+
+// The device allocator installed with lp_set_allocator (both null: default).
+void current_allocator(lp_alloc_fn* alloc_fn, lp_free_fn* free_fn, void** ctx);
+
+}  // namespace tsx
+
+#define TSX_CUDA_TRY(call, ret)                                                           \
+    do {                                                                                  \
+        cudaError_t e_ = (call);                                                          \
+        if (e_ != cudaSuccess) {                                                          \
+            tsx::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                           __LINE__);                                                     \
+            return ret;                                                                   \
+        }                                                                                 \
+    } while (0)

@@ -1,0 +1,127 @@
+"""Batched solve (one block per LP, condensed tableau in shared memory) vs the
+oracle, LP by LP.  The batch runs the same FP64 method with the same tie rules,
+so every LP's status, pivot count, objective, x and y -- and its full tableau
+rebuilt from the condensed one -- equal the oracle's (tolerance 0).
+"""
+import numpy as np
+import pytest
+
+import lpgen
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def tsx():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_10979_gb300 import build
+    build.build()
+    import paper_2211_10979_gb300 as mod
+    mod.use_torch_allocator()
+    return mod
+
+
+def _problems(shapes, seed0):
+    return [lpgen.dense_lp(m, n, seed0 + k) for k, (m, n) in enumerate(shapes)]
+
+
+def _check(batch_sol, problems, refs, idx=None):
+    for k in (range(len(problems)) if idx is None else idx):
+        ref = refs[k]
+        assert batch_sol.status[k] == ref.status, k
+        assert batch_sol.iters[k] == ref.iters, k
+        assert batch_sol.obj[k] == ref.obj, k
+        np.testing.assert_array_equal(batch_sol.x[k], ref.x)
+        np.testing.assert_array_equal(batch_sol.y[k], ref.y)
+
+
+MIXED = [(1, 1), (1, 9), (9, 1), (3, 4), (16, 16), (17, 31), (31, 17), (40, 64), (64, 40),
+         (100, 128), (128, 100), (128, 128), (77, 91), (5, 120), (120, 5)]
+
+
+@pytest.mark.parametrize("threads", [0, 32, 64, 128, 256])
+def test_mixed_batch_equals_oracle(tsx, threads):
+    problems = _problems(MIXED, 500)
+    refs = [oracle.solve(*p) for p in problems]
+    with tsx.Batch(problems) as bt:
+        bt.solve(tsx.batch_options(threads=threads, keep_tableaux=1))
+        sol = bt.results()
+        _check(sol, problems, refs)
+        for k in (0, 4, 9, 11):
+            np.testing.assert_array_equal(bt.tableau(k), refs[k].T)
+        assert sol.stats["total_pivots"] == sum(r.iters for r in refs)
+
+
+def test_graph_replay_and_direct_launch_agree(tsx):
+    shapes = lpgen.batch_shapes(200, 16, 128, 3)
+    problems = _problems(shapes, 900)
+    refs = [oracle.solve(*p) for p in problems]
+    with tsx.Batch(problems) as bt:
+        for rep in range(3):   # the first solve captures the graph, later ones replay it
+            bt.solve(tsx.batch_options(threads=64))
+            sol = bt.results()
+            assert sol.stats["graph"] == 1
+            _check(sol, problems, refs)
+        bt.solve(tsx.batch_options(threads=64, use_graph=0))
+        _check(bt.results(), problems, refs)
+
+
+def test_config_4096_small_lps(tsx):
+    # the batching workload: 4096 LPs, m and n uniform in [16, 128], FP64
+    shapes = lpgen.batch_shapes(4096, 16, 128, 1)
+    problems = _problems(shapes, 10_000)
+    refs = [oracle.solve(*p) for p in problems]
+    with tsx.Batch(problems) as bt:
+        bt.solve()                     # autotuned threads per size class
+        sol = bt.results()
+    _check(sol, problems, refs)
+    st = sol.stats
+    assert sum(st["lps_per_class"]) == 4096
+    assert all(t in (0, 32, 64, 128, 256) for t in st["threads"])
+
+
+def test_special_lps_inside_a_batch(tsx):
+    cyc = (np.array([[0.5, -5.5, -2.5, 9.0], [0.5, -1.5, -0.5, 1.0], [1.0, 0.0, 0.0, 0.0]]),
+           np.array([0.0, 0.0, 1.0]), np.array([10.0, -57.0, -9.0, -24.0]))
+    unb = (np.array([[1.0, -2.0], [1.0, 0.0]]), np.array([4.0, 3.0]), np.array([0.0, 1.0]))
+    zero = (np.ones((3, 2)), np.array([1.0, 2.0, 3.0]), np.array([-1.0, -1.0]))
+    A0, b0, c0 = lpgen.dense_lp(20, 15, 7)
+    bad = (A0, b0.copy(), c0)
+    bad[1][3] = -1.0
+    ok = lpgen.dense_lp(30, 25, 8)
+    problems = [cyc, unb, zero, bad, ok]
+    with tsx.Batch(problems) as bt:
+        for kw in ({"k_cyc": 3}, {"rule": 1}, {}):
+            bt.solve(tsx.batch_options(**kw))
+            sol = bt.results()
+            for k in (0, 1, 2, 4):
+                ref = oracle.solve(*problems[k], oracle.Options(**kw))
+                assert sol.status[k] == ref.status and sol.iters[k] == ref.iters and sol.obj[k] == ref.obj
+            assert sol.status[3] == tsx.LP_ERR_INVALID
+
+
+def test_device_inputs(tsx):
+    import torch
+    problems = _problems([(20, 30), (50, 10), (64, 64)], 77)
+    refs = [oracle.solve(*p) for p in problems]
+    m = np.array([p[0].shape[0] for p in problems], dtype=np.int32)
+    n = np.array([p[0].shape[1] for p in problems], dtype=np.int32)
+    dA = torch.from_numpy(np.concatenate([p[0].ravel() for p in problems])).cuda()
+    db = torch.from_numpy(np.concatenate([p[1] for p in problems])).cuda()
+    dc = torch.from_numpy(np.concatenate([p[2] for p in problems])).cuda()
+    s = torch.cuda.current_stream().cuda_stream
+    with tsx.Batch(m=m, n=n, A=dA, b=db, c=dc, device=True, stream=s) as bt:
+        bt.solve(tsx.batch_options(stream=s))
+        _check(bt.results(), problems, refs)
+
+
+def test_too_large_for_shared_memory_is_refused(tsx):
+    A, b, c = lpgen.dense_lp(200, 200, 1)
+    with pytest.raises(ValueError, match="shared memory"):
+        tsx.Batch([(A, b, c)])
+    with pytest.raises(ValueError, match="m > 0"):
+        tsx.Batch(m=np.array([0], np.int32), n=np.array([3], np.int32), A=np.zeros(0), b=np.zeros(0),
+                  c=np.zeros(3))
