@@ -52,8 +52,12 @@ def parse_args(argv=None):
     ap.add_argument("--path", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--blocks", type=int, default=0)
-    ap.add_argument("--workload", choices=["single", "batch"], default="single",
-                    help="batch: 4096 small LPs (m, n uniform in [16, 128]) per step")
+    ap.add_argument("--workload", choices=["single", "batch", "serve"], default="single",
+                    help="batch: 4096 small LPs (m, n uniform in [16, 128]) per step; serve: a "
+                         "Poisson stream of LPs (m, n log-uniform in [32, 4096]) through the server")
+    ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
+    ap.add_argument("--serve-seconds", type=float, default=1.0, help="serve: length of the stream")
+    ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--plain-sample", type=int, default=256,
                     help="LPs of the batch solved one at a time for the plain-path figure")
@@ -581,6 +585,95 @@ def run_batch(args, rank, world, local):
     return 0
 
 
+def play_stream(tsx, torch, dev, shapes, arrivals, seeds, server_kw):
+    """Submits each request at its arrival time (inputs generated on the device
+    just before), waits for all, returns per-request (status, latency s, obj)
+    and the server's statistics.  Latency runs from the scheduled arrival."""
+    stream = torch.cuda.Stream(dev)
+    sptr = stream.cuda_stream
+    out = []
+    with tsx.Server(**server_kw) as sv:
+        held = []
+        t0 = time.monotonic()
+        for (m, n), t_arr, sd in zip(shapes, arrivals, seeds):
+            delay = t0 + t_arr - time.monotonic()
+            if delay > 0:
+                time.sleep(delay)
+            dA = torch.empty(m * n, dtype=torch.float64, device=dev)
+            db = torch.empty(m, dtype=torch.float64, device=dev)
+            dc = torch.empty(n, dtype=torch.float64, device=dev)
+            tsx.lp_generate_dense(m, n, sd, dA, db, dc, sptr)
+            stream.synchronize()
+            held.append((sv.submit_device(m, n, dA, db, dc), t0 + t_arr, (dA, db, dc)))
+        for ticket, t_sched, _ in held:
+            sv.wait(ticket)
+            r = sv.result(ticket)
+            out.append((r.status, r.t_done - t_sched, r.obj, r.t_done))
+        st = sv.stats()
+    return out, st, t0
+
+
+def run_serve(args, rank, world, local):
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2211_10979_gb300 as tsx
+    from paper_2211_10979_gb300 import build as tsx_build
+    tsx_build.build()
+    count = max(1, int(args.rate * args.serve_seconds))
+    seed = 5 + rank
+    arrivals = lpgen.poisson_arrivals(count, args.rate, seed)
+    shapes = lpgen.loguniform_shapes(count, 32, 4096, seed)
+    seeds = [100_000 * seed + k for k in range(count)]
+    # warm-up: tune the batched solver and load every kernel once
+    play_stream(tsx, torch, dev, shapes[:64], arrivals[:64] * 0.0, seeds[:64], {"workers": 4})
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    served, st, t0 = play_stream(tsx, torch, dev, shapes, arrivals, seeds,
+                                 {"workers": args.serve_workers})
+    clk = clocks.stop()
+    plain, st_plain, t0p = play_stream(tsx, torch, dev, shapes, arrivals, seeds,
+                                       {"workers": 1, "batch_small": 0})
+
+    def summary(res, t_start):
+        lat = np.array([r[1] for r in res])
+        t_end = max(r[3] for r in res)
+        ok = sum(1 for r in res if r[0] == 0)
+        return {"solves_per_s": len(res) / (t_end - t_start), "optimal": ok,
+                "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+                "mean_ms": float(lat.mean() * 1e3), "max_ms": float(lat.max() * 1e3)}
+
+    s_srv = summary(served, t0)
+    s_pl = summary(plain, t0p)
+    rel = [abs(a[2] - b[2]) / max(1e-300, abs(b[2])) for a, b in zip(served, plain)]
+    line = {
+        "metric": "LPs/s", "value": s_srv["solves_per_s"], "unit": "LPs/s", "n_gpus": world,
+        "steps": 1, "warmup": 1, "ms_per_step": 1e3 * count / s_srv["solves_per_s"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 tableau + f64 recovery (m, n > 128); f64 micro-batches (m, n <= 128)",
+        "data": "synthetic",
+        "config": {"workload": f"Poisson stream, {args.rate:.0f} LPs/s for {args.serve_seconds:.1f} s "
+                               f"({count} LPs), m and n log-uniform in [32, 4096], inputs generated on "
+                               "the device at arrival; continuous batching, 64 GiB admission budget",
+                   "workers": args.serve_workers, "batches": st["batches"], "batched_lps": st["batched_lps"],
+                   "peak_admitted_bytes": st["peak_bytes"]},
+        "latency": {"p50_ms": s_srv["p50_ms"], "p99_ms": s_srv["p99_ms"], "mean_ms": s_srv["mean_ms"],
+                    "max_ms": s_srv["max_ms"], "from": "scheduled arrival to result on the host"},
+        "plain": dict(s_pl, path="one LP at a time in arrival order (1 worker, no micro-batches)"),
+        "speedup_vs_plain": s_srv["solves_per_s"] / s_pl["solves_per_s"],
+        "objective_rel_diff_vs_plain_max": max(rel),
+        "optimal": s_srv["optimal"],
+        "e2e": {"value": s_srv["solves_per_s"], "unit": "LPs/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": int(sum(8 * (m + n + 1) for m, n in shapes)),
+                "note": "inputs are generated on the device at each arrival; results copied to the host"},
+        "roofline": None,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     rank, world, local = dist_env()
@@ -590,6 +683,10 @@ def main(argv=None):
         return run_reference(args, rank, world)
     if args.workload == "batch":
         return run_batch(args, rank, world, local)
+    if args.workload == "serve":
+        if rank != 0:
+            return 0
+        return run_serve(args, rank, world, local)
     return run_gpu(args, rank, world, local)
 
 

@@ -48,7 +48,8 @@ typedef enum {
     LP_ERR_NOMEM = -2,   /* device allocation failed                            */
     LP_ERR_CUDA = -3,    /* a CUDA runtime call failed                          */
     LP_ERR_TIMEOUT = -4, /* a device-wide barrier wait exceeded its time limit  */
-    LP_ERR_STATE = -5    /* call out of order (e.g. solution before a solve)    */
+    LP_ERR_STATE = -5,   /* call out of order (e.g. solution before a solve)    */
+    LP_PENDING = 100     /* lps_wait: the request has not finished yet          */
 } lp_status;
 
 enum { LP_RULE_DANTZIG = 0, LP_RULE_BLAND = 1 };
@@ -272,6 +273,83 @@ lp_status lp_batch_get_stats(lp_batch_t h, lp_batch_stats *stats);
 
 /* Free the batch (NULL is ignored). */
 void lp_batch_destroy(lp_batch_t h);
+
+/* ------------------------------------------------------------------------
+ * Request server with continuous batching.  Requests (one LP each) enter a
+ * FIFO queue; a pool of worker threads, each with its own CUDA stream, admits
+ * them in arrival order while the device-memory budget allows.  LPs with
+ * m, n <= small_max_dim are taken together -- every such request waiting at
+ * that moment, up to batch_max -- and solved as one micro-batch by the batched
+ * solver (FP64, results equal lp_solve's); the others are solved one per
+ * worker by lp_create / lp_solve with the given precision (default FP32
+ * tableau + FP64 recovery).  Requests arriving while others are on the GPU are
+ * admitted as workers and memory free up, and their work overlaps on the
+ * device.  The paper has no serving layer; every solve inside is the method of
+ * lp_solve.
+ * ------------------------------------------------------------------------ */
+typedef struct lp_server *lps_t;
+
+typedef struct {
+    long long budget_bytes;       /* device bytes admitted requests may hold
+                                     (tableau, inputs, work; default 64 GiB)    */
+    int workers;                  /* concurrent solves (default 8)              */
+    int precision;                /* single-LP lane (default LP_PREC_FP32)      */
+    int batch_small;              /* 1 (default): micro-batch the small LPs     */
+    int batch_max;                /* max LPs per micro-batch (default 1024)     */
+    int small_max_dim;            /* small: m, n <= this (default 128)          */
+} lps_options;
+
+typedef struct {
+    long long submitted, completed;
+    double wall_s;                /* first submit to last completion            */
+    double lat_p50_ms, lat_p99_ms, lat_mean_ms, lat_max_ms;   /* submit -> done */
+    double queue_p50_ms, queue_p99_ms;                        /* submit -> admit*/
+    long long batches, batched_lps;
+    long long peak_bytes;         /* largest admitted total                     */
+} lps_stats;
+
+void lps_options_init(lps_options *opt);
+
+/* Start a server on the current device (worker threads start at once).
+ * NULL opt = defaults.  Returns NULL on error. */
+lps_t lps_open(const lps_options *opt);
+
+/* Submit an LP from HOST arrays (copied before return).  Returns a ticket
+ * (>= 0) or -1 on error (bad sizes, larger than the budget, closing). */
+long long lps_submit(lps_t sv, int m, int n, const double *A, const double *b, const double *c);
+
+/* Submit an LP whose arrays are on the device (referenced: they must stay
+ * valid and unchanged until the request finishes; their contents must be
+ * complete when this is called). */
+long long lps_submit_device(lps_t sv, int m, int n, const double *dA, const double *db,
+                            const double *dc);
+
+/* Wait for a request: its status once finished, or LP_PENDING after
+ * timeout_s seconds (timeout_s < 0: no limit). */
+int lps_wait(lps_t sv, long long ticket, double timeout_s);
+
+/* Result of a finished request to HOST arrays (any may be NULL): x (n), y (m),
+ * objective, pivots; times[3] = submit, admit, done (seconds of a monotonic
+ * clock).  Returns the request's status, LP_ERR_STATE if unfinished. */
+lp_status lps_result(lps_t sv, long long ticket, double *x, double *y, double *obj,
+                     long long *iters, double *times);
+
+/* Forget a finished request (frees its stored result). */
+lp_status lps_release(lps_t sv, long long ticket);
+
+lp_status lps_get_stats(lps_t sv, lps_stats *stats);
+
+/* Finish every queued request, stop the workers, free the server. */
+void lps_close(lps_t sv);
+
+/* Seeded synthetic LP written on the device (inputs for tests and benchmarks,
+ * not part of the method): the dense generator A_ij = 1 + 9u,
+ * b_i = 100 + 900u, c_j = 1 + 9u with u from the counter-based SplitMix64
+ * stream of `seed` (draws in the order A row-major, b, c), identical to the
+ * Python generator lpgen.dense_lp.  dA (m x n), db (m), dc (n) are device
+ * arrays; runs on `stream`. */
+lp_status lp_generate_dense(int m, int n, unsigned long long seed, double *dA, double *db,
+                            double *dc, void *stream);
 
 /* Solve without allocating any device memory.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory

@@ -21,11 +21,13 @@ from .abi import (LP_ERR_CUDA, LP_ERR_INVALID, LP_ERR_NOMEM, LP_ERR_NUMERIC, LP_
                   lp_set_allocator, lp_solve, lp_solve_noalloc, lp_stats, lp_version,
                   lp_batch_options, lp_batch_options_init, lp_batch_create, lp_batch_create_device,
                   lp_batch_solve, lp_batch_get, lp_batch_get_tableau, lp_batch_get_stats,
-                  lp_batch_destroy)
+                  lp_batch_destroy, LP_PENDING, lps_options, lps_options_init, lps_open, lps_submit,
+                  lps_submit_device, lps_wait, lps_result, lps_release, lps_get_stats, lps_close,
+                  lp_generate_dense)
 
 __all__ = [n for n in dir(abi) if n.startswith(("lp_", "LP_"))] + [
     "STATUS_NAMES", "Solution", "Problem", "solve", "use_torch_allocator", "options",
-    "Batch", "BatchSolution", "batch_options"]
+    "Batch", "BatchSolution", "batch_options", "Server", "ServedResult", "server_options"]
 
 _torch_hooks = None
 
@@ -212,6 +214,84 @@ class Batch:
     def close(self):
         if getattr(self, "h", None):
             lp_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:   # noqa: BLE001 - interpreter shutdown
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def server_options(**kw) -> lps_options:
+    """lps_options with the library defaults, then the given fields."""
+    o = lps_options_init()
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(f"lps_options has no field {k!r}")
+        setattr(o, k, v)
+    return o
+
+
+@dataclass
+class ServedResult:
+    status: int
+    iters: int
+    x: np.ndarray
+    y: np.ndarray
+    obj: float
+    t_submit: float
+    t_admit: float
+    t_done: float
+
+
+class Server:
+    """Owns one lps_t (request server with continuous batching)."""
+
+    def __init__(self, **opts):
+        self.h = lps_open(server_options(**opts))
+        self.shapes = {}
+
+    def submit(self, A, b, c) -> int:
+        A = np.ascontiguousarray(A, dtype=np.float64)
+        m, n = A.shape
+        t = lps_submit(self.h, m, n, A, np.ascontiguousarray(b, dtype=np.float64),
+                       np.ascontiguousarray(c, dtype=np.float64))
+        self.shapes[t] = (m, n)
+        return t
+
+    def submit_device(self, m, n, dA, db, dc) -> int:
+        t = lps_submit_device(self.h, m, n, dA, db, dc)
+        self.shapes[t] = (m, n)
+        return t
+
+    def wait(self, ticket, timeout_s=-1.0) -> int:
+        return lps_wait(self.h, ticket, timeout_s)
+
+    def result(self, ticket, release=True) -> ServedResult:
+        m, n = self.shapes[ticket]
+        x = np.empty(n)
+        y = np.empty(m)
+        obj = np.empty(1)
+        times = np.empty(3)
+        st, it = lps_result(self.h, ticket, x, y, obj, times)
+        if release:
+            lps_release(self.h, ticket)
+            del self.shapes[ticket]
+        return ServedResult(st, it, x, y, float(obj[0]), *times.tolist())
+
+    def stats(self) -> dict:
+        return lps_get_stats(self.h).as_dict()
+
+    def close(self):
+        if getattr(self, "h", None):
+            lps_close(self.h)
             self.h = None
 
     def __del__(self):

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(PKG, "libtabsimplex.so")
 LP_OPTIMAL, LP_UNBOUNDED, LP_ITER_LIMIT, LP_ERR_NUMERIC = 0, 1, 2, 3
 LP_ERR_INVALID, LP_ERR_NOMEM, LP_ERR_CUDA, LP_ERR_TIMEOUT, LP_ERR_STATE = -1, -2, -3, -4, -5
 STATUS_NAMES = {0: "OPTIMAL", 1: "UNBOUNDED", 2: "ITER_LIMIT", 3: "NUMERIC", -1: "INVALID",
-                -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE"}
+                -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE", 100: "PENDING"}
 LP_RULE_DANTZIG, LP_RULE_BLAND = 0, 1
 LP_PATH_AUTO, LP_PATH_PERSISTENT, LP_PATH_MULTILAUNCH = 0, 1, 2
 LP_PREC_FP64, LP_PREC_FP32 = 0, 1
@@ -27,7 +27,10 @@ EXPORTS = ("lp_options_init", "lp_create", "lp_create_device", "lp_solve", "lp_g
            "lp_get_tableau", "lp_get_pivot_log", "lp_get_stats", "lp_destroy", "lp_last_error",
            "lp_set_allocator", "lp_version", "lp_solve_noalloc", "lp_batch_options_init",
            "lp_batch_create", "lp_batch_create_device", "lp_batch_solve", "lp_batch_get",
-           "lp_batch_get_tableau", "lp_batch_get_stats", "lp_batch_destroy")
+           "lp_batch_get_tableau", "lp_batch_get_stats", "lp_batch_destroy", "lps_options_init",
+           "lps_open", "lps_submit", "lps_submit_device", "lps_wait", "lps_result", "lps_release",
+           "lps_get_stats", "lps_close", "lp_generate_dense")
+LP_PENDING = 100
 
 # capacity of the library's fixed work-buffer array used by lp_solve_noalloc
 LP_NOALLOC_SCRATCH_BYTES = 2 * 1024 * 1024
@@ -117,6 +120,37 @@ class lp_batch_stats(ctypes.Structure):
         return d
 
 
+class lps_options(ctypes.Structure):
+    _fields_ = [
+        ("budget_bytes", ctypes.c_longlong),
+        ("workers", ctypes.c_int),
+        ("precision", ctypes.c_int),
+        ("batch_small", ctypes.c_int),
+        ("batch_max", ctypes.c_int),
+        ("small_max_dim", ctypes.c_int),
+    ]
+
+
+class lps_stats(ctypes.Structure):
+    _fields_ = [
+        ("submitted", ctypes.c_longlong),
+        ("completed", ctypes.c_longlong),
+        ("wall_s", ctypes.c_double),
+        ("lat_p50_ms", ctypes.c_double),
+        ("lat_p99_ms", ctypes.c_double),
+        ("lat_mean_ms", ctypes.c_double),
+        ("lat_max_ms", ctypes.c_double),
+        ("queue_p50_ms", ctypes.c_double),
+        ("queue_p99_ms", ctypes.c_double),
+        ("batches", ctypes.c_longlong),
+        ("batched_lps", ctypes.c_longlong),
+        ("peak_bytes", ctypes.c_longlong),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 
@@ -161,6 +195,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "lp_batch_get_tableau": (ctypes.c_int, [vp, ctypes.c_int, vp]),
             "lp_batch_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(lp_batch_stats)]),
             "lp_batch_destroy": (None, [vp]),
+            "lps_options_init": (None, [ctypes.POINTER(lps_options)]),
+            "lps_open": (vp, [ctypes.POINTER(lps_options)]),
+            "lps_submit": (ctypes.c_longlong, [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]),
+            "lps_submit_device": (ctypes.c_longlong, [vp, ctypes.c_int, ctypes.c_int, vp, vp, vp]),
+            "lps_wait": (ctypes.c_int, [vp, ctypes.c_longlong, ctypes.c_double]),
+            "lps_result": (ctypes.c_int, [vp, ctypes.c_longlong, vp, vp, vp, llp, vp]),
+            "lps_release": (ctypes.c_int, [vp, ctypes.c_longlong]),
+            "lps_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(lps_stats)]),
+            "lps_close": (None, [vp]),
+            "lp_generate_dense": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -310,3 +354,61 @@ def lp_batch_get_stats(h: int) -> lp_batch_stats:
 def lp_batch_destroy(h: int) -> None:
     if h:
         load().lp_batch_destroy(h)
+
+
+# ------------------------------------------------------------- request server
+def lps_options_init() -> lps_options:
+    o = lps_options()
+    load().lps_options_init(ctypes.byref(o))
+    return o
+
+
+def lps_open(opts: lps_options | None = None) -> int:
+    h = load().lps_open(ctypes.byref(opts) if opts is not None else None)
+    if not h:
+        raise RuntimeError(lp_last_error())
+    return h
+
+
+def lps_submit(sv: int, m: int, n: int, A, b, c) -> int:
+    t = load().lps_submit(sv, int(m), int(n), _ptr(A), _ptr(b), _ptr(c))
+    if t < 0:
+        raise ValueError(lp_last_error())
+    return int(t)
+
+
+def lps_submit_device(sv: int, m: int, n: int, dA, db, dc) -> int:
+    t = load().lps_submit_device(sv, int(m), int(n), _ptr(dA), _ptr(db), _ptr(dc))
+    if t < 0:
+        raise ValueError(lp_last_error())
+    return int(t)
+
+
+def lps_wait(sv: int, ticket: int, timeout_s: float = -1.0) -> int:
+    return int(load().lps_wait(sv, int(ticket), float(timeout_s)))
+
+
+def lps_result(sv: int, ticket: int, x=None, y=None, obj=None, times=None):
+    it = ctypes.c_longlong(0)
+    st = load().lps_result(sv, int(ticket), _ptr(x), _ptr(y), _ptr(obj), ctypes.byref(it), _ptr(times))
+    return int(st), int(it.value)
+
+
+def lps_release(sv: int, ticket: int) -> int:
+    return int(load().lps_release(sv, int(ticket)))
+
+
+def lps_get_stats(sv: int) -> lps_stats:
+    s = lps_stats()
+    if load().lps_get_stats(sv, ctypes.byref(s)) != 0:
+        raise RuntimeError(lp_last_error())
+    return s
+
+
+def lps_close(sv: int) -> None:
+    if sv:
+        load().lps_close(sv)
+
+
+def lp_generate_dense(m: int, n: int, seed: int, dA, db, dc, stream=None) -> int:
+    return int(load().lp_generate_dense(int(m), int(n), int(seed), _ptr(dA), _ptr(db), _ptr(dc), stream))

@@ -1,0 +1,467 @@
+// Request server for LP solves with continuous batching (lps_* in
+// include/tabsimplex.h), and the device-side seeded input generator.
+//
+// Requests enter a FIFO queue.  A pool of worker threads (each with its own
+// CUDA stream) takes work as soon as a worker is free and the device-memory
+// budget allows: LPs small enough for the batched solver are taken together --
+// every small request waiting at that moment, up to batch_max -- and solved as
+// one micro-batch (lp_batch_*); the others are solved one per worker through
+// the single-LP path (lp_create / lp_solve, FP32 + FP64 recovery by default).
+// Requests that arrive while others are on the GPU join the next micro-batch
+// or the next free worker, so their work overlaps on the device.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "tabsimplex.h"
+#include "tsx_host.h"
+
+using namespace tsx;
+
+// ------------------------------------------------------------- generator
+// The seeded dense LP of the benchmarks (the same definition as the Python
+// generator lpgen.dense_lp): draw k of seed s is SplitMix64's output function
+// applied to s + (k + 1) * 0x9E3779B97F4A7C15; u = (x >> 11) * 2^-53; draws in
+// the order A (row-major), b, c; A_ij = 1 + 9u, b_i = 100 + 900u, c_j = 1 + 9u
+// (product rounded, then the sum: no fused multiply-add).
+__device__ __forceinline__ double gen_u01(unsigned long long seed, unsigned long long k) {
+    unsigned long long z = seed + (k + 1ull) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return (double)(z >> 11) * 0x1.0p-53;
+}
+
+__global__ void k_generate_dense(int m, int n, unsigned long long seed, double* __restrict__ A,
+                                 double* __restrict__ b, double* __restrict__ c) {
+    const unsigned long long mn = (unsigned long long)m * n;
+    const unsigned long long total = mn + m + n;
+    for (unsigned long long k = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; k < total;
+         k += (unsigned long long)gridDim.x * blockDim.x) {
+        const double u = gen_u01(seed, k);
+        if (k < mn)
+            A[k] = __dadd_rn(1.0, __dmul_rn(9.0, u));
+        else if (k < mn + m)
+            b[k - mn] = __dadd_rn(100.0, __dmul_rn(900.0, u));
+        else
+            c[k - mn - m] = __dadd_rn(1.0, __dmul_rn(9.0, u));
+    }
+}
+
+lp_status lp_generate_dense(int m, int n, unsigned long long seed, double* dA, double* db, double* dc,
+                            void* stream) {
+    if (m <= 0 || n <= 0 || !dA || !db || !dc) {
+        set_error("lp_generate_dense: need m, n > 0 and three device arrays");
+        return LP_ERR_INVALID;
+    }
+    const unsigned long long total = (unsigned long long)m * n + m + n;
+    const int grid = (int)std::min<unsigned long long>((total + 255) / 256, 152ull * 32);
+    k_generate_dense<<<grid, 256, 0, (cudaStream_t)stream>>>(m, n, seed, dA, db, dc);
+    TSX_CUDA_TRY(cudaGetLastError(), LP_ERR_CUDA);
+    return LP_OPTIMAL;
+}
+
+// ---------------------------------------------------------------- server
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+double seconds(Clock::time_point t) {
+    return std::chrono::duration<double>(t.time_since_epoch()).count();
+}
+
+struct Request {
+    long long id = 0;
+    int m = 0, n = 0;
+    std::vector<double> hA, hb, hc;       // host inputs (lps_submit)
+    const double *dA = nullptr, *db = nullptr, *dc = nullptr;   // device inputs
+    bool on_device = false;
+    size_t bytes = 0;                     // device memory held while admitted
+    bool small = false;
+    int status = 100;                     // running until done
+    long long iters = 0;
+    double obj = 0.0;
+    std::vector<double> x, y;
+    Clock::time_point t_submit, t_admit, t_done;
+    bool done = false;
+};
+
+// Device bytes a request holds while it is solved.
+size_t request_bytes(int m, int n, bool small, int precision) {
+    const size_t in = 8ull * ((size_t)m * n + m + n);
+    if (small) return in + 64ull * (m + n) + 4096;
+    const size_t W = (size_t)n + m + 1;
+    const size_t elem = precision == LP_PREC_FP32 ? 4 : 8;
+    const size_t ld = (W + 31) / 32 * 32;
+    const size_t tab = (size_t)(m + 1) * ld * elem + (size_t)(m + 1 + 2 * ld) * elem;
+    return in + tab + 64ull * (m + n) + (1ull << 20);
+}
+
+}  // namespace
+
+struct lp_server {
+    lps_options opt{};
+    int device = 0;
+    std::mutex mu;
+    std::condition_variable cv_work;      // workers wait for requests
+    std::condition_variable cv_done;      // clients wait for results
+    std::deque<std::shared_ptr<Request>> queue;
+    std::unordered_map<long long, std::shared_ptr<Request>> all;
+    std::vector<std::thread> workers;
+    std::vector<double> lat_ms, queue_ms;
+    long long next_id = 0;
+    long long used = 0, peak = 0;
+    long long submitted = 0, completed = 0, batches = 0, batched_lps = 0;
+    bool stopping = false;
+    bool started = false;
+    Clock::time_point t_first, t_last;
+};
+
+void lps_options_init(lps_options* o) {
+    if (!o) return;
+    memset(o, 0, sizeof *o);
+    o->budget_bytes = 64ll << 30;
+    o->workers = 8;
+    o->precision = LP_PREC_FP32;
+    o->batch_small = 1;
+    o->batch_max = 1024;
+    o->small_max_dim = 128;
+}
+
+// Solves one single-path request on the calling worker thread.
+static void solve_single(lp_server* sv, Request& r, cudaStream_t s) {
+    lp_t h = r.on_device ? lp_create_device(r.m, r.n, r.dA, r.db, r.dc, (void*)s)
+                         : lp_create(r.m, r.n, r.hA.data(), r.hb.data(), r.hc.data());
+    if (!h) {
+        r.status = LP_ERR_INVALID;
+        return;
+    }
+    lp_options o;
+    lp_options_init(&o);
+    o.precision = sv->opt.precision;
+    o.stream = r.on_device ? (void*)s : nullptr;
+    r.status = lp_solve(h, &o);
+    r.x.assign(r.n, 0.0);
+    r.y.assign(r.m, 0.0);
+    long long it = 0;
+    if (r.status >= 0) lp_get_solution(h, r.x.data(), r.y.data(), &r.obj, nullptr, &it);
+    r.iters = it;
+    lp_destroy(h);
+}
+
+// Solves a micro-batch of small requests on the calling worker thread.
+static void solve_batch(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs, cudaStream_t s) {
+    const int count = (int)rs.size();
+    std::vector<int> m(count), n(count);
+    size_t smn = 0, sm = 0, sn = 0;
+    for (int k = 0; k < count; ++k) {
+        m[k] = rs[k]->m;
+        n[k] = rs[k]->n;
+        smn += (size_t)m[k] * n[k];
+        sm += m[k];
+        sn += n[k];
+    }
+    // pack the inputs on the device (host requests: H2D, device requests: D2D)
+    double* pack = nullptr;
+    const size_t bytes = 8 * (smn + sm + sn);
+    auto fail = [&](int st) {
+        for (auto& r : rs) r->status = st;
+    };
+    if (cudaMallocAsync((void**)&pack, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        fail(LP_ERR_NOMEM);
+        return;
+    }
+    double *pA = pack, *pb = pack + smn, *pc = pb + sm;
+    size_t oa = 0, ob = 0, oc = 0;
+    bool ok = true;
+    for (auto& rp : rs) {
+        Request& r = *rp;
+        const size_t a = (size_t)r.m * r.n;
+        const cudaMemcpyKind kind = r.on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        ok = ok && cudaMemcpyAsync(pA + oa, r.on_device ? (const void*)r.dA : r.hA.data(), 8 * a, kind, s) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(pb + ob, r.on_device ? (const void*)r.db : r.hb.data(), 8ull * r.m, kind, s) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(pc + oc, r.on_device ? (const void*)r.dc : r.hc.data(), 8ull * r.n, kind, s) == cudaSuccess;
+        oa += a;
+        ob += r.m;
+        oc += r.n;
+    }
+    lp_batch_t h = ok ? lp_batch_create_device(count, m.data(), n.data(), pA, pb, pc, (void*)s) : nullptr;
+    if (!h) {
+        fail(LP_ERR_INVALID);
+        cudaFreeAsync(pack, s);
+        cudaStreamSynchronize(s);
+        return;
+    }
+    lp_batch_options bo;
+    lp_batch_options_init(&bo);
+    bo.stream = (void*)s;
+    std::vector<int> st(count);
+    std::vector<long long> it(count);
+    std::vector<double> obj(count), x(sn), y(sm);
+    if (lp_batch_solve(h, &bo) == LP_OPTIMAL &&
+        lp_batch_get(h, st.data(), it.data(), obj.data(), x.data(), y.data()) == LP_OPTIMAL) {
+        size_t xo = 0, yo = 0;
+        for (int k = 0; k < count; ++k) {
+            Request& r = *rs[k];
+            r.status = st[k];
+            r.iters = it[k];
+            r.obj = obj[k];
+            r.x.assign(x.begin() + xo, x.begin() + xo + r.n);
+            r.y.assign(y.begin() + yo, y.begin() + yo + r.m);
+            xo += r.n;
+            yo += r.m;
+        }
+    } else {
+        fail(LP_ERR_CUDA);
+    }
+    lp_batch_destroy(h);
+    cudaFreeAsync(pack, s);
+    cudaStreamSynchronize(s);
+    std::lock_guard<std::mutex> lk(sv->mu);
+    ++sv->batches;
+    sv->batched_lps += count;
+}
+
+static void worker_main(lp_server* sv) {
+    cudaSetDevice(sv->device);
+    use_default_allocator(true);
+    cudaStream_t s = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    for (;;) {
+        std::vector<std::shared_ptr<Request>> take;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            // strict arrival order: the head is admitted first once the budget
+            // allows; small requests queued right behind it join its micro-batch
+            sv->cv_work.wait(lk, [&] {
+                return sv->stopping || (!sv->queue.empty() &&
+                                        sv->used + (long long)sv->queue.front()->bytes <= sv->opt.budget_bytes);
+            });
+            if (sv->queue.empty()) {
+                if (sv->stopping) break;
+                continue;
+            }
+            auto head = sv->queue.front();
+            sv->queue.pop_front();
+            sv->used += (long long)head->bytes;
+            take.push_back(head);
+            if (head->small && sv->opt.batch_small) {
+                for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)take.size() < sv->opt.batch_max;) {
+                    if ((*it)->small && sv->used + (long long)(*it)->bytes <= sv->opt.budget_bytes) {
+                        sv->used += (long long)(*it)->bytes;
+                        take.push_back(*it);
+                        it = sv->queue.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+            }
+            sv->peak = std::max(sv->peak, sv->used);
+            const auto now = Clock::now();
+            for (auto& r : take) r->t_admit = now;
+        }
+        if (take.size() == 1 && !(take[0]->small && sv->opt.batch_small))
+            solve_single(sv, *take[0], s);
+        else
+            solve_batch(sv, take, s);
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            const auto now = Clock::now();
+            for (auto& r : take) {
+                r->t_done = now;
+                r->done = true;
+                sv->used -= (long long)r->bytes;
+                ++sv->completed;
+                sv->lat_ms.push_back(1e3 * std::chrono::duration<double>(r->t_done - r->t_submit).count());
+                sv->queue_ms.push_back(1e3 * std::chrono::duration<double>(r->t_admit - r->t_submit).count());
+                r->hA.clear();
+                r->hA.shrink_to_fit();
+                r->hb.clear();
+                r->hc.clear();
+            }
+            sv->t_last = now;
+        }
+        sv->cv_done.notify_all();
+        sv->cv_work.notify_all();
+    }
+    cudaStreamDestroy(s);
+}
+
+lps_t lps_open(const lps_options* opt) {
+    lp_server* sv = new lp_server();
+    if (opt)
+        sv->opt = *opt;
+    else
+        lps_options_init(&sv->opt);
+    if (sv->opt.workers <= 0 || sv->opt.budget_bytes <= 0 || sv->opt.batch_max <= 0 || sv->opt.precision < 0 ||
+        sv->opt.precision > 1) {
+        set_error("lps_open: invalid options");
+        delete sv;
+        return nullptr;
+    }
+    cudaGetDevice(&sv->device);
+    for (int w = 0; w < sv->opt.workers; ++w) sv->workers.emplace_back(worker_main, sv);
+    return sv;
+}
+
+static long long enqueue(lp_server* sv, std::shared_ptr<Request> r) {
+    r->small = sv->opt.batch_small && r->m <= sv->opt.small_max_dim && r->n <= sv->opt.small_max_dim;
+    r->bytes = request_bytes(r->m, r->n, r->small, sv->opt.precision);
+    if ((long long)r->bytes > sv->opt.budget_bytes) {
+        set_error("lps_submit: request needs %zu bytes, more than the budget", r->bytes);
+        return -1;
+    }
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        if (sv->stopping) {
+            set_error("lps_submit: server is closing");
+            return -1;
+        }
+        r->id = sv->next_id++;
+        r->t_submit = Clock::now();
+        if (!sv->started) {
+            sv->started = true;
+            sv->t_first = r->t_submit;
+        }
+        sv->all[r->id] = r;
+        sv->queue.push_back(r);
+        ++sv->submitted;
+    }
+    sv->cv_work.notify_one();
+    return r->id;
+}
+
+long long lps_submit(lps_t sv, int m, int n, const double* A, const double* b, const double* c) {
+    if (!sv || m <= 0 || n <= 0 || !A || !b || !c) {
+        set_error("lps_submit: bad argument");
+        return -1;
+    }
+    auto r = std::make_shared<Request>();
+    r->m = m;
+    r->n = n;
+    r->hA.assign(A, A + (size_t)m * n);
+    r->hb.assign(b, b + m);
+    r->hc.assign(c, c + n);
+    return enqueue(sv, r);
+}
+
+long long lps_submit_device(lps_t sv, int m, int n, const double* dA, const double* db, const double* dc) {
+    if (!sv || m <= 0 || n <= 0 || !dA || !db || !dc) {
+        set_error("lps_submit_device: bad argument");
+        return -1;
+    }
+    auto r = std::make_shared<Request>();
+    r->m = m;
+    r->n = n;
+    r->dA = dA;
+    r->db = db;
+    r->dc = dc;
+    r->on_device = true;
+    return enqueue(sv, r);
+}
+
+int lps_wait(lps_t sv, long long ticket, double timeout_s) {
+    if (!sv) return LP_ERR_INVALID;
+    std::unique_lock<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) {
+        set_error("lps_wait: unknown ticket %lld", ticket);
+        return LP_ERR_INVALID;
+    }
+    auto r = it->second;
+    const auto pred = [&] { return r->done; };
+    if (timeout_s < 0)
+        sv->cv_done.wait(lk, pred);
+    else if (!sv->cv_done.wait_for(lk, std::chrono::duration<double>(timeout_s), pred))
+        return 100;
+    return r->status;
+}
+
+lp_status lps_result(lps_t sv, long long ticket, double* x, double* y, double* obj, long long* iters,
+                     double* times) {
+    if (!sv) return LP_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end()) {
+        set_error("lps_result: unknown ticket %lld", ticket);
+        return LP_ERR_INVALID;
+    }
+    Request& r = *it->second;
+    if (!r.done) {
+        set_error("lps_result: request %lld is not finished", ticket);
+        return LP_ERR_STATE;
+    }
+    if (x && !r.x.empty()) memcpy(x, r.x.data(), sizeof(double) * r.n);
+    if (y && !r.y.empty()) memcpy(y, r.y.data(), sizeof(double) * r.m);
+    if (obj) *obj = r.obj;
+    if (iters) *iters = r.iters;
+    if (times) {
+        times[0] = seconds(r.t_submit);
+        times[1] = seconds(r.t_admit);
+        times[2] = seconds(r.t_done);
+    }
+    return (lp_status)r.status;
+}
+
+lp_status lps_release(lps_t sv, long long ticket) {
+    if (!sv) return LP_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    auto it = sv->all.find(ticket);
+    if (it == sv->all.end() || !it->second->done) {
+        set_error("lps_release: unknown or unfinished ticket %lld", ticket);
+        return LP_ERR_STATE;
+    }
+    sv->all.erase(it);
+    return LP_OPTIMAL;
+}
+
+static double percentile(std::vector<double> v, double q) {
+    if (v.empty()) return 0.0;
+    std::sort(v.begin(), v.end());
+    const double pos = q * (double)(v.size() - 1);
+    const size_t lo = (size_t)pos;
+    const size_t hi = std::min(lo + 1, v.size() - 1);
+    return v[lo] + (v[hi] - v[lo]) * (pos - (double)lo);
+}
+
+lp_status lps_get_stats(lps_t sv, lps_stats* st) {
+    if (!sv || !st) return LP_ERR_INVALID;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    memset(st, 0, sizeof *st);
+    st->submitted = sv->submitted;
+    st->completed = sv->completed;
+    st->wall_s = sv->completed ? std::chrono::duration<double>(sv->t_last - sv->t_first).count() : 0.0;
+    st->lat_p50_ms = percentile(sv->lat_ms, 0.50);
+    st->lat_p99_ms = percentile(sv->lat_ms, 0.99);
+    st->lat_max_ms = sv->lat_ms.empty() ? 0.0 : *std::max_element(sv->lat_ms.begin(), sv->lat_ms.end());
+    double sum = 0.0;
+    for (double v : sv->lat_ms) sum += v;
+    st->lat_mean_ms = sv->lat_ms.empty() ? 0.0 : sum / (double)sv->lat_ms.size();
+    st->queue_p50_ms = percentile(sv->queue_ms, 0.50);
+    st->queue_p99_ms = percentile(sv->queue_ms, 0.99);
+    st->batches = sv->batches;
+    st->batched_lps = sv->batched_lps;
+    st->peak_bytes = sv->peak;
+    return LP_OPTIMAL;
+}
+
+void lps_close(lps_t sv) {
+    if (!sv) return;
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->stopping = true;
+    }
+    sv->cv_work.notify_all();
+    for (auto& t : sv->workers) t.join();
+    delete sv;
+}

@@ -49,7 +49,17 @@ static lp_alloc_fn g_alloc = nullptr;
 static lp_free_fn g_free = nullptr;
 static void* g_alloc_ctx = nullptr;
 
+static thread_local bool t_default_alloc = false;
+
+void tsx::use_default_allocator(bool on) { t_default_alloc = on; }
+
 void tsx::current_allocator(lp_alloc_fn* alloc_fn, lp_free_fn* free_fn, void** ctx) {
+    if (t_default_alloc) {
+        *alloc_fn = nullptr;
+        *free_fn = nullptr;
+        *ctx = nullptr;
+        return;
+    }
     std::lock_guard<std::mutex> lk(g_alloc_mu);
     *alloc_fn = g_alloc;
     *free_fn = g_free;
@@ -237,12 +247,7 @@ static lp_handle* create_common(int m, int n, cudaStream_t stream, bool own_stre
     h->n = n;
     h->W = n + m + 1;
     cudaGetDevice(&h->device);
-    {
-        std::lock_guard<std::mutex> lk(g_alloc_mu);
-        h->alloc = g_alloc;
-        h->dealloc = g_free;
-        h->alloc_ctx = g_alloc_ctx;
-    }
+    current_allocator(&h->alloc, &h->dealloc, &h->alloc_ctx);
     if (own_stream) {
         if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
             set_error("lp_create: cudaStreamCreate failed: %s", cudaGetErrorString(cudaGetLastError()));

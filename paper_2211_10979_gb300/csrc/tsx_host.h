@@ -12,8 +12,13 @@ namespace tsx {
 // Records the thread's last error message (read by lp_last_error).
 void set_error(const char* fmt, ...);
 
-// The device allocator installed with lp_set_allocator (both null: default).
+// The device allocator installed with lp_set_allocator (both null: default);
+// null on threads that asked for the default with use_default_allocator.
 void current_allocator(lp_alloc_fn* alloc_fn, lp_free_fn* free_fn, void** ctx);
+
+// Handles created on the calling thread ignore lp_set_allocator's hook and use
+// cudaMallocAsync / cudaFreeAsync (the request server's worker threads).
+void use_default_allocator(bool on);
 
 }  // namespace tsx
 
