@@ -58,6 +58,7 @@ def parse_args(argv=None):
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="serve: length of the stream")
     ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--serve-blocks", type=int, default=0, help="serve: grid cap per single-lane solve")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--plain-sample", type=int, default=256,
                     help="LPs of the batch solved one at a time for the plain-path figure")
@@ -610,6 +611,7 @@ def play_stream(tsx, torch, dev, shapes, arrivals, seeds, server_kw):
             r = sv.result(ticket)
             out.append((r.status, r.t_done - t_sched, r.obj, r.t_done))
         st = sv.stats()
+        st["last_error"] = sv.last_error()
     return out, st, t0
 
 
@@ -631,7 +633,7 @@ def run_serve(args, rank, world, local):
     clocks = ClockSampler(local)
     clocks.start()
     served, st, t0 = play_stream(tsx, torch, dev, shapes, arrivals, seeds,
-                                 {"workers": args.serve_workers})
+                                 {"workers": args.serve_workers, "blocks_per_lp": args.serve_blocks})
     clk = clocks.stop()
     plain, st_plain, t0p = play_stream(tsx, torch, dev, shapes, arrivals, seeds,
                                        {"workers": 1, "batch_small": 0})
@@ -646,6 +648,9 @@ def run_serve(args, rank, world, local):
 
     s_srv = summary(served, t0)
     s_pl = summary(plain, t0p)
+    hist = {}
+    for r in served:
+        hist[tsx.STATUS_NAMES.get(r[0], str(r[0]))] = hist.get(tsx.STATUS_NAMES.get(r[0], str(r[0])), 0) + 1
     rel = [abs(a[2] - b[2]) / max(1e-300, abs(b[2])) for a, b in zip(served, plain)]
     line = {
         "metric": "LPs/s", "value": s_srv["solves_per_s"], "unit": "LPs/s", "n_gpus": world,
@@ -663,7 +668,7 @@ def run_serve(args, rank, world, local):
         "plain": dict(s_pl, path="one LP at a time in arrival order (1 worker, no micro-batches)"),
         "speedup_vs_plain": s_srv["solves_per_s"] / s_pl["solves_per_s"],
         "objective_rel_diff_vs_plain_max": max(rel),
-        "optimal": s_srv["optimal"],
+        "optimal": s_srv["optimal"], "status_counts": hist, "last_error": st["last_error"] or None,
         "e2e": {"value": s_srv["solves_per_s"], "unit": "LPs/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": int(sum(8 * (m + n + 1) for m, n in shapes)),
                 "note": "inputs are generated on the device at each arrival; results copied to the host"},

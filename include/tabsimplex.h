@@ -204,9 +204,11 @@ const char *lp_version(void);
  * Steps 1-3 with the same tie rules), FP64.  Results equal lp_solve's entry
  * for entry.  The block keeps the condensed tableau (the nonbasic columns and
  * the right-hand side; the basic columns of the full tableau are unit
- * vectors), which must fit in shared memory: 8 ((m+1) ldc + m + 1 + ldc) +
- * 4 (m + n) bytes <= the device's opt-in block limit (227 KB on GB300;
- * ldc = n + 1 or n + 2, odd), e.g. m = n = 128 needs 134 KB.
+ * vectors): 8 ((m+1) ldc + m + 1 + ldc) + 4 (m + n) bytes (ldc = n + 1 or
+ * n + 2, odd), e.g. m = n = 128 needs 134 KB.  In shared memory when it fits
+ * the device's opt-in block limit (227 KB on GB300), otherwise in a global
+ * workspace slice allocated with the batch (one block per LP either way, so
+ * large LPs are better served by lp_solve).
  * ------------------------------------------------------------------------ */
 typedef struct lp_batch *lp_batch_t;
 
@@ -232,8 +234,10 @@ typedef struct {
     long long total_pivots;       /* pivots of all LPs                          */
     long long kernel_launches;    /* kernels of the last solve (graph nodes)    */
     int buckets;                  /* shared-memory size classes used            */
-    int threads[4];               /* threads per LP chosen for each class       */
-    int lps_per_class[4];
+    int threads[5];               /* threads per LP chosen for each class: four
+                                     shared-memory size classes, then the LPs
+                                     whose tableau lives in global memory       */
+    int lps_per_class[5];
     double tune_ms;               /* time spent autotuning (first solve)        */
     int graph;                    /* 1 if the solve replayed a CUDA graph       */
 } lp_batch_stats;
@@ -244,9 +248,9 @@ void lp_batch_options_init(lp_batch_options *opt);
  * variables; A holds the LPs' constraint matrices back to back (each m[k] x
  * n[k] row-major), b the right-hand sides back to back (sum of m[k]) and c the
  * price vectors back to back (sum of n[k]).  Copied to the device.  Each LP
- * must satisfy lp_create's conditions and fit in shared memory (see above);
- * otherwise NULL (lp_last_error names the LP).  Per-LP input errors found on
- * the device (non-finite data, b < 0) are reported as that LP's status. */
+ * needs m, n > 0, else NULL (lp_last_error names the LP).  Per-LP input errors
+ * found on the device (non-finite data, b < 0) are reported as that LP's
+ * status. */
 lp_batch_t lp_batch_create(int count, const int *m, const int *n, const double *A,
                            const double *b, const double *c);
 
@@ -277,12 +281,13 @@ void lp_batch_destroy(lp_batch_t h);
 /* ------------------------------------------------------------------------
  * Request server with continuous batching.  Requests (one LP each) enter a
  * FIFO queue; a pool of worker threads, each with its own CUDA stream, admits
- * them in arrival order while the device-memory budget allows.  LPs with
- * m, n <= small_max_dim are taken together -- every such request waiting at
- * that moment, up to batch_max -- and solved as one micro-batch by the batched
- * solver (FP64, results equal lp_solve's); the others are solved one per
+ * them in arrival order while the device-memory budget allows.  LPs up to a
+ * size (shared-memory fit, or batch_max_bytes) are taken together -- every such
+ * request waiting at that moment, up to batch_max -- and solved as one
+ * micro-batch (FP64, results equal lp_solve's); the others are solved one per
  * worker by lp_create / lp_solve with the given precision (default FP32
- * tableau + FP64 recovery).  Requests arriving while others are on the GPU are
+ * tableau + FP64 recovery) on a share of the GPU's blocks, so that several run
+ * side by side.  Requests arriving while others are on the GPU are
  * admitted as workers and memory free up, and their work overlaps on the
  * device.  The paper has no serving layer; every solve inside is the method of
  * lp_solve.
@@ -296,7 +301,17 @@ typedef struct {
     int precision;                /* single-LP lane (default LP_PREC_FP32)      */
     int batch_small;              /* 1 (default): micro-batch the small LPs     */
     int batch_max;                /* max LPs per micro-batch (default 1024)     */
-    int small_max_dim;            /* small: m, n <= this (default 128)          */
+    int small_max_dim;            /* > 0: micro-batch only LPs with m, n <= this;
+                                     0 (default): every LP that fits the
+                                     batched solver's shared memory             */
+    int blocks_per_lp;            /* grid cap of a single-lane solve; 0
+                                     (default): 4 x SMs / workers, at least 16  */
+    long long batch_max_bytes;    /* > 0: LPs whose condensed tableau (8 (m+1)
+                                     (n+2) bytes) is at most this also go
+                                     through the micro-batches, solved from
+                                     global memory one block per LP (pays off
+                                     only when many such LPs wait together);
+                                     0 (default): shared-memory LPs only        */
 } lps_options;
 
 typedef struct {
@@ -338,6 +353,10 @@ lp_status lps_result(lps_t sv, long long ticket, double *x, double *y, double *o
 lp_status lps_release(lps_t sv, long long ticket);
 
 lp_status lps_get_stats(lps_t sv, lps_stats *stats);
+
+/* Message of the latest failed solve on any worker ("" if none); valid until
+ * the calling thread's next call. */
+const char *lps_last_error(lps_t sv);
 
 /* Finish every queued request, stop the workers, free the server. */
 void lps_close(lps_t sv);

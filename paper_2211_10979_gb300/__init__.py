@@ -22,7 +22,7 @@ from .abi import (LP_ERR_CUDA, LP_ERR_INVALID, LP_ERR_NOMEM, LP_ERR_NUMERIC, LP_
                   lp_batch_options, lp_batch_options_init, lp_batch_create, lp_batch_create_device,
                   lp_batch_solve, lp_batch_get, lp_batch_get_tableau, lp_batch_get_stats,
                   lp_batch_destroy, LP_PENDING, lps_options, lps_options_init, lps_open, lps_submit,
-                  lps_submit_device, lps_wait, lps_result, lps_release, lps_get_stats, lps_close,
+                  lps_submit_device, lps_wait, lps_result, lps_release, lps_get_stats, lps_last_error, lps_close,
                   lp_generate_dense)
 
 __all__ = [n for n in dir(abi) if n.startswith(("lp_", "LP_"))] + [
@@ -288,6 +288,9 @@ class Server:
 
     def stats(self) -> dict:
         return lps_get_stats(self.h).as_dict()
+
+    def last_error(self) -> str:
+        return lps_last_error(self.h)
 
     def close(self):
         if getattr(self, "h", None):

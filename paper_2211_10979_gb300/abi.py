@@ -29,7 +29,7 @@ EXPORTS = ("lp_options_init", "lp_create", "lp_create_device", "lp_solve", "lp_g
            "lp_batch_create", "lp_batch_create_device", "lp_batch_solve", "lp_batch_get",
            "lp_batch_get_tableau", "lp_batch_get_stats", "lp_batch_destroy", "lps_options_init",
            "lps_open", "lps_submit", "lps_submit_device", "lps_wait", "lps_result", "lps_release",
-           "lps_get_stats", "lps_close", "lp_generate_dense")
+           "lps_get_stats", "lps_last_error", "lps_close", "lp_generate_dense")
 LP_PENDING = 100
 
 # capacity of the library's fixed work-buffer array used by lp_solve_noalloc
@@ -107,8 +107,8 @@ class lp_batch_stats(ctypes.Structure):
         ("total_pivots", ctypes.c_longlong),
         ("kernel_launches", ctypes.c_longlong),
         ("buckets", ctypes.c_int),
-        ("threads", ctypes.c_int * 4),
-        ("lps_per_class", ctypes.c_int * 4),
+        ("threads", ctypes.c_int * 5),
+        ("lps_per_class", ctypes.c_int * 5),
         ("tune_ms", ctypes.c_double),
         ("graph", ctypes.c_int),
     ]
@@ -128,6 +128,8 @@ class lps_options(ctypes.Structure):
         ("batch_small", ctypes.c_int),
         ("batch_max", ctypes.c_int),
         ("small_max_dim", ctypes.c_int),
+        ("blocks_per_lp", ctypes.c_int),
+        ("batch_max_bytes", ctypes.c_longlong),
     ]
 
 
@@ -203,6 +205,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "lps_result": (ctypes.c_int, [vp, ctypes.c_longlong, vp, vp, vp, llp, vp]),
             "lps_release": (ctypes.c_int, [vp, ctypes.c_longlong]),
             "lps_get_stats": (ctypes.c_int, [vp, ctypes.POINTER(lps_stats)]),
+            "lps_last_error": (ctypes.c_char_p, [vp]),
             "lps_close": (None, [vp]),
             "lp_generate_dense": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, vp, vp, vp, vp]),
         }
@@ -403,6 +406,11 @@ def lps_get_stats(sv: int) -> lps_stats:
     if load().lps_get_stats(sv, ctypes.byref(s)) != 0:
         raise RuntimeError(lp_last_error())
     return s
+
+
+def lps_last_error(sv: int) -> str:
+    msg = load().lps_last_error(sv)
+    return msg.decode() if msg else ""
 
 
 def lps_close(sv: int) -> None:

@@ -20,8 +20,11 @@ using namespace tsx;
 
 namespace {
 
-constexpr int kClasses = 4;
-constexpr size_t kClassMax[kClasses - 1] = {24 * 1024, 56 * 1024, 112 * 1024};   // last: device limit
+constexpr int kClasses = 5;
+// shared-memory size classes; the last one holds the LPs that keep their
+// tableau in a global workspace slice
+constexpr int kGlobal = kClasses - 1;
+constexpr size_t kClassMax[kClasses - 2] = {24 * 1024, 56 * 1024, 112 * 1024};   // 4th: device limit
 constexpr int kCandidates[4] = {32, 64, 128, 256};
 
 struct DBlock {
@@ -69,6 +72,7 @@ struct lp_batch {
     double* y = nullptr;
     unsigned long long* total = nullptr;
     DBlock keep;
+    DBlock gwork;                    // global workspace of the kGlobal class
     int tuned[kClasses] = {};
     cudaGraphExec_t graph = nullptr;
     BatchParams graph_params{};
@@ -125,6 +129,7 @@ void lp_batch_destroy(lp_batch_t h) {
     if (h->stream) cudaStreamSynchronize(h->stream);
     if (h->graph) cudaGraphExecDestroy(h->graph);
     bdev_free(h, h->keep);
+    bdev_free(h, h->gwork);
     bdev_free(h, h->work);
     bdev_free(h, h->inputs);
     if (h->stream) cudaStreamSynchronize(h->stream);
@@ -149,6 +154,23 @@ static size_t kernel_static_smem() {
     return fa.sharedSizeBytes;
 }
 
+static int condensed_ld(int n) { return (n + 1) % 2 == 1 ? n + 1 : n + 2; }
+
+size_t tsx::batch_smem_limit() {
+    int device = 0, optin = 0;
+    cudaGetDevice(&device);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    size_t stat = 0;
+    for (size_t v : {kernel_static_smem<32>(), kernel_static_smem<64>(), kernel_static_smem<128>(),
+                     kernel_static_smem<256>()})
+        stat = std::max(stat, v);
+    return optin > 0 ? (size_t)optin - stat - 256 : 0;
+}
+
+bool tsx::batch_fits(int m, int n, size_t limit) {
+    return m > 0 && n > 0 && batch_smem_bytes(m, n, condensed_ld(n)) <= limit;
+}
+
 static lp_batch* batch_common(int count, const int* m, const int* n, cudaStream_t stream, bool own_stream) {
     if (count <= 0 || !m || !n) {
         set_error("lp_batch_create: need count > 0 and the m, n arrays");
@@ -159,13 +181,8 @@ static lp_batch* batch_common(int count, const int* m, const int* n, cudaStream_
     cudaGetDevice(&h->device);
     current_allocator(&h->alloc, &h->dealloc, &h->actx);
     cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device);
-    int optin = 0;
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-    size_t stat = 0;
-    for (size_t v : {kernel_static_smem<32>(), kernel_static_smem<64>(), kernel_static_smem<128>(),
-                     kernel_static_smem<256>()})
-        stat = std::max(stat, v);
-    const size_t limit = optin > 0 ? (size_t)optin - stat - 256 : 0;
+    const size_t limit = batch_smem_limit();
+    size_t gbytes = 0;
     h->lps.resize(count);
     for (int k = 0; k < count; ++k) {
         if (m[k] <= 0 || n[k] <= 0) {
@@ -176,20 +193,20 @@ static lp_batch* batch_common(int count, const int* m, const int* n, cudaStream_
         BatchLP& L = h->lps[k];
         L.m = m[k];
         L.n = n[k];
-        L.ldc = (n[k] + 1) % 2 == 1 ? n[k] + 1 : n[k] + 2;
+        L.ldc = condensed_ld(n[k]);
         const size_t smem = batch_smem_bytes(L.m, L.n, L.ldc);
-        if (smem > limit) {
-            set_error("lp_batch_create: LP %d (m=%d, n=%d) needs %zu bytes of shared memory, more than the "
-                      "%zu available; solve it with lp_create/lp_solve",
-                      k, m[k], n[k], smem, limit);
-            delete h;
-            return nullptr;
+        int cls = kGlobal;
+        if (smem <= limit) {
+            cls = kGlobal - 1;
+            for (int q = 0; q < kGlobal - 1; ++q)
+                if (smem <= kClassMax[q]) { cls = q; break; }
+            h->class_smem[cls] = std::max(h->class_smem[cls], smem);
+            L.w_off = -1;
+        } else {
+            L.w_off = (long long)gbytes;
+            gbytes += align_up(smem, 256);
         }
-        int cls = kClasses - 1;
-        for (int q = 0; q < kClasses - 1; ++q)
-            if (smem <= kClassMax[q]) { cls = q; break; }
         L.bucket = cls;
-        h->class_smem[cls] = std::max(h->class_smem[cls], smem);
         ++h->class_count[cls];
         L.a_off = h->sum_mn;
         L.b_off = h->sum_m;
@@ -210,16 +227,13 @@ static lp_batch* batch_common(int count, const int* m, const int* n, cudaStream_
     } else {
         h->stream = stream;
     }
-    bool ok = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&h->e_in, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&h->e_out, cudaEventDisableTiming) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) == cudaSuccess &&
-              cudaEventCreate(&h->ev0) == cudaSuccess && cudaEventCreate(&h->ev1) == cudaSuccess;
-    for (int q = 0; q < kClasses; ++q)
-        ok = ok && cudaStreamCreateWithFlags(&h->side[q], cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&h->join[q], cudaEventDisableTiming) == cudaSuccess;
-    if (!ok) {
-        set_error("lp_batch_create: stream/event creation failed");
+    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+        set_error("lp_batch_create: event creation failed");
+        lp_batch_destroy(h);
+        return nullptr;
+    }
+    if (gbytes && !bdev_alloc_block(h, h->gwork, gbytes)) {
+        set_error("lp_batch_create: device allocation of %zu workspace bytes failed", gbytes);
         lp_batch_destroy(h);
         return nullptr;
     }
@@ -329,10 +343,37 @@ lp_batch_t lp_batch_create_device(int count, const int* m, const int* n, const d
     return h;
 }
 
+// The dynamic shared-memory limit of a kernel is process-wide state: it is
+// raised once per kernel instance to the device's maximum (never lowered, so
+// concurrent batches on other threads cannot race on it).
+template <int NT>
+static cudaError_t allow_max_smem() {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, k_batch_solve<NT>);
+        err = cudaFuncSetAttribute(k_batch_solve<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   optin - (int)fa.sharedSizeBytes);
+    });
+    return err;
+}
+
 template <int NT>
 static cudaError_t launch_class(lp_batch* h, const BatchParams& P, int q, cudaStream_t s) {
+    if (q == kGlobal) {
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_solve_global<NT>, NT, 0);
+        const int grid = std::max(1, std::min(h->class_count[q], std::max(per, 1) * h->nsm));
+        k_batch_solve_global<NT><<<grid, NT, 0, s>>>(P, h->lists[q], h->class_count[q], h->queues + q,
+                                                     (unsigned char*)h->gwork.ptr);
+        return cudaGetLastError();
+    }
     const size_t smem = h->class_smem[q];
-    cudaError_t e = cudaFuncSetAttribute(k_batch_solve<NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_max_smem<NT>();
     if (e != cudaSuccess) return e;
     int per = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_solve<NT>, NT, smem);
@@ -350,13 +391,31 @@ static cudaError_t launch_class_nt(lp_batch* h, const BatchParams& P, int q, int
     }
 }
 
-// Every class, concurrently: fork from s to one stream per class, join back.
-static cudaError_t enqueue_solve(lp_batch* h, const BatchParams& P, const int* nt, cudaStream_t s) {
+// Streams and events of the graph path, created on its first use.
+static bool ensure_graph_streams(lp_batch* h) {
+    if (h->cap) return true;
+    bool ok = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&h->e_in, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&h->e_out, cudaEventDisableTiming) == cudaSuccess;
+    for (int q = 0; q < kClasses; ++q)
+        ok = ok && cudaStreamCreateWithFlags(&h->side[q], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&h->join[q], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) == cudaSuccess;
+    return ok;
+}
+
+// Every class: with `fork` (graph capture), concurrently on one stream per
+// class joined back into s; without, one after the other on s.
+static cudaError_t enqueue_solve(lp_batch* h, const BatchParams& P, const int* nt, cudaStream_t s, bool fork) {
     cudaError_t e = cudaMemsetAsync(h->queues, 0, sizeof(unsigned) * kClasses, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->total, 0, sizeof(unsigned long long), s);
-    if (e == cudaSuccess) e = cudaEventRecord(h->fork, s);
+    if (fork && e == cudaSuccess) e = cudaEventRecord(h->fork, s);
     for (int q = 0; q < kClasses && e == cudaSuccess; ++q) {
         if (!h->class_count[q]) continue;
+        if (!fork) {
+            e = launch_class_nt(h, P, q, nt[q], s);
+            continue;
+        }
         e = cudaStreamWaitEvent(h->side[q], h->fork, 0);
         if (e == cudaSuccess) e = launch_class_nt(h, P, q, nt[q], h->side[q]);
         if (e == cudaSuccess) e = cudaEventRecord(h->join[q], h->side[q]);
@@ -470,25 +529,24 @@ lp_status lp_batch_solve(lp_batch_t h, const lp_batch_options* opt) {
             h->graph = nullptr;
             h->graph_valid = false;
             // the attributes are set outside the capture
-            for (int q = 0; q < kClasses; ++q) {
+            for (int q = 0; q < kGlobal; ++q) {
                 if (!h->class_count[q]) continue;
-                // a zero-length launch probe is not needed: set the attribute via a
-                // launch-free call on each template instance
-                const size_t smem = h->class_smem[q];
                 cudaError_t e = cudaSuccess;
                 switch (nt[q]) {
-                    case 32: e = cudaFuncSetAttribute(k_batch_solve<32>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-                    case 64: e = cudaFuncSetAttribute(k_batch_solve<64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-                    case 128: e = cudaFuncSetAttribute(k_batch_solve<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
-                    default: e = cudaFuncSetAttribute(k_batch_solve<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem); break;
+                    case 32: e = allow_max_smem<32>(); break;
+                    case 64: e = allow_max_smem<64>(); break;
+                    case 128: e = allow_max_smem<128>(); break;
+                    default: e = allow_max_smem<256>(); break;
                 }
                 TSX_CUDA_TRY(e, LP_ERR_CUDA);
             }
-            // captured on the batch's own stream: the caller's stream may be the
-            // legacy default stream, which cannot be captured
+            if (!ensure_graph_streams(h)) {
+                set_error("lp_batch_solve: stream/event creation failed");
+                return LP_ERR_CUDA;
+            }
             cudaGraph_t g = nullptr;
             TSX_CUDA_TRY(cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal), LP_ERR_CUDA);
-            cudaError_t e = enqueue_solve(h, P, nt, h->cap);
+            cudaError_t e = enqueue_solve(h, P, nt, h->cap, true);
             cudaError_t e2 = cudaStreamEndCapture(h->cap, &g);
             if (e != cudaSuccess || e2 != cudaSuccess || !g) {
                 if (g) cudaGraphDestroy(g);
@@ -514,7 +572,7 @@ lp_status lp_batch_solve(lp_batch_t h, const lp_batch_options* opt) {
         used_graph = true;
     } else {
         TSX_CUDA_TRY(cudaEventRecord(h->ev0, s), LP_ERR_CUDA);
-        TSX_CUDA_TRY(enqueue_solve(h, P, nt, s), LP_ERR_CUDA);
+        TSX_CUDA_TRY(enqueue_solve(h, P, nt, s, false), LP_ERR_CUDA);
         TSX_CUDA_TRY(cudaEventRecord(h->ev1, s), LP_ERR_CUDA);
     }
     unsigned long long total = 0;

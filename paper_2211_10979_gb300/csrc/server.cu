@@ -18,6 +18,7 @@
 #include <deque>
 #include <memory>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <unordered_map>
 #include <vector>
@@ -98,7 +99,7 @@ struct Request {
 // Device bytes a request holds while it is solved.
 size_t request_bytes(int m, int n, bool small, int precision) {
     const size_t in = 8ull * ((size_t)m * n + m + n);
-    if (small) return in + 64ull * (m + n) + 4096;
+    if (small) return 2 * in + 8ull * (size_t)(m + 2) * (n + 3) + 64ull * (m + n) + 4096;
     const size_t W = (size_t)n + m + 1;
     const size_t elem = precision == LP_PREC_FP32 ? 4 : 8;
     const size_t ld = (W + 31) / 32 * 32;
@@ -111,6 +112,8 @@ size_t request_bytes(int m, int n, bool small, int precision) {
 struct lp_server {
     lps_options opt{};
     int device = 0;
+    size_t smem_limit = 0;               // batched solver's shared memory per LP
+    int blocks = 0;                      // grid cap of a single-lane solve
     std::mutex mu;
     std::condition_variable cv_work;      // workers wait for requests
     std::condition_variable cv_done;      // clients wait for results
@@ -121,6 +124,7 @@ struct lp_server {
     long long next_id = 0;
     long long used = 0, peak = 0;
     long long submitted = 0, completed = 0, batches = 0, batched_lps = 0;
+    std::string last_error;              // message of the latest failed solve
     bool stopping = false;
     bool started = false;
     Clock::time_point t_first, t_last;
@@ -134,7 +138,15 @@ void lps_options_init(lps_options* o) {
     o->precision = LP_PREC_FP32;
     o->batch_small = 1;
     o->batch_max = 1024;
-    o->small_max_dim = 128;
+    o->small_max_dim = 0;
+    o->blocks_per_lp = 0;
+    o->batch_max_bytes = 0;
+}
+
+// Keeps the calling worker's last library error for lps_last_error.
+static void note_error(lp_server* sv, const char* where) {
+    std::lock_guard<std::mutex> lk(sv->mu);
+    sv->last_error = std::string(where) + ": " + lp_last_error();
 }
 
 // Solves one single-path request on the calling worker thread.
@@ -142,14 +154,17 @@ static void solve_single(lp_server* sv, Request& r, cudaStream_t s) {
     lp_t h = r.on_device ? lp_create_device(r.m, r.n, r.dA, r.db, r.dc, (void*)s)
                          : lp_create(r.m, r.n, r.hA.data(), r.hb.data(), r.hc.data());
     if (!h) {
+        note_error(sv, "create");
         r.status = LP_ERR_INVALID;
         return;
     }
     lp_options o;
     lp_options_init(&o);
     o.precision = sv->opt.precision;
+    o.blocks = sv->blocks;
     o.stream = r.on_device ? (void*)s : nullptr;
     r.status = lp_solve(h, &o);
+    if (r.status < 0) note_error(sv, "solve");
     r.x.assign(r.n, 0.0);
     r.y.assign(r.m, 0.0);
     long long it = 0;
@@ -197,6 +212,7 @@ static void solve_batch(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs
     }
     lp_batch_t h = ok ? lp_batch_create_device(count, m.data(), n.data(), pA, pb, pc, (void*)s) : nullptr;
     if (!h) {
+        note_error(sv, "micro-batch create");
         fail(LP_ERR_INVALID);
         cudaFreeAsync(pack, s);
         cudaStreamSynchronize(s);
@@ -205,6 +221,7 @@ static void solve_batch(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs
     lp_batch_options bo;
     lp_batch_options_init(&bo);
     bo.stream = (void*)s;
+    bo.use_graph = 0;   // solved once: a graph would not be replayed
     std::vector<int> st(count);
     std::vector<long long> it(count);
     std::vector<double> obj(count), x(sn), y(sm);
@@ -222,6 +239,7 @@ static void solve_batch(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs
             yo += r.m;
         }
     } else {
+        note_error(sv, "micro-batch solve");
         fail(LP_ERR_CUDA);
     }
     lp_batch_destroy(h);
@@ -310,12 +328,24 @@ lps_t lps_open(const lps_options* opt) {
         return nullptr;
     }
     cudaGetDevice(&sv->device);
+    sv->smem_limit = batch_smem_limit();
+    // each single-lane solve gets a share of the GPU's blocks (a quarter with
+    // the default 8 workers), so that solves of several workers run side by side
+    int nsm = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, sv->device);
+    sv->blocks = sv->opt.blocks_per_lp > 0 ? sv->opt.blocks_per_lp
+                                           : std::max(16, 4 * nsm / std::max(1, sv->opt.workers));
     for (int w = 0; w < sv->opt.workers; ++w) sv->workers.emplace_back(worker_main, sv);
     return sv;
 }
 
 static long long enqueue(lp_server* sv, std::shared_ptr<Request> r) {
-    r->small = sv->opt.batch_small && r->m <= sv->opt.small_max_dim && r->n <= sv->opt.small_max_dim;
+    // the batch lane: LPs whose condensed tableau fits shared memory, or is at
+    // most batch_max_bytes (solved from global memory, one block per LP)
+    const size_t cbytes = 8ull * (size_t)(r->m + 1) * (size_t)(r->n + 2);
+    r->small = sv->opt.batch_small &&
+               (batch_fits(r->m, r->n, sv->smem_limit) || cbytes <= (size_t)sv->opt.batch_max_bytes) &&
+               (sv->opt.small_max_dim <= 0 || (r->m <= sv->opt.small_max_dim && r->n <= sv->opt.small_max_dim));
     r->bytes = request_bytes(r->m, r->n, r->small, sv->opt.precision);
     if ((long long)r->bytes > sv->opt.budget_bytes) {
         set_error("lps_submit: request needs %zu bytes, more than the budget", r->bytes);
@@ -453,6 +483,14 @@ lp_status lps_get_stats(lps_t sv, lps_stats* st) {
     st->batched_lps = sv->batched_lps;
     st->peak_bytes = sv->peak;
     return LP_OPTIMAL;
+}
+
+const char* lps_last_error(lps_t sv) {
+    if (!sv) return "";
+    thread_local std::string copy;
+    std::lock_guard<std::mutex> lk(sv->mu);
+    copy = sv->last_error;
+    return copy.c_str();
 }
 
 void lps_close(lps_t sv) {

@@ -12,7 +12,9 @@
 //     row p:  1 / piv;     row i != p:  fma(-T[i][q], 1 / piv, 0),
 // and every other slot follows Step 3 unchanged.  Ties are broken by the
 // original variable index, so pivots and values equal the full-tableau run.
-// The largest LP of m = n = 128 needs (m+1) x (n+1) doubles = 133 KB.
+// The largest LP of m = n = 128 needs (m+1) x (n+1) doubles = 133 KB.  An LP
+// whose condensed tableau does not fit in shared memory keeps it in a global
+// workspace slice instead (k_batch_solve_global; L2-resident for medium LPs).
 #pragma once
 
 #include "tsx_device.cuh"
@@ -27,6 +29,7 @@ struct BatchLP {              // one LP of the batch
     long long b_off;          // offset of b (and of y) in the packed b / y
     long long c_off;          // offset of c (and of x) in the packed c / x
     long long t_off;          // offset of the kept condensed tableau ((m+1) x ldc)
+    long long w_off;          // byte offset of its global workspace slice, -1 if in shared memory
 };
 
 struct BatchParams {
@@ -121,7 +124,8 @@ __device__ RatPart batch_block_rat(RatPart a, BatchScratch& s) {
     return s.rat_out;
 }
 
-// Solves LP `k` of the batch in shared memory (NT threads).
+// Solves LP `k` of the batch (NT threads) with its tableau at `smem` (shared
+// memory, or the LP's global workspace slice).
 template <int NT>
 __device__ void batch_solve_one(const BatchParams& P, int k, unsigned char* smem, BatchScratch& sc) {
     const BatchLP L = P.lps[k];
@@ -139,8 +143,8 @@ __device__ void batch_solve_one(const BatchParams& P, int k, unsigned char* smem
 
     // Initialization Step: condensed Table I (slack basis), plus input checks
     int bad = 0;
-    for (int t = tid; t < (m + 1) * ldc; t += NT) {
-        const int i = t / ldc, j = t - i * ldc;
+    for (long long t = tid; t < (long long)(m + 1) * ldc; t += NT) {
+        const int i = (int)(t / ldc), j = (int)(t - (long long)i * ldc);
         double v = 0.0;
         if (j < n)
             v = i == 0 ? -c[j] : A[(size_t)(i - 1) * n + j];
@@ -241,7 +245,7 @@ __device__ void batch_solve_one(const BatchParams& P, int k, unsigned char* smem
     }
     if (P.keepT) {
         double* kt = P.keepT + L.t_off;
-        for (int t = tid; t < (m + 1) * ldc; t += NT) kt[t] = T[t];
+        for (long long t = tid; t < (long long)(m + 1) * ldc; t += NT) kt[t] = T[t];
         for (int j = tid; j < n; j += NT) P.keepvar[L.c_off + j] = var[j];
         for (int i = tid; i < m; i += NT) P.keepbasis[L.b_off + i] = basis[i];
     }
@@ -261,6 +265,22 @@ __global__ void __launch_bounds__(NT) k_batch_solve(BatchParams P, const int* __
         __syncthreads();
         if (t >= count) return;
         batch_solve_one<NT>(P, list[t], smem, sc);
+    }
+}
+
+// LPs too large for shared memory: the same solve on a global workspace slice.
+template <int NT>
+__global__ void __launch_bounds__(NT) k_batch_solve_global(BatchParams P, const int* __restrict__ list, int count,
+                                                          unsigned* __restrict__ queue, unsigned char* work) {
+    __shared__ BatchScratch sc;
+    for (;;) {
+        if (threadIdx.x == 0) sc.lp = (int)atomicAdd(queue, 1u);
+        __syncthreads();
+        const int t = sc.lp;
+        __syncthreads();
+        if (t >= count) return;
+        const int k = list[t];
+        batch_solve_one<NT>(P, k, work + P.lps[k].w_off, sc);
     }
 }
 

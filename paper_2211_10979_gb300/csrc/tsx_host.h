@@ -20,6 +20,11 @@ void current_allocator(lp_alloc_fn* alloc_fn, lp_free_fn* free_fn, void** ctx);
 // cudaMallocAsync / cudaFreeAsync (the request server's worker threads).
 void use_default_allocator(bool on);
 
+// Shared-memory bytes the batched solver has for one LP on the current device,
+// and whether an m x n LP fits in them.
+size_t batch_smem_limit();
+bool batch_fits(int m, int n, size_t limit);
+
 }  // namespace tsx
 
 #define TSX_CUDA_TRY(call, ret)                                                           \

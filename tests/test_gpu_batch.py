@@ -118,10 +118,21 @@ def test_device_inputs(tsx):
         _check(bt.results(), problems, refs)
 
 
-def test_too_large_for_shared_memory_is_refused(tsx):
-    A, b, c = lpgen.dense_lp(200, 200, 1)
-    with pytest.raises(ValueError, match="shared memory"):
-        tsx.Batch([(A, b, c)])
+@pytest.mark.parametrize("threads", [0, 64, 256])
+def test_lps_beyond_shared_memory_use_global_workspace(tsx, threads):
+    # condensed tableaux above the shared-memory limit (m = n = 200: 323 KB)
+    # are solved from a global workspace slice, mixed with shared-memory ones
+    problems = _problems([(200, 200), (40, 50), (300, 120), (129, 400), (64, 64), (500, 90)], 321)
+    refs = [oracle.solve(*p) for p in problems]
+    with tsx.Batch(problems) as bt:
+        bt.solve(tsx.batch_options(threads=threads, keep_tableaux=1))
+        sol = bt.results()
+        _check(sol, problems, refs)
+        np.testing.assert_array_equal(bt.tableau(0), refs[0].T)
+        assert sol.stats["lps_per_class"][4] == 4
+
+
+def test_invalid_sizes_refused(tsx):
     with pytest.raises(ValueError, match="m > 0"):
         tsx.Batch(m=np.array([0], np.int32), n=np.array([3], np.int32), A=np.zeros(0), b=np.zeros(0),
                   c=np.zeros(3))

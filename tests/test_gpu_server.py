@@ -54,7 +54,7 @@ def test_results_same_alone_and_in_the_mix(tsx):
     # a mix of small (micro-batched) and larger (single-path) LPs submitted
     # from two client threads while earlier ones are being solved
     shapes = [(20, 30), (64, 64), (300, 250), (16, 128), (128, 16), (700, 400), (50, 50),
-              (256, 1024), (90, 120), (33, 77), (1500, 600), (128, 128)] * 3
+              (256, 1024), (90, 120), (33, 77), (1500, 600), (128, 128), (1200, 1100)] * 3
     problems = [lpgen.dense_lp(m, n, 4000 + k) for k, (m, n) in enumerate(shapes)]
     tickets = [None] * len(problems)
     with tsx.Server(workers=4) as sv:
@@ -75,7 +75,7 @@ def test_results_same_alone_and_in_the_mix(tsx):
     assert st["completed"] == len(problems) and st["batched_lps"] > 0
     for k, ((m, n), (A, b, c), r) in enumerate(zip(shapes, problems, results)):
         ref = oracle.solve(A, b, c)
-        if m <= 128 and n <= 128:
+        if (m + 1) * (n + 2) * 8 < 200_000:
             # micro-batched: the FP64 method, equal to the oracle
             assert r.iters == ref.iters and r.obj == ref.obj
             np.testing.assert_array_equal(r.x, ref.x)
@@ -115,6 +115,21 @@ def test_budget_admission_and_device_inputs(tsx):
         ref = oracle.solve(A, b, c)
         assert code == tsx.LP_OPTIMAL
         assert abs(r.obj - ref.obj) <= 1e-9 * abs(ref.obj)
+
+
+def test_global_memory_micro_batches(tsx):
+    # with batch_max_bytes set, medium LPs join the micro-batches too (solved
+    # from global memory one block per LP): still the FP64 method, oracle-exact
+    shapes = [(200, 200), (300, 150), (60, 60), (400, 90)] * 2
+    problems = [lpgen.dense_lp(m, n, 800 + k) for k, (m, n) in enumerate(shapes)]
+    with tsx.Server(workers=2, batch_max_bytes=8 << 20) as sv:
+        tickets = [sv.submit(*p) for p in problems]
+        res = [(sv.wait(t, 120.0), sv.result(t)) for t in tickets]
+        assert sv.stats()["batched_lps"] == len(problems)
+    for (A, b, c), (code, r) in zip(problems, res):
+        ref = oracle.solve(A, b, c)
+        assert code == tsx.LP_OPTIMAL and r.obj == ref.obj and r.iters == ref.iters
+        np.testing.assert_array_equal(r.x, ref.x)
 
 
 def test_plain_mode_and_stats(tsx):
