@@ -174,7 +174,7 @@ def profile_traffic(m, n):
     if not ent:
         return None
     from paper_2211_10979_gb300 import build as b
-    if ent.get("source_digest") != b.source_digest():
+    if ent.get("source_digest") != b.source_digest(b.PIVOT_SOURCES):
         return None   # the kernel changed since the counters were taken
     return ent
 

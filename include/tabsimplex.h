@@ -393,7 +393,7 @@ lp_status lp_generate_dense(int m, int n, unsigned long long seed, double *dA, d
  *   opt         options as for lp_solve (NULL = defaults); opt->stream is the
  *               stream used; log_capacity must be 0 and blocks <= 1024
  *   iters       host output (may be NULL): pivots performed
- * The work buffers need 8 (m + 1) + 9 ld + 16 ceil(ld / 128) + 16 * 1024 bytes
+ * The work buffers need 8 (m + 1) + 9 ld + 16 ceil(ld / 128) + 32 * 1024 bytes
  * plus about 1.5 KiB of alignment and state, at most LP_NOALLOC_SCRATCH_BYTES
  * (about m + ld <= 2.2e5, e.g. m = n = 70000); larger sizes return LP_ERR_INVALID
  * before any device work, with the sizes in lp_last_error().

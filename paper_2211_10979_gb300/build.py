@@ -37,11 +37,18 @@ def _deps():
     return out
 
 
-def source_digest() -> str:
-    """SHA-256 (first 16 hex digits) over the library's sources and header."""
+# Sources that define the single-LP pivot kernels and their launch.
+PIVOT_SOURCES = ("tabsimplex.cu", "tsx_device.cuh", "tsx_kernels.cuh", "tsx_host.h", "tabsimplex.h")
+
+
+def source_digest(names=None) -> str:
+    """SHA-256 (first 16 hex digits) over the library's sources and header, or
+    over the files with the given base names only."""
     import hashlib
     h = hashlib.sha256()
     for path in sorted(_deps()):
+        if names is not None and os.path.basename(path) not in names:
+            continue
         if path.endswith((".cu", ".cuh", ".h", ".cpp")):
             h.update(os.path.basename(path).encode())
             with open(path, "rb") as fh:

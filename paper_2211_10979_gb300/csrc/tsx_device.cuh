@@ -50,10 +50,12 @@ struct ArgPart {      // best entering candidate of a column range
     int jfirst;       // lowest column with entry < -eps_d (Bland), INT_MAX if none
 };
 
-struct RatPart {      // best leaving candidate of a row range
+struct __align__(16) RatPart {   // best leaving candidate of a row range
     double r;         // minimum ratio rhs_i / T[i][q], +inf if none
     int key;          // tie-break key: row index (Dantzig) or basic variable (Bland)
     int i;            // its row (1..m), INT_MAX if none
+    double a;         // its pivot element T[i][q] (exact in double for both tableau types)
+    double pad;
 };
 
 struct DevState {
@@ -192,7 +194,7 @@ __device__ __forceinline__ bool sector_nonzero(const Sector<V>& s) {
 }
 
 __device__ __forceinline__ ArgPart arg_none() { return ArgPart{__longlong_as_double(0x7ff0000000000000LL), INT_MAX, INT_MAX}; }
-__device__ __forceinline__ RatPart rat_none() { return RatPart{__longlong_as_double(0x7ff0000000000000LL), INT_MAX, INT_MAX}; }
+__device__ __forceinline__ RatPart rat_none() { return RatPart{__longlong_as_double(0x7ff0000000000000LL), INT_MAX, INT_MAX, 0.0, 0.0}; }
 
 // (v, j) lexicographic minimum: the most negative entry, lowest column on ties.
 __device__ __forceinline__ void arg_merge(ArgPart& a, const ArgPart& b) {
@@ -237,6 +239,7 @@ __device__ __forceinline__ RatPart warp_rat(RatPart a) {
         b.r = __shfl_xor_sync(0xffffffffu, a.r, o);
         b.key = __shfl_xor_sync(0xffffffffu, a.key, o);
         b.i = __shfl_xor_sync(0xffffffffu, a.i, o);
+        b.a = __shfl_xor_sync(0xffffffffu, a.a, o);
         rat_merge(a, b);
     }
     return a;
@@ -255,11 +258,13 @@ __device__ __forceinline__ ArgPart load_arg(const ArgPart* src) {
 __device__ __forceinline__ void store_rat(RatPart* dst, const RatPart& a) {
     long long bits = __double_as_longlong(a.r);
     __stcg(reinterpret_cast<int4*>(dst), make_int4((int)(bits & 0xffffffff), (int)(bits >> 32), a.key, a.i));
+    __stcg(reinterpret_cast<double2*>(dst) + 1, make_double2(a.a, 0.0));
 }
 __device__ __forceinline__ RatPart load_rat(const RatPart* src) {
     int4 w = __ldcg(reinterpret_cast<const int4*>(src));
+    double2 x = __ldcg(reinterpret_cast<const double2*>(src) + 1);
     long long bits = ((long long)(unsigned)w.y << 32) | (unsigned)w.x;
-    return RatPart{__longlong_as_double(bits), w.z, w.w};
+    return RatPart{__longlong_as_double(bits), w.z, w.w, x.x, 0.0};
 }
 
 struct BlockScratch {
@@ -388,6 +393,7 @@ __device__ void phase_ratio(const Params<V>& P, int q, int bland, BlockScratch& 
             c.r = (double)div_rn(__ldcg(row + (P.W - 1)), a);
             c.i = (int)i;
             c.key = bland ? __ldcg(P.basis + (i - 1)) : (int)i;
+            c.a = (double)a;
             rat_merge(best, c);
         }
     }
@@ -403,24 +409,38 @@ __device__ RatPart phase_leaving(const Params<V>& P, BlockScratch& s) {
     return block_rat(a, s);
 }
 
-// P3b: pivot-row staging.  (1) The 32-B column groups of row p holding a
-// nonzero entry -- exactly the groups whose scaled entries R can be nonzero --
-// are compacted into P.act (warp ballot, one atomic per warp; the order of the
-// list does not matter, every group is updated independently).  With
-// skip_zero == 0 every group is listed.  (2) R[j] = T[p][j] / piv over the
-// padded row, element j on block j mod G so the divisions spread over all SMs.
+// P3b: pivot-row staging.  (1) R[j] = T[p][j] / piv over the padded row,
+// element j on block j mod G so the divisions spread over all SMs.  (2) The
+// 32-B column groups of row p holding a nonzero entry -- exactly the groups
+// whose R entries can be nonzero -- compacted into P.act (warp ballot, one
+// atomic per warp; the order of the list does not matter, every group is
+// updated independently).  With skip_zero == 0 every group is listed.  The
+// first element and the first sector of each thread are loaded together, so
+// both parts wait on one round trip.
 template <typename V>
 __device__ void phase_stage_row(const Params<V>& P, int p, V piv) {
     constexpr int E = Lanes<V>::E;
     const V* row = P.T + (size_t)p * (size_t)P.ld;
     const int lane = threadIdx.x & 31;
     const long long nsec = P.ld / E;
+    const long long nth = (long long)gridDim.x * blockDim.x;
+    const long long e0 = (long long)threadIdx.x * gridDim.x + blockIdx.x;
     const long long wi = (long long)(threadIdx.x >> 5) * gridDim.x + blockIdx.x;
     const long long nwi = (long long)(blockDim.x >> 5) * gridDim.x;
+    const long long k0 = wi * 32 + lane;
+    V x = V(0);
+    Sector<V> t;
+    if (e0 < P.ld) x = __ldcg(row + e0);
+    if (k0 < nsec) t = ld_sector_cg(row + E * k0);
+    if (e0 < P.ld) __stcg(P.R + e0, div_rn(x, piv));
+    for (long long e = e0 + nth; e < P.ld; e += nth) __stcg(P.R + e, div_rn(__ldcg(row + e), piv));
     for (long long base = wi * 32; base < nsec; base += nwi * 32) {
         const long long k = base + lane;
         bool nz = false;
-        if (k < nsec) nz = P.skip_zero ? sector_nonzero(ld_sector_cg(row + E * k)) : true;
+        if (k < nsec) {
+            if (base != wi * 32) t = ld_sector_cg(row + E * k);
+            nz = P.skip_zero ? sector_nonzero(t) : true;
+        }
         const unsigned mask = __ballot_sync(0xffffffffu, nz);
         if (mask) {
             unsigned off = 0;
@@ -429,9 +449,6 @@ __device__ void phase_stage_row(const Params<V>& P, int p, V piv) {
             if (nz) P.act[off + __popc(mask & ((1u << lane) - 1u))] = (int)k;
         }
     }
-    const long long nth = (long long)gridDim.x * blockDim.x;
-    for (long long e = (long long)threadIdx.x * gridDim.x + blockIdx.x; e < P.ld; e += nth)
-        __stcg(P.R + e, div_rn(__ldcg(row + e), piv));
 }
 
 // P4a: the objective row and the pivot row, every column group.  One warp per

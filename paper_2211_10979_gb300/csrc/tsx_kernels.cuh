@@ -129,17 +129,19 @@ __device__ __forceinline__ void finish(const Params<V>& P, int status, long long
     }
 }
 
-// Phase timer of block 0, thread 0 (other threads keep it at zero).
+// Phase timer of block 0, thread 0, kept in shared memory so that no
+// registers are held across the pivot loop.
 struct PhaseClock {
-    long long acc[6] = {0, 0, 0, 0, 0, 0};
-    long long t = 0;
-    bool on = false;
+    long long acc[6];
+    long long t;
     __device__ void start() {
-        on = blockIdx.x == 0 && threadIdx.x == 0;
-        if (on) t = global_ns();
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            for (int k = 0; k < 6; ++k) acc[k] = 0;
+            t = global_ns();
+        }
     }
     __device__ void lap(int k) {   // closes interval k, opens the next one
-        if (on) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
             const long long now = global_ns();
             acc[k] += now - t;
             t = now;
@@ -153,7 +155,8 @@ struct PhaseClock {
 template <int NT, typename V>
 __global__ void __launch_bounds__(NT, 512 / NT) k_pivot_persistent(Params<V> P) {
     __shared__ BlockScratch s;
-    PhaseClock clk;
+    __shared__ PhaseClock clk;
+    clk.start();
     phase_init_argmin(P);
     if (!grid_barrier(P.st, P.timeout_ns, s)) return;
     long long it = 0;
@@ -171,7 +174,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_pivot_persistent(Params<V> P) 
         clk.lap(3);
         const RatPart l = phase_leaving(P, s);            // Step 2 (global)
         if (l.i == INT_MAX) { finish(P, kUnbounded, it, bland, degen, clk.acc); return; }
-        const V piv = __ldcg(P.F + l.i);
+        const V piv = (V)l.a;   // the pivot element, carried by the partial
         if (!isfinite((double)piv) || !isfinite(l.r)) { finish(P, kNumeric, it, bland, degen, clk.acc); return; }
         phase_stage_row(P, l.i, piv);                     // Step 3 (pivot row)
         if (blockIdx.x == 0 && threadIdx.x == 0) record_pivot(P, it, q, l.i);
@@ -220,7 +223,7 @@ __global__ void __launch_bounds__(NT) k_ml_stage(Params<V> P) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&P.st->status, kRunning, kUnbounded);
         return;
     }
-    const V piv = __ldcg(P.F + l.i);
+    const V piv = (V)l.a;   // the pivot element, carried by the partial
     if (!isfinite((double)piv) || !isfinite(l.r)) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&P.st->status, kRunning, kNumeric);
         return;
