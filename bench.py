@@ -656,7 +656,8 @@ def run_serve(args, rank, world, local):
         "metric": "LPs/s", "value": s_srv["solves_per_s"], "unit": "LPs/s", "n_gpus": world,
         "steps": 1, "warmup": 1, "ms_per_step": 1e3 * count / s_srv["solves_per_s"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 tableau + f64 recovery (m, n > 128); f64 micro-batches (m, n <= 128)",
+        "dtype": "f64 micro-batches (LPs whose condensed tableau fits one SM's shared memory); "
+                 "f32 tableau + f64 recovery (the others)",
         "data": "synthetic",
         "config": {"workload": f"Poisson stream, {args.rate:.0f} LPs/s for {args.serve_seconds:.1f} s "
                                f"({count} LPs), m and n log-uniform in [32, 4096], inputs generated on "
