@@ -60,6 +60,8 @@ def parse_args(argv=None):
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--serve-blocks", type=int, default=0, help="serve: grid cap per single-lane solve")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--batch-threads", type=int, default=0,
+                    help="batch: threads per LP (32/64/128/256); 0 = autotuned per size class")
     ap.add_argument("--plain-sample", type=int, default=256,
                     help="LPs of the batch solved one at a time for the plain-path figure")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
@@ -477,7 +479,7 @@ def run_batch(args, rank, world, local):
     x = np.empty(int(n.sum()))
     y = np.empty(int(m.sum()))
     h = tsx.lp_batch_create_device(count, m, n, dA, db, dc, sptr)
-    opts = tsx.batch_options(stream=sptr)
+    opts = tsx.batch_options(stream=sptr, threads=args.batch_threads)
     try:
         for _ in range(args.warmup):   # the first solve autotunes and captures the graph
             tsx.lp_batch_solve(h, opts)

@@ -24,7 +24,9 @@ constexpr int kClasses = 5;
 // shared-memory size classes; the last one holds the LPs that keep their
 // tableau in a global workspace slice
 constexpr int kGlobal = kClasses - 1;
-constexpr size_t kClassMax[kClasses - 2] = {24 * 1024, 56 * 1024, 112 * 1024};   // 4th: device limit
+// The shared-memory classes hold LPs of which 8, 3, 2 and 1 fit one SM at a
+// time (bounds from the device's shared memory per SM, see class_bounds).
+constexpr int kPerSm[kClasses - 1] = {8, 3, 2, 1};
 constexpr int kCandidates[4] = {32, 64, 128, 256};
 
 struct DBlock {
@@ -167,6 +169,27 @@ size_t tsx::batch_smem_limit() {
     return optin > 0 ? (size_t)optin - stat - 256 : 0;
 }
 
+// Dynamic shared-memory bound of each shared-memory class: the largest LP
+// block of which kPerSm[q] fit on one SM next to each other (each block also
+// holds the kernel's static scratch and the per-block reservation).
+static void class_bounds(size_t* bound) {
+    int device = 0, per_sm = 0, reserved = 0;
+    cudaGetDevice(&device);
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device);
+    size_t stat = 0;
+    for (size_t v : {kernel_static_smem<32>(), kernel_static_smem<64>(), kernel_static_smem<128>(),
+                     kernel_static_smem<256>()})
+        stat = std::max(stat, v);
+    const size_t limit = tsx::batch_smem_limit();
+    for (int q = 0; q < kClasses - 1; ++q) {
+        const size_t share = (size_t)std::max(per_sm, 0) / (size_t)kPerSm[q];
+        const size_t over = stat + (size_t)std::max(reserved, 0);
+        bound[q] = share > over ? std::min(limit, (share - over) / 16 * 16) : 0;
+    }
+    bound[kClasses - 2] = limit;
+}
+
 bool tsx::batch_fits(int m, int n, size_t limit) {
     return m > 0 && n > 0 && batch_smem_bytes(m, n, condensed_ld(n)) <= limit;
 }
@@ -182,6 +205,8 @@ static lp_batch* batch_common(int count, const int* m, const int* n, cudaStream_
     current_allocator(&h->alloc, &h->dealloc, &h->actx);
     cudaDeviceGetAttribute(&h->nsm, cudaDevAttrMultiProcessorCount, h->device);
     const size_t limit = batch_smem_limit();
+    size_t bound[kClasses - 1];
+    class_bounds(bound);
     size_t gbytes = 0;
     h->lps.resize(count);
     for (int k = 0; k < count; ++k) {
@@ -199,7 +224,7 @@ static lp_batch* batch_common(int count, const int* m, const int* n, cudaStream_
         if (smem <= limit) {
             cls = kGlobal - 1;
             for (int q = 0; q < kGlobal - 1; ++q)
-                if (smem <= kClassMax[q]) { cls = q; break; }
+                if (smem <= bound[q]) { cls = q; break; }
             h->class_smem[cls] = std::max(h->class_smem[cls], smem);
             L.w_off = -1;
         } else {

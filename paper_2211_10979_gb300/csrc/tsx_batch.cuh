@@ -60,6 +60,8 @@ __host__ __device__ inline size_t batch_smem_bytes(int m, int n, int ldc) {
     return (bytes + 15) / 16 * 16;
 }
 
+constexpr int kRc = 4;        // scaled-pivot-row entries per lane kept in registers
+
 struct BArg {                 // entering candidate
     double v;                 // objective-row entry
     int var;                  // its variable (tie-break), INT_MAX if none
@@ -81,9 +83,8 @@ struct BatchScratch {
     int lp;
 };
 
-template <int NT>
-__device__ BArg batch_block_arg(BArg a, BatchScratch& s) {
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// Warp-wide entering candidate (every lane returns the warp's result).
+__device__ __forceinline__ BArg warp_barg(BArg a) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         BArg b;
@@ -94,34 +95,35 @@ __device__ BArg batch_block_arg(BArg a, BatchScratch& s) {
         b.fslot = __shfl_xor_sync(0xffffffffu, a.fslot, o);
         barg_merge(a, b);
     }
-    if (NT == 32) return a;
-    __syncthreads();
-    if (lane == 0) s.arg[w] = a;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        BArg r = s.arg[0];
-        for (int k = 1; k < NT / 32; ++k) barg_merge(r, s.arg[k]);
-        s.arg_out = r;
-    }
-    __syncthreads();
-    return s.arg_out;
+    return a;
 }
 
+__device__ __forceinline__ BArg barg_none() {
+    return BArg{__longlong_as_double(0x7ff0000000000000LL), INT_MAX, -1, INT_MAX, -1};
+}
+
+// Step 1 candidate of objective-row slot j (value v, variable var).
+__device__ __forceinline__ void barg_consider(BArg& a, double v, int vj, int j, double eps_d) {
+    if (v < -eps_d) {
+        if (v < a.v || (v == a.v && vj < a.var)) { a.v = v; a.var = vj; a.slot = j; }
+        if (vj < a.fvar) { a.fvar = vj; a.fslot = j; }
+    }
+}
+
+// Block-wide ratio-test minimum with one barrier: each warp reduces, lane 0
+// posts the warp's partial, every thread merges the posted partials.  The
+// partials' slots are next written after at least one more barrier.
 template <int NT>
 __device__ RatPart batch_block_rat(RatPart a, BatchScratch& s) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     a = warp_rat(a);
     if (NT == 32) return a;
-    __syncthreads();
     if (lane == 0) s.rat[w] = a;
     __syncthreads();
-    if (threadIdx.x == 0) {
-        RatPart r = s.rat[0];
-        for (int k = 1; k < NT / 32; ++k) rat_merge(r, s.rat[k]);
-        s.rat_out = r;
-    }
-    __syncthreads();
-    return s.rat_out;
+    RatPart r = s.rat[0];
+#pragma unroll
+    for (int k = 1; k < NT / 32; ++k) rat_merge(r, s.rat[k]);
+    return r;
 }
 
 // Solves LP `k` of the batch (NT threads) with its tableau at `smem` (shared
@@ -161,53 +163,45 @@ __device__ void batch_solve_one(const BatchParams& P, int k, unsigned char* smem
     if (bad) status = -1;   // LP_ERR_INVALID
     long long it = 0;
     int bland = P.rule == 1, degen = 0;
+    // Step 1 of the first pivot: warp 0 scans the objective row
+    if (warp == 0) {
+        BArg a0 = barg_none();
+        for (int j = lane; j < n; j += 32) barg_consider(a0, T[j], var[j], j, P.eps_d);
+        a0 = warp_barg(a0);
+        if (lane == 0) sc.arg_out = a0;
+    }
+    __syncthreads();
     while (status == kRunning) {
         // Step 1: entering slot (most negative objective-row entry; ties and
-        // Bland's rule by variable index)
-        BArg a{__longlong_as_double(0x7ff0000000000000LL), INT_MAX, -1, INT_MAX, -1};
-        for (int j = tid; j < n; j += NT) {
-            const double v = T[j];
-            if (v < -P.eps_d) {
-                const int vj = var[j];
-                if (v < a.v || (v == a.v && vj < a.var)) { a.v = v; a.var = vj; a.slot = j; }
-                if (vj < a.fvar) { a.fvar = vj; a.fslot = j; }
-            }
-        }
-        a = batch_block_arg<NT>(a, sc);
+        // Bland's rule by variable index), left by the previous update
+        const BArg a = sc.arg_out;
         const int qs = bland ? a.fslot : a.slot;
         if (qs < 0) { status = kOptimal; break; }
         if (it >= cap) { status = kIterLimit; break; }
-        // Step 2: minimum ratio on slot qs (ties: row, or basic variable in Bland mode)
+        // Step 2: minimum ratio on slot qs (ties: row, or basic variable in
+        // Bland mode); column qs is copied to F on the way
         RatPart best = rat_none();
+        if (tid == 0) F[0] = T[qs];
         for (int i = 1 + tid; i <= m; i += NT) {
             const double av = T[(size_t)i * ldc + qs];
+            F[i] = av;
             if (av > P.eps_p) {
                 RatPart cnd;
                 cnd.r = __ddiv_rn(T[(size_t)i * ldc + n], av);
                 cnd.i = i;
                 cnd.key = bland ? basis[i - 1] : i;
+                cnd.a = av;
+                cnd.pad = 0.0;
                 rat_merge(best, cnd);
             }
         }
         best = batch_block_rat<NT>(best, sc);
         if (best.i == INT_MAX) { status = kUnbounded; break; }
         const int p = best.i;
-        const double piv = T[(size_t)p * ldc + qs];
+        const double piv = best.a;
         if (!isfinite(piv) || !isfinite(best.r)) { status = kNumeric; break; }
-        // Step 3: pivot column and scaled pivot row staged first
-        for (int i = tid; i <= m; i += NT) F[i] = T[(size_t)i * ldc + qs];
+        // Step 3: scaled pivot row; the leaving variable takes slot qs
         for (int j = tid; j <= n; j += NT) R[j] = j == qs ? __ddiv_rn(1.0, piv) : __ddiv_rn(T[(size_t)p * ldc + j], piv);
-        __syncthreads();
-        for (int i = warp; i <= m; i += NW) {
-            double* row = T + (size_t)i * ldc;
-            if (i == p) {
-                for (int j = lane; j <= n; j += 32) row[j] = R[j];
-            } else {
-                const double f = F[i];
-                for (int j = lane; j <= n; j += 32) row[j] = __fma_rn(-f, R[j], j == qs ? 0.0 : row[j]);
-            }
-        }
-        __syncthreads();
         if (tid == 0) {
             const int leaving = basis[p - 1];
             basis[p - 1] = var[qs];
@@ -221,6 +215,39 @@ __device__ void batch_solve_one(const BatchParams& P, int k, unsigned char* smem
             } else {
                 degen = 0;
                 bland = 0;
+            }
+        }
+        __syncthreads();
+        // rank-1 update; the warp of row 0 also finds the next entering slot.
+        // The first kRc entries of R per lane stay in registers for all rows.
+        double rr[kRc];
+#pragma unroll
+        for (int t = 0; t < kRc; ++t) {
+            const int j = lane + 32 * t;
+            rr[t] = j <= n ? R[j] : 0.0;
+        }
+        for (int i = warp; i <= m; i += NW) {
+            double* row = T + (size_t)i * ldc;
+            if (i == p) {
+                for (int j = lane; j <= n; j += 32) row[j] = R[j];
+            } else if (i == 0) {
+                const double f = F[0];
+                BArg an = barg_none();
+                for (int j = lane; j <= n; j += 32) {
+                    const double v = __fma_rn(-f, R[j], j == qs ? 0.0 : row[j]);
+                    row[j] = v;
+                    if (j < n) barg_consider(an, v, var[j], j, P.eps_d);
+                }
+                an = warp_barg(an);
+                if (lane == 0) sc.arg_out = an;
+            } else {
+                const double f = F[i];
+#pragma unroll
+                for (int t = 0; t < kRc; ++t) {
+                    const int j = lane + 32 * t;
+                    if (j <= n) row[j] = __fma_rn(-f, rr[t], j == qs ? 0.0 : row[j]);
+                }
+                for (int j = lane + 32 * kRc; j <= n; j += 32) row[j] = __fma_rn(-f, R[j], j == qs ? 0.0 : row[j]);
             }
         }
         __syncthreads();
