@@ -59,6 +59,8 @@ def parse_args(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="serve: length of the stream")
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--serve-blocks", type=int, default=0, help="serve: grid cap per single-lane solve")
+    ap.add_argument("--serve-path", type=int, default=2,
+                    help="serve: single-lane solve path (1 persistent cooperative, 2 one launch per phase)")
     ap.add_argument("--batch-count", type=int, default=4096)
     ap.add_argument("--batch-threads", type=int, default=0,
                     help="batch: threads per LP (32/64/128/256); 0 = autotuned per size class")
@@ -635,10 +637,11 @@ def run_serve(args, rank, world, local):
     clocks = ClockSampler(local)
     clocks.start()
     served, st, t0 = play_stream(tsx, torch, dev, shapes, arrivals, seeds,
-                                 {"workers": args.serve_workers, "blocks_per_lp": args.serve_blocks})
+                                 {"workers": args.serve_workers, "blocks_per_lp": args.serve_blocks,
+                                  "path": args.serve_path})
     clk = clocks.stop()
     plain, st_plain, t0p = play_stream(tsx, torch, dev, shapes, arrivals, seeds,
-                                       {"workers": 1, "batch_small": 0})
+                                       {"workers": 1, "batch_small": 0, "path": 0})
 
     def summary(res, t_start):
         lat = np.array([r[1] for r in res])
@@ -664,7 +667,9 @@ def run_serve(args, rank, world, local):
         "config": {"workload": f"Poisson stream, {args.rate:.0f} LPs/s for {args.serve_seconds:.1f} s "
                                f"({count} LPs), m and n log-uniform in [32, 4096], inputs generated on "
                                "the device at arrival; continuous batching, 64 GiB admission budget",
-                   "workers": args.serve_workers, "batches": st["batches"], "batched_lps": st["batched_lps"],
+                   "workers": args.serve_workers, "blocks_per_lp": args.serve_blocks or "default",
+                   "single_lane_path": args.serve_path,
+                   "batches": st["batches"], "batched_lps": st["batched_lps"],
                    "peak_admitted_bytes": st["peak_bytes"]},
         "latency": {"p50_ms": s_srv["p50_ms"], "p99_ms": s_srv["p99_ms"], "mean_ms": s_srv["mean_ms"],
                     "max_ms": s_srv["max_ms"], "from": "scheduled arrival to result on the host"},

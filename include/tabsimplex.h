@@ -312,6 +312,11 @@ typedef struct {
                                      global memory one block per LP (pays off
                                      only when many such LPs wait together);
                                      0 (default): shared-memory LPs only        */
+    int path;                     /* lp_options.path of the single-lane solves;
+                                     default LP_PATH_MULTILAUNCH, whose kernels
+                                     overlap with other workers' solves (the
+                                     cooperative launches of the persistent
+                                     path largely run one at a time)            */
 } lps_options;
 
 typedef struct {

@@ -130,6 +130,7 @@ class lps_options(ctypes.Structure):
         ("small_max_dim", ctypes.c_int),
         ("blocks_per_lp", ctypes.c_int),
         ("batch_max_bytes", ctypes.c_longlong),
+        ("path", ctypes.c_int),
     ]
 
 

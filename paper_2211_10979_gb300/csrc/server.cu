@@ -141,6 +141,7 @@ void lps_options_init(lps_options* o) {
     o->small_max_dim = 0;
     o->blocks_per_lp = 0;
     o->batch_max_bytes = 0;
+    o->path = LP_PATH_MULTILAUNCH;
 }
 
 // Keeps the calling worker's last library error for lps_last_error.
@@ -162,6 +163,7 @@ static void solve_single(lp_server* sv, Request& r, cudaStream_t s) {
     lp_options_init(&o);
     o.precision = sv->opt.precision;
     o.blocks = sv->blocks;
+    o.path = sv->opt.path;
     o.stream = r.on_device ? (void*)s : nullptr;
     r.status = lp_solve(h, &o);
     if (r.status < 0) note_error(sv, "solve");
@@ -322,7 +324,7 @@ lps_t lps_open(const lps_options* opt) {
     else
         lps_options_init(&sv->opt);
     if (sv->opt.workers <= 0 || sv->opt.budget_bytes <= 0 || sv->opt.batch_max <= 0 || sv->opt.precision < 0 ||
-        sv->opt.precision > 1) {
+        sv->opt.precision > 1 || sv->opt.path < LP_PATH_AUTO || sv->opt.path > LP_PATH_MULTILAUNCH) {
         set_error("lps_open: invalid options");
         delete sv;
         return nullptr;

@@ -108,7 +108,7 @@ struct RecBufs {                     // FP64 recovery buffers
     int* singular = nullptr;
     double *M = nullptr, *inv = nullptr, *xS = nullptr, *yR = nullptr, *bR = nullptr, *cS = nullptr;
     double *rp = nullptr, *rd = nullptr, *aS = nullptr, *rho = nullptr, *venter = nullptr;
-    int *pivrow = nullptr, *used = nullptr, *S = nullptr, *Rr = nullptr;
+    int *pivrow = nullptr, *S = nullptr, *Rr = nullptr;
 };
 
 struct lp_handle {
@@ -571,7 +571,7 @@ static lp_status ensure_recovery(lp_handle* h, int k) {
         const size_t o_M = cv.take(K * 2 * K * 8), o_inv = cv.take(K * K * 8);
         size_t o_v[9];
         for (auto& o : o_v) o = cv.take(K * 8);
-        size_t o_i[4];
+        size_t o_i[3];
         for (auto& o : o_i) o = cv.take(K * 4);
         if (!dev_alloc_block(h, r.kb, align_up(cv.off, 256))) {
             set_error("lp_solve: allocation of the recovery matrices (k = %d) failed", k);
@@ -583,8 +583,8 @@ static lp_status ensure_recovery(lp_handle* h, int k) {
         r.inv = (double*)(b + o_inv);
         double** vs[9] = {&r.xS, &r.yR, &r.bR, &r.cS, &r.rp, &r.rd, &r.aS, &r.rho, &r.venter};
         for (int t = 0; t < 9; ++t) *vs[t] = (double*)(b + o_v[t]);
-        int** is[4] = {&r.pivrow, &r.used, &r.S, &r.Rr};
-        for (int t = 0; t < 4; ++t) *is[t] = (int*)(b + o_i[t]);
+        int** is[3] = {&r.pivrow, &r.S, &r.Rr};
+        for (int t = 0; t < 3; ++t) *is[t] = (int*)(b + o_i[t]);
         r.kcap = kc;
     }
     return LP_OPTIMAL;
@@ -610,22 +610,25 @@ static lp_status recover_factor(lp_handle* h, const lp_options& o, cudaStream_t 
     if (k > 0) {
         const size_t kk = (size_t)k;
         k_rec_gather<<<grid_for((long long)(2 * kk * kk), 256, 152 * 16), 256, 0, s>>>(n, h->A, r.S, r.Rr, k, r.M);
-        CUDA_TRY(cudaMemsetAsync(r.used, 0, kk * 4, s), LP_ERR_CUDA);
         CUDA_TRY(cudaMemsetAsync(r.singular, 0, 4, s), LP_ERR_CUDA);
         k_reset_state<<<1, 32, 0, s>>>(r.rst);
         int nsm = 0, per = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rec_gauss_jordan<256>, 256, 0);
+        const size_t bits = sizeof(unsigned) * ((kk + 31) / 32);
+        if (bits > 48 * 1024) {
+            set_error("lp_solve: k = %d structural basic variables exceed the refactorisation's limit", k);
+            return LP_ERR_INVALID;
+        }
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rec_gauss_jordan<256>, 256, bits);
         const int g = std::max(1, std::min(nsm * std::max(per, 1), grid_for((long long)(2 * kk * kk), 256, 1 << 20)));
         int* sg = r.singular;
         int* pv = r.pivrow;
-        int* us = r.used;
         double* Mx = r.M;
         DevState* rs = r.rst;
         long long to = std::max(0LL, o.barrier_timeout_ns);
         int kv = k;
-        void* args[] = {&Mx, &kv, &pv, &us, &sg, &rs, &to};
-        CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_rec_gauss_jordan<256>, g, 256, args, 0, s), LP_ERR_CUDA);
+        void* args[] = {&Mx, &kv, &pv, &sg, &rs, &to};
+        CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_rec_gauss_jordan<256>, g, 256, args, bits, s), LP_ERR_CUDA);
         k_rec_finish<<<grid_for((long long)(kk * kk), 256, 152 * 16), 256, 0, s>>>(r.M, k, r.pivrow, r.inv);
         k_rec_gather_rhs<<<grid_for(k, 256, 1024), 256, 0, s>>>(h->b, h->c, r.S, r.Rr, k, r.bR, r.cS);
         const int gw = grid_for(32LL * k, 256, 4096);

@@ -53,18 +53,24 @@ __device__ __forceinline__ void piv_merge(PivPart& a, const PivPart& b) {
 // yet, lowest row on ties), then the other rows subtract their multiple of the
 // pivot row on columns > c.  Rows are not swapped (pivrow[c] records the row)
 // and the pivot rows are scaled at the end (k_rec_finish).  Sets *singular if a
-// pivot is zero.
+// pivot is zero.  Each block keeps the used rows in its own shared-memory
+// bitmap (ceil(k / 32) words of dynamic shared memory), so no block's choice
+// can see a later step's mark.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_rec_gauss_jordan(double* M, int k, int* pivrow, int* used,
-                                                        int* singular, DevState* st, long long timeout_ns) {
+__global__ void __launch_bounds__(NT) k_rec_gauss_jordan(double* M, int k, int* pivrow, int* singular,
+                                                        DevState* st, long long timeout_ns) {
     __shared__ PivPart sp[NT / 32];
     __shared__ PivPart sbest;
     __shared__ BlockScratch s;
+    extern __shared__ unsigned used_bits[];
     const size_t w2 = 2 * (size_t)k;
+    const int nwords = (k + 31) / 32;
+    for (int w = threadIdx.x; w < nwords; w += NT) used_bits[w] = 0u;
+    __syncthreads();
     for (int c = 0; c < k; ++c) {
         PivPart best{-1.0, INT_MAX};
         for (int r = threadIdx.x; r < k; r += NT)
-            if (!__ldcg(used + r)) piv_merge(best, PivPart{fabs(__ldcg(M + r * w2 + c)), r});
+            if (!((used_bits[r >> 5] >> (r & 31)) & 1u)) piv_merge(best, PivPart{fabs(__ldcg(M + r * w2 + c)), r});
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
             PivPart b{__shfl_xor_sync(0xffffffffu, best.v, o), __shfl_xor_sync(0xffffffffu, best.r, o)};
@@ -92,9 +98,9 @@ __global__ void __launch_bounds__(NT) k_rec_gauss_jordan(double* M, int k, int* 
             const double l = __ldcg(M + r * w2 + c) * ip;
             if (l != 0.0) M[r * w2 + j] = __fma_rn(-l, __ldcg(M + pr * w2 + j), __ldcg(M + r * w2 + j));
         }
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
-            used[pr] = 1;
-            pivrow[c] = pr;
+        if (threadIdx.x == 0) {
+            used_bits[pr >> 5] |= 1u << (pr & 31);   // this block's copy; read after the barrier
+            if (blockIdx.x == 0) pivrow[c] = pr;
         }
         if (!grid_barrier(st, timeout_ns, s)) return;
     }

@@ -154,3 +154,38 @@ def test_fp32_full_size_16384(tsx):
     assert pv <= 1e-9 and dv <= 1e-9
     assert abs(c @ sol32.x - b @ sol32.y) <= 1e-9 * abs(sol64.obj)
     assert st32["primal_violation"] <= 1e-9 and st32["dual_violation"] <= 1e-9
+
+
+@pytest.mark.parametrize("path", [1, 2])
+def test_concurrent_solves_equal_their_solo_runs(tsx, path):
+    # eight host threads solve medium LPs at once on full grids, so the
+    # refactorisation's blocks run interleaved with other solves' kernels;
+    # every result must equal the same solve run alone
+    import threading
+    shapes = [(300, 500), (640, 410), (512, 512), (800, 350)] * 6
+    problems = [lpgen.dense_lp(m, n, 600 + k) for k, (m, n) in enumerate(shapes)]
+    opts = dict(precision=tsx.LP_PREC_FP32, path=path, blocks=304)
+
+    def solve(k):
+        with tsx.Problem(*problems[k]) as pr:
+            st = pr.solve(tsx.options(**opts))
+            return st, pr.solution()
+
+    alone = [solve(k) for k in range(len(problems))]
+    together = [None] * len(problems)
+
+    def worker(idx):
+        for k in idx:
+            together[k] = solve(k)
+
+    th = [threading.Thread(target=worker, args=(range(j, len(problems), 8),)) for j in range(8)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    for k in range(len(problems)):
+        (st1, s1), (st2, s2) = alone[k], together[k]
+        assert st1 == st2 == tsx.LP_OPTIMAL, k
+        assert s1.obj == s2.obj and s1.iters == s2.iters, k
+        np.testing.assert_array_equal(s1.x, s2.x)
+        np.testing.assert_array_equal(s1.y, s2.y)
