@@ -49,6 +49,8 @@ def parse_args(argv=None):
     ap.add_argument("--seeds", type=int, default=3, help="distinct LPs cycled through the steps")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--skip-zero", type=int, default=1)
+    ap.add_argument("--layout", choices=["condensed", "full"], default="condensed",
+                    help="device tableau: nonbasic columns + RHS (condensed) or the whole Table I (full)")
     ap.add_argument("--path", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--blocks", type=int, default=0)
@@ -256,8 +258,9 @@ def run_gpu(args, rank, world, local):
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
     prec = tsx.LP_PREC_FP32 if args.precision == "fp32" else tsx.LP_PREC_FP64
+    layout = tsx.LP_LAYOUT_FULL if args.layout == "full" else tsx.LP_LAYOUT_CONDENSED
     opts = tsx.options(stream=sptr, skip_zero_columns=args.skip_zero, path=args.path,
-                       threads=args.threads, blocks=args.blocks, precision=prec)
+                       threads=args.threads, blocks=args.blocks, precision=prec, layout=layout)
 
     x = np.empty(n)
     y = np.empty(m)
@@ -314,7 +317,7 @@ def run_gpu(args, rank, world, local):
         try:
             st = tsx.lp_solve(h, tsx.options(skip_zero_columns=args.skip_zero, path=args.path,
                                              threads=args.threads, blocks=args.blocks,
-                                             precision=prec))
+                                             precision=prec, layout=layout))
             if st != tsx.LP_OPTIMAL:
                 raise RuntimeError(f"solve ended {tsx.STATUS_NAMES.get(st, st)}")
             _, it = tsx.lp_get_solution(h, xo, yo, oo, bo)
@@ -382,6 +385,7 @@ def run_gpu(args, rank, world, local):
             cpu = oracle_sample(m, n, seeds[0], args.cpu_seconds)
             cpu.pop("seconds")
             cpu.pop("pivots")
+        elem = 4 if args.precision == "fp32" else 8
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
@@ -394,7 +398,8 @@ def run_gpu(args, rank, world, local):
                             "A~U[1,10), b~U[100,1000), c~U[1,10); slack basis; Dantzig)",
                 "m": m, "n": n, "seeds_per_rank": len(seeds),
                 "pivots_per_step": pivots / args.steps,
-                "l2": f"inputs larger than L2 (tableau {(m + 1) * stats[0]['ld'] * 8 / 1e9:.2f} GB)",
+                "l2": f"inputs larger than L2 (tableau {(m + 1) * stats[0]['ld'] * elem / 1e9:.2f} GB)",
+                "layout": args.layout,
                 "path": {1: "persistent", 2: "multilaunch"}.get(stats[0]["path"]),
                 "grid": stats[0]["grid"], "block": stats[0]["block"],
                 "skip_zero_columns": args.skip_zero,

@@ -98,7 +98,18 @@ typedef struct {
                                      (default 1e-9, absolute)                   */
     int cleanup_max;              /* cap on FP64 cleanup pivots (default 1000);
                                      beyond it the solve ends LP_ERR_NUMERIC    */
+    int layout;                   /* LP_LAYOUT_CONDENSED (default): the device
+                                     keeps the objective row and constraint
+                                     rows over the n nonbasic columns plus the
+                                     right-hand side ((m+1) x (n+1)); the basic
+                                     columns of Table I are exact unit vectors,
+                                     so every stored value, pivot and result is
+                                     the full tableau's, with half the bytes
+                                     at m = n.  LP_LAYOUT_FULL: the Table I
+                                     tableau itself ((m+1) x (n+m+1))           */
 } lp_options;
+
+enum { LP_LAYOUT_CONDENSED = 0, LP_LAYOUT_FULL = 1 };
 
 /* Per-solve measurements (device time from CUDA events on the solve stream). */
 typedef struct {
@@ -106,10 +117,12 @@ typedef struct {
     double build_ms;              /* tableau build (Initialization Step)        */
     double pivot_ms;              /* all pivot kernels (Steps 1-3 + iterate)    */
     long long kernel_launches;    /* kernels launched by the solve              */
-    double dense_update_bytes;    /* sum over pivots of 2 (m+1) W s bytes       */
-    double update_bytes;          /* sum over pivots of the bytes Step 3 has to
-                                     move: 64 (m + 1) bytes per 32-byte column
-                                     group it updates (read + write)            */
+    double dense_update_bytes;    /* sum over pivots of 2 (m+1) (n+m+1) s bytes
+                                     (the full tableau, read + written)         */
+    double update_bytes;          /* sum over pivots of the bytes the pivot
+                                     kernels have to move: 64 bytes per row and
+                                     32-byte column group Step 3 updates (read +
+                                     write), plus Steps 1-2 and the staging     */
     int path;                     /* LP_PATH_PERSISTENT or LP_PATH_MULTILAUNCH  */
     int grid;                     /* blocks of the pivot kernels                */
     int block;                    /* threads per block                          */
@@ -126,6 +139,7 @@ typedef struct {
     double primal_violation;      /* FP32 path: max(0, -min basic value)        */
     double dual_violation;        /* FP32 path: max(0, -min objective-row entry)*/
     double gap;                   /* FP32 path: |c^T x - b^T y|                 */
+    int layout;                   /* LP_LAYOUT_CONDENSED or LP_LAYOUT_FULL      */
 } lp_stats;
 
 /* Fill *opt with the defaults listed above.  NULL is ignored. */
@@ -398,7 +412,8 @@ lp_status lp_generate_dense(int m, int n, unsigned long long seed, double *dA, d
  *   opt         options as for lp_solve (NULL = defaults); opt->stream is the
  *               stream used; log_capacity must be 0 and blocks <= 1024
  *   iters       host output (may be NULL): pivots performed
- * The work buffers need 8 (m + 1) + 9 ld + 16 ceil(ld / 128) + 32 * 1024 bytes
+ * The tableau is the full Table I layout (opt->layout is ignored).
+ * The work buffers need 8 (m + 1) + 9 ld + 32 ceil(ld / 128) + 32 * 1024 bytes
  * plus about 1.5 KiB of alignment and state, at most LP_NOALLOC_SCRATCH_BYTES
  * (about m + ld <= 2.2e5, e.g. m = n = 70000); larger sizes return LP_ERR_INVALID
  * before any device work, with the sizes in lp_last_error().

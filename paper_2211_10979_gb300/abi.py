@@ -19,6 +19,7 @@ LP_ERR_INVALID, LP_ERR_NOMEM, LP_ERR_CUDA, LP_ERR_TIMEOUT, LP_ERR_STATE = -1, -2
 STATUS_NAMES = {0: "OPTIMAL", 1: "UNBOUNDED", 2: "ITER_LIMIT", 3: "NUMERIC", -1: "INVALID",
                 -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE", 100: "PENDING"}
 LP_RULE_DANTZIG, LP_RULE_BLAND = 0, 1
+LP_LAYOUT_CONDENSED, LP_LAYOUT_FULL = 0, 1
 LP_PATH_AUTO, LP_PATH_PERSISTENT, LP_PATH_MULTILAUNCH = 0, 1, 2
 LP_PREC_FP64, LP_PREC_FP32 = 0, 1
 
@@ -55,6 +56,7 @@ class lp_options(ctypes.Structure):
         ("eps_p_fp32", ctypes.c_double),
         ("recover_tol", ctypes.c_double),
         ("cleanup_max", ctypes.c_int),
+        ("layout", ctypes.c_int),
     ]
 
 
@@ -79,6 +81,7 @@ class lp_stats(ctypes.Structure):
         ("primal_violation", ctypes.c_double),
         ("dual_violation", ctypes.c_double),
         ("gap", ctypes.c_double),
+        ("layout", ctypes.c_int),
     ]
 
     def as_dict(self):

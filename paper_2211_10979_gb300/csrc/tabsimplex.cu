@@ -84,10 +84,13 @@ struct Carve {
 };
 
 // ---------------------------------------------------------------- handle
-struct Work {                        // pivot buffers for one precision
+struct Work {                        // pivot buffers for one precision and layout
     Block blk;
     int elem = 0;                    // bytes per tableau entry (8 or 4), 0 = none
+    int cond = -1;                   // 1: condensed tableau, 0: full
+    int Ws = 0;                      // stored width: n + 1 (condensed) or n + m + 1
     int ld = 0;
+    int* var = nullptr;              // condensed: variable of each column slot (n)
     void* T = nullptr;
     void* F = nullptr;
     void* R = nullptr;
@@ -210,6 +213,7 @@ void lp_options_init(lp_options* o) {
     o->eps_p_fp32 = 1e-6;
     o->recover_tol = 1e-9;
     o->cleanup_max = 1000;
+    o->layout = LP_LAYOUT_CONDENSED;
 }
 
 static void destroy_impl(lp_handle* h) {
@@ -361,11 +365,12 @@ lp_t lp_create_device(int m, int n, const double* dA, const double* db, const do
 static int tableau_ld(int W, int elem) { return (int)align_up((size_t)W, 128 / elem); }
 
 // (Re)allocates the pivot buffers for a tableau of `elem`-byte entries.
-static lp_status ensure_work(lp_handle* h, int elem) {
-    if (h->work.elem == elem && h->work.blk.ptr) return LP_OPTIMAL;
+static lp_status ensure_work(lp_handle* h, int elem, int cond) {
+    if (h->work.elem == elem && h->work.cond == cond && h->work.blk.ptr) return LP_OPTIMAL;
     dev_free(h, h->work.blk);
     h->work = Work{};
-    const int ld = tableau_ld(h->W, elem);
+    const int Ws = cond ? h->n + 1 : h->W;
+    const int ld = tableau_ld(Ws, elem);
     const int E = 32 / elem;
     const int nstrips = (ld + 32 * E - 1) / (32 * E);
     Carve cv;
@@ -375,13 +380,17 @@ static lp_status ensure_work(lp_handle* h, int elem) {
     const size_t o_act = cv.take((size_t)(ld / E) * sizeof(int));
     const size_t o_cp = cv.take((size_t)nstrips * sizeof(ArgPart));
     const size_t o_rp = cv.take((size_t)h->max_grid * sizeof(RatPart));
+    const size_t o_var = cv.take((size_t)h->n * sizeof(int));
     if (!dev_alloc_block(h, h->work.blk, align_up(cv.off, 256))) {
         set_error("lp_solve: device allocation of %zu bytes for the tableau failed", cv.off);
         return LP_ERR_NOMEM;
     }
     char* base = (char*)h->work.blk.ptr;
     h->work.elem = elem;
+    h->work.cond = cond;
+    h->work.Ws = Ws;
     h->work.ld = ld;
+    h->work.var = (int*)(base + o_var);
     h->work.T = base + o_T;
     h->work.F = base + o_F;
     h->work.R = base + o_R;
@@ -430,14 +439,17 @@ static lp_status run_multilaunch(const Params<V>& P, int grid, cudaStream_t s, l
 // Pivot-kernel parameters over a tableau of V with the given buffers.
 template <typename V>
 static Params<V> make_params(int m, int n, int ld, V* T, V* F, V* R, int* act, ArgPart* cpart, RatPart* rpart,
-                             DevState* st, int* basis, const lp_options& o, double eps_d, double eps_p) {
+                             DevState* st, int* basis, const lp_options& o, double eps_d, double eps_p,
+                             int* var = nullptr) {
     constexpr int E = Lanes<V>::E;
     Params<V> P{};
     P.T = T;
     P.ld = ld;
     P.m = m;
     P.n = n;
-    P.W = n + m + 1;
+    P.cond = var ? 1 : 0;
+    P.var = var;
+    P.W = var ? n + 1 : n + m + 1;
     P.basis = basis;
     P.F = F;
     P.R = R;
@@ -477,7 +489,8 @@ static lp_status pivot_phase(lp_handle* h, const lp_options& o, cudaStream_t s, 
     const int m = h->m, n = h->n;
     const int ld = h->work.ld;
     Params<V> P = make_params<V>(m, n, ld, (V*)h->work.T, (V*)h->work.F, (V*)h->work.R, h->work.act,
-                                 h->work.cpart, h->work.rpart, h->st, h->basis, o, eps_d, eps_p);
+                                 h->work.cpart, h->work.rpart, h->st, h->basis, o, eps_d, eps_p,
+                                 h->work.cond ? h->work.var : nullptr);
     P.log_cap = o.log_capacity > 0 ? h->log_cap : 0;
     P.qlog = P.log_cap ? (int*)h->logs.ptr : nullptr;
     P.plog = P.log_cap ? (int*)h->logs.ptr + P.log_cap : nullptr;
@@ -500,7 +513,8 @@ static lp_status pivot_phase(lp_handle* h, const lp_options& o, cudaStream_t s, 
         constexpr int E = Lanes<V>::E;
         const size_t groups = (size_t)(m + 1) * (size_t)(ld / E);
         int g = (int)std::min<size_t>((groups + 255) / 256, 152 * 16);
-        k_build<V><<<g, 256, 0, s>>>(m, n, h->W, ld, h->A, h->b, h->c, (V*)h->work.T, h->basis);
+        k_build<V><<<g, 256, 0, s>>>(m, n, h->work.Ws, ld, h->A, h->b, h->c, (V*)h->work.T, h->basis,
+                                     h->work.cond ? h->work.var : nullptr);
     }
     CUDA_TRY(cudaGetLastError(), LP_ERR_CUDA);
     cudaEventRecord(h->ev[1], s);
@@ -794,7 +808,7 @@ static lp_status solve_nt(lp_handle* h, const lp_options& o, cudaStream_t s) {
         h->log_cap = o.log_capacity;
     }
     const bool fp32 = o.precision == LP_PREC_FP32;
-    lp_status st = ensure_work(h, fp32 ? 4 : 8);
+    lp_status st = ensure_work(h, fp32 ? 4 : 8, o.layout == LP_LAYOUT_CONDENSED ? 1 : 0);
     if (st != LP_OPTIMAL) return st;
 
     h->stats = lp_stats{};
@@ -831,6 +845,7 @@ static lp_status solve_nt(lp_handle* h, const lp_options& o, cudaStream_t s) {
     h->stats.grid = grid;
     h->stats.block = NT;
     h->stats.ld = ld;
+    h->stats.layout = h->work.cond ? LP_LAYOUT_CONDENSED : LP_LAYOUT_FULL;
     h->stats.precision = o.precision;
     h->stats.pivot_status = (int)st;
     for (int k = 0; k < 6; ++k) h->stats.phase_ms[k] = 1e-6 * (double)hs.phase_ns[k];
@@ -870,7 +885,8 @@ lp_status lp_solve(lp_t h, const lp_options* opt) {
         lp_options_init(&o);
     if (!(o.eps_d >= 0.0) || !(o.eps_p >= 0.0) || o.rule < 0 || o.rule > 1 || o.path < 0 || o.path > 2 ||
         o.log_capacity < 0 || o.precision < 0 || o.precision > 1 || !(o.eps_d_fp32 >= 0.0) ||
-        !(o.eps_p_fp32 >= 0.0) || !(o.recover_tol >= 0.0) || o.cleanup_max < 0) {
+        !(o.eps_p_fp32 >= 0.0) || !(o.recover_tol >= 0.0) || o.cleanup_max < 0 ||
+        (o.layout != LP_LAYOUT_CONDENSED && o.layout != LP_LAYOUT_FULL)) {
         set_error("lp_solve: invalid options");
         return LP_ERR_INVALID;
     }
@@ -902,15 +918,20 @@ lp_status lp_get_solution(lp_t h, double* x, double* y, double* obj, int* basis,
     CUDA_TRY(cudaStreamWaitEvent(s, h->ready, 0), LP_ERR_CUDA);
     const int m = h->m, n = h->n;
     if ((x || y || obj) && !h->sol_ready) {
-        const int ld = h->work.ld;
+        const int ld = h->work.ld, Ws = h->work.Ws, cond = h->work.cond;
         int g = std::min((n + m + 1 + 255) / 256, 1024);
         int gx = std::min((m + 255) / 256, 1024);
+        int gy = std::min((n + 255) / 256, 1024);
         if (h->work.elem == 8) {
-            k_extract_dense<double><<<g, 256, 0, s>>>(m, n, h->W, ld, (const double*)h->work.T, h->sol);
-            k_extract_x<double><<<gx, 256, 0, s>>>(m, n, h->W, ld, (const double*)h->work.T, h->basis, h->sol);
+            const double* T = (const double*)h->work.T;
+            k_extract_dense<double><<<g, 256, 0, s>>>(m, n, Ws, ld, T, cond, h->sol);
+            if (cond) k_extract_y_cond<double><<<gy, 256, 0, s>>>(m, n, T, h->work.var, h->sol);
+            k_extract_x<double><<<gx, 256, 0, s>>>(m, n, Ws, ld, T, h->basis, h->sol);
         } else {
-            k_extract_dense<float><<<g, 256, 0, s>>>(m, n, h->W, ld, (const float*)h->work.T, h->sol);
-            k_extract_x<float><<<gx, 256, 0, s>>>(m, n, h->W, ld, (const float*)h->work.T, h->basis, h->sol);
+            const float* T = (const float*)h->work.T;
+            k_extract_dense<float><<<g, 256, 0, s>>>(m, n, Ws, ld, T, cond, h->sol);
+            if (cond) k_extract_y_cond<float><<<gy, 256, 0, s>>>(m, n, T, h->work.var, h->sol);
+            k_extract_x<float><<<gx, 256, 0, s>>>(m, n, Ws, ld, T, h->basis, h->sol);
         }
         CUDA_TRY(cudaGetLastError(), LP_ERR_CUDA);
     }
@@ -941,6 +962,33 @@ lp_status lp_get_tableau(lp_t h, double* T) {
     cudaStream_t s = h->stream;
     CUDA_TRY(cudaStreamWaitEvent(s, h->ready, 0), LP_ERR_CUDA);
     const size_t rows = (size_t)h->m + 1, W = (size_t)h->W;
+    if (h->work.cond) {
+        // condensed: the full Table I tableau is rebuilt on the device
+        Block tmp;
+        const size_t o_slot = align_up(rows * W * sizeof(double), 256);
+        if (!dev_alloc_block(h, tmp, o_slot + (size_t)(h->n + h->m) * sizeof(int))) {
+            set_error("lp_get_tableau: allocation of the expanded copy failed");
+            return LP_ERR_NOMEM;
+        }
+        double* out = (double*)tmp.ptr;
+        int* slot_of = (int*)((char*)tmp.ptr + o_slot);
+        const int m = h->m, n = h->n;
+        k_slot_of<<<grid_for(n + m, 256, 1024), 256, 0, s>>>(m, n, h->work.var, slot_of);
+        k_slot_of_set<<<grid_for(n, 256, 1024), 256, 0, s>>>(n, h->work.var, slot_of);
+        const int ge = grid_for((long long)(rows * W), 256, 152 * 16);
+        if (h->work.elem == 8)
+            k_expand_cond<double><<<ge, 256, 0, s>>>(m, n, h->work.ld, (const double*)h->work.T, h->work.var,
+                                                     slot_of, out);
+        else
+            k_expand_cond<float><<<ge, 256, 0, s>>>(m, n, h->work.ld, (const float*)h->work.T, h->work.var,
+                                                    slot_of, out);
+        k_expand_units<<<grid_for(m, 256, 1024), 256, 0, s>>>(m, n, h->basis, out);
+        CUDA_TRY(cudaGetLastError(), LP_ERR_CUDA);
+        CUDA_TRY(cudaMemcpyAsync(T, out, rows * W * sizeof(double), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+        CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
+        dev_free(h, tmp);
+        return LP_OPTIMAL;
+    }
     if (h->work.elem == 8) {
         CUDA_TRY(cudaMemcpy2DAsync(T, W * sizeof(double), h->work.T, (size_t)h->work.ld * sizeof(double),
                                    W * sizeof(double), rows, cudaMemcpyDeviceToHost, s),
@@ -1070,7 +1118,7 @@ static lp_status noalloc_nt(int m, int n, const double* dA, const double* db, co
     {
         const size_t groups = (size_t)(m + 1) * (size_t)(ld / 4);
         int g = (int)std::min<size_t>((groups + 255) / 256, 152 * 16);
-        k_build<double><<<g, 256, 0, s>>>(m, n, n + m + 1, ld, dA, db, dc, dT, dbasis);
+        k_build<double><<<g, 256, 0, s>>>(m, n, n + m + 1, ld, dA, db, dc, dT, dbasis, nullptr);
     }
     CUDA_TRY(cudaGetLastError(), LP_ERR_CUDA);
     if (path == LP_PATH_PERSISTENT) {

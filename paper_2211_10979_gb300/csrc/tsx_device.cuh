@@ -44,10 +44,13 @@ constexpr int kMaxWarps = 32;      // warps per block upper bound (1024 threads)
 // status codes (same values as lp_status in tabsimplex.h)
 constexpr int kOptimal = 0, kUnbounded = 1, kIterLimit = 2, kNumeric = 3, kTimeout = -4;
 
-struct ArgPart {      // best entering candidate of a column range
+struct __align__(16) ArgPart {   // best entering candidate of a column range
     double v;         // most negative objective-row entry (< -eps_d), +inf if none
-    int j;            // its column (lowest on ties), INT_MAX if none
-    int jfirst;       // lowest column with entry < -eps_d (Bland), INT_MAX if none
+    int key;          // its variable (lowest on ties), INT_MAX if none
+    int slot;         // its column in the stored tableau
+    int fkey;         // lowest variable with entry < -eps_d (Bland), INT_MAX if none
+    int fslot;        // its column
+    int pad[2];
 };
 
 struct __align__(16) RatPart {   // best leaving candidate of a row range
@@ -70,6 +73,7 @@ struct DevState {
     double theta;                      // minimum ratio of the current pivot
     unsigned bar_count;                // grid barrier: blocks arrived
     unsigned bar_gen;                  // grid barrier: generation
+    int qvar;                          // entering variable (one-launch-per-phase path)
     unsigned nact;                     // active 32-B column groups of this pivot
     unsigned next_slot;                // P4 work counter (slots handed out)
     long long phase_ns[6];             // block 0's time per phase: work of
@@ -102,6 +106,8 @@ struct Params {
     long long timeout_ns;
     int nstrips;         // ceil(ld / (32 E)): warp strips of the objective row
     int skip_zero;       // leave column groups whose R entries are all zero
+    int cond;            // 1: condensed tableau (nonbasic columns + RHS), 0: full
+    int* var;            // condensed: n, the variable held by each column slot
 };
 
 // ------------------------------------------------------------------ helpers
@@ -193,26 +199,37 @@ __device__ __forceinline__ bool sector_nonzero(const Sector<V>& s) {
     return nz;
 }
 
-__device__ __forceinline__ ArgPart arg_none() { return ArgPart{__longlong_as_double(0x7ff0000000000000LL), INT_MAX, INT_MAX}; }
+__device__ __forceinline__ ArgPart arg_none() {
+    return ArgPart{__longlong_as_double(0x7ff0000000000000LL), INT_MAX, INT_MAX, INT_MAX, INT_MAX, {0, 0}};
+}
 __device__ __forceinline__ RatPart rat_none() { return RatPart{__longlong_as_double(0x7ff0000000000000LL), INT_MAX, INT_MAX, 0.0, 0.0}; }
 
-// (v, j) lexicographic minimum: the most negative entry, lowest column on ties.
+// (v, key) lexicographic minimum: the most negative entry, lowest variable on
+// ties; and the lowest candidate variable (Bland).  The key of a column is its
+// variable: the column index itself in the full tableau, var[] in the
+// condensed one.
 __device__ __forceinline__ void arg_merge(ArgPart& a, const ArgPart& b) {
-    if (b.v < a.v || (b.v == a.v && b.j < a.j)) { a.v = b.v; a.j = b.j; }
-    a.jfirst = min(a.jfirst, b.jfirst);
+    if (b.v < a.v || (b.v == a.v && b.key < a.key)) { a.v = b.v; a.key = b.key; a.slot = b.slot; }
+    if (b.fkey < a.fkey) { a.fkey = b.fkey; a.fslot = b.fslot; }
 }
 
-__device__ __forceinline__ void arg_consider(ArgPart& a, double v, int j, int jend, double eps_d) {
+__device__ __forceinline__ void arg_consider(ArgPart& a, double v, int j, int key, int jend, double eps_d) {
     if (j < jend && v < -eps_d) {
-        if (v < a.v || (v == a.v && j < a.j)) { a.v = v; a.j = j; }
-        a.jfirst = min(a.jfirst, j);
+        if (v < a.v || (v == a.v && key < a.key)) { a.v = v; a.key = key; a.slot = j; }
+        if (key < a.fkey) { a.fkey = key; a.fslot = j; }
     }
 }
 
+// Columns j .. j+E-1 of the objective row; var == null: full tableau (key = j).
 template <typename V>
-__device__ __forceinline__ void arg_consider_sector(ArgPart& a, const Sector<V>& s, int j, int jend, double eps_d) {
+__device__ __forceinline__ void arg_consider_sector(ArgPart& a, const Sector<V>& s, int j, int jend, double eps_d,
+                                                    const int* var) {
 #pragma unroll
-    for (int e = 0; e < Lanes<V>::E; ++e) arg_consider(a, (double)s.v[e], j + e, jend, eps_d);
+    for (int e = 0; e < Lanes<V>::E; ++e) {
+        const int jj = j + e;
+        const int key = (var && jj < jend) ? __ldcg(var + jj) : jj;
+        arg_consider(a, (double)s.v[e], jj, key, jend, eps_d);
+    }
 }
 
 // (r, key) lexicographic minimum: smallest ratio, lowest key on ties.
@@ -225,8 +242,10 @@ __device__ __forceinline__ ArgPart warp_arg(ArgPart a) {
     for (int o = 16; o > 0; o >>= 1) {
         ArgPart b;
         b.v = __shfl_xor_sync(0xffffffffu, a.v, o);
-        b.j = __shfl_xor_sync(0xffffffffu, a.j, o);
-        b.jfirst = __shfl_xor_sync(0xffffffffu, a.jfirst, o);
+        b.key = __shfl_xor_sync(0xffffffffu, a.key, o);
+        b.slot = __shfl_xor_sync(0xffffffffu, a.slot, o);
+        b.fkey = __shfl_xor_sync(0xffffffffu, a.fkey, o);
+        b.fslot = __shfl_xor_sync(0xffffffffu, a.fslot, o);
         arg_merge(a, b);
     }
     return a;
@@ -248,12 +267,14 @@ __device__ __forceinline__ RatPart warp_rat(RatPart a) {
 // Partials are read by other blocks after a barrier: 128-bit L2 accesses.
 __device__ __forceinline__ void store_arg(ArgPart* dst, const ArgPart& a) {
     long long bits = __double_as_longlong(a.v);
-    __stcg(reinterpret_cast<int4*>(dst), make_int4((int)(bits & 0xffffffff), (int)(bits >> 32), a.j, a.jfirst));
+    __stcg(reinterpret_cast<int4*>(dst), make_int4((int)(bits & 0xffffffff), (int)(bits >> 32), a.key, a.slot));
+    __stcg(reinterpret_cast<int4*>(dst) + 1, make_int4(a.fkey, a.fslot, 0, 0));
 }
 __device__ __forceinline__ ArgPart load_arg(const ArgPart* src) {
     int4 w = __ldcg(reinterpret_cast<const int4*>(src));
+    int4 u = __ldcg(reinterpret_cast<const int4*>(src) + 1);
     long long bits = ((long long)(unsigned)w.y << 32) | (unsigned)w.x;
-    return ArgPart{__longlong_as_double(bits), w.z, w.w};
+    return ArgPart{__longlong_as_double(bits), w.z, w.w, u.x, u.y, {0, 0}};
 }
 __device__ __forceinline__ void store_rat(RatPart* dst, const RatPart& a) {
     long long bits = __double_as_longlong(a.r);
@@ -360,7 +381,7 @@ __device__ void phase_init_argmin(const Params<V>& P) {
     for (long long s = gw; s < P.nstrips; s += nw) {
         const int j = (int)s * 32 * E + lane * E;
         ArgPart a = arg_none();
-        if (j < P.ld) arg_consider_sector(a, ld_sector_cg(P.T + j), j, P.W - 1, P.eps_d);
+        if (j < P.ld) arg_consider_sector(a, ld_sector_cg(P.T + j), j, P.W - 1, P.eps_d, P.cond ? P.var : nullptr);
         a = warp_arg(a);
         if (lane == 0) store_arg(P.cpart + s, a);
     }
@@ -418,9 +439,15 @@ __device__ RatPart phase_leaving(const Params<V>& P, BlockScratch& s) {
 // first element and the first sector of each thread are loaded together, so
 // both parts wait on one round trip.
 template <typename V>
-__device__ void phase_stage_row(const Params<V>& P, int p, V piv) {
+__device__ void phase_stage_row(const Params<V>& P, int p, int q, V piv) {
     constexpr int E = Lanes<V>::E;
     const V* row = P.T + (size_t)p * (size_t)P.ld;
+    if (P.cond) {   // condensed: every column is updated; slot q takes the leaving variable's column
+        const long long nth = (long long)gridDim.x * blockDim.x;
+        for (long long e = (long long)threadIdx.x * gridDim.x + blockIdx.x; e < P.ld; e += nth)
+            __stcg(P.R + e, div_rn(e == q ? V(1) : __ldcg(row + e), piv));
+        return;
+    }
     const int lane = threadIdx.x & 31;
     const long long nsec = P.ld / E;
     const long long nth = (long long)gridDim.x * blockDim.x;
@@ -455,13 +482,14 @@ __device__ void phase_stage_row(const Params<V>& P, int p, V piv) {
 // strip: T[0][j] = fma(-F[0], R[j], T[0][j]) with the strip's argmin partial of
 // the new objective row (the next Step 1's input), and T[p][j] = R[j].
 template <typename V>
-__device__ void phase_update_edge_rows(const Params<V>& P, int p) {
+__device__ void phase_update_edge_rows(const Params<V>& P, int p, int q) {
     constexpr int E = Lanes<V>::E;
     const int lane = threadIdx.x & 31;
     const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
     const V f0 = __ldcg(P.F);
     const int jend = P.W - 1;
+    const int zq = P.cond ? q : -1;   // condensed: slot q starts from the unit column e_p
     for (long long s = gw; s < P.nstrips; s += nw) {
         const int j = (int)s * 32 * E + lane * E;
         ArgPart a = arg_none();
@@ -469,10 +497,10 @@ __device__ void phase_update_edge_rows(const Params<V>& P, int p) {
             const Sector<V> r = ld_sector_cg(P.R + j);
             Sector<V> o = ld_sector_stream(P.T + j);
 #pragma unroll
-            for (int e = 0; e < E; ++e) o.v[e] = fma_rn(-f0, r.v[e], o.v[e]);
+            for (int e = 0; e < E; ++e) o.v[e] = fma_rn(-f0, r.v[e], j + e == zq ? V(0) : o.v[e]);
             st_sector(P.T + j, o);
             st_sector(P.T + (size_t)p * (size_t)P.ld + j, r);
-            arg_consider_sector(a, o, j, jend, P.eps_d);
+            arg_consider_sector(a, o, j, jend, P.eps_d, P.cond ? P.var : nullptr);
         }
         a = warp_arg(a);
         if (lane == 0) store_arg(P.cpart + s, a);
@@ -482,13 +510,15 @@ __device__ void phase_update_edge_rows(const Params<V>& P, int p) {
 // One work slot: rows i0 .. i0+nrows-1 (row p excluded) of the column group
 // listed at entry c*32 + lane.
 template <typename V>
-__device__ __forceinline__ void update_slot(const Params<V>& P, int p, unsigned nact, long long c, int i0,
+__device__ __forceinline__ void update_slot(const Params<V>& P, int p, int zq, unsigned nact, long long c, int i0,
                                             int nrows, const V* f) {
     constexpr int E = Lanes<V>::E;
     const long long e = c * 32 + (threadIdx.x & 31);
     if (e >= (long long)nact) return;
-    const size_t col = (size_t)E * (size_t)__ldcg(P.act + e);
+    const size_t col = (size_t)E * (size_t)(P.cond ? (int)e : __ldcg(P.act + e));
     const Sector<V> r = ld_sector_cg(P.R + col);
+    // condensed: the entry of slot q starts from the leaving variable's unit column (0 off row p)
+    const int eq = zq - (int)col;
     Sector<V> v[kRowsInFlight];
 #pragma unroll
     for (int k = 0; k < kRowsInFlight; ++k) {
@@ -500,7 +530,7 @@ __device__ __forceinline__ void update_slot(const Params<V>& P, int p, unsigned 
         const int i = i0 + k;
         if (k < nrows && i != p) {
 #pragma unroll
-            for (int e2 = 0; e2 < E; ++e2) v[k].v[e2] = fma_rn(-f[k], r.v[e2], v[k].v[e2]);
+            for (int e2 = 0; e2 < E; ++e2) v[k].v[e2] = fma_rn(-f[k], r.v[e2], e2 == eq ? V(0) : v[k].v[e2]);
             st_sector(P.T + (size_t)i * (size_t)P.ld + col, v[k]);
         }
     }
@@ -513,7 +543,7 @@ __device__ __forceinline__ void update_slot(const Params<V>& P, int p, unsigned 
 // registers while the row group is unchanged.  One listed column group per
 // lane.  Groups not listed have R == 0: their update is the identity.
 template <typename V>
-__device__ void phase_update_bulk(const Params<V>& P, int p, unsigned nact) {
+__device__ void phase_update_bulk(const Params<V>& P, int p, int zq, unsigned nact) {
     const int lane = threadIdx.x & 31;
     const long long nchunks = ((long long)nact + 31) / 32;
     const long long ngroups = ((long long)P.m + kRowsInFlight - 1) / kRowsInFlight;
@@ -542,17 +572,18 @@ __device__ void phase_update_bulk(const Params<V>& P, int p, unsigned nact) {
 #pragma unroll
                 for (int k = 0; k < kRowsInFlight; ++k) f[k] = k < nrows ? __ldcg(P.F + i0 + k) : V(0);
             }
-            update_slot(P, p, nact, c, i0, nrows, f);
+            update_slot(P, p, zq, nact, c, i0, nrows, f);
         }
     }
 }
 
 template <typename V>
-__device__ void phase_update(const Params<V>& P, int p) {
-    const unsigned nact = *(volatile const unsigned*)&P.st->nact;
+__device__ void phase_update(const Params<V>& P, int p, int q) {
+    constexpr int E = Lanes<V>::E;
+    const unsigned nact = P.cond ? (unsigned)(P.ld / E) : *(volatile const unsigned*)&P.st->nact;
     if (blockIdx.x == 0 && threadIdx.x == 0) P.st->active_sectors += nact;
-    phase_update_edge_rows(P, p);
-    phase_update_bulk(P, p, nact);
+    phase_update_edge_rows(P, p, q);
+    phase_update_bulk(P, p, P.cond ? q : -1, nact);
 }
 
 }  // namespace tsx

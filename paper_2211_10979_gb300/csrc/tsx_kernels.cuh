@@ -58,10 +58,12 @@ __global__ void k_validate(int m, int n, const double* __restrict__ A, const dou
 // row i = [A_i, e_i | b_i]; padding columns [W, ld) are zero.  One thread per
 // 32-byte sector; the float tableau takes the inputs rounded to nearest.
 // Also seeds the slack basis.
+// W is the stored width: n + m + 1 (full) or n + 1 (condensed, var != null:
+// the slack columns are basic unit vectors and are not stored; var[j] = j).
 template <typename V>
 __global__ void k_build(int m, int n, int W, int ld, const double* __restrict__ A,
                         const double* __restrict__ b, const double* __restrict__ c,
-                        V* __restrict__ T, int* __restrict__ basis) {
+                        V* __restrict__ T, int* __restrict__ basis, int* __restrict__ var) {
     constexpr int E = Lanes<V>::E;
     const size_t per_row = (size_t)ld / E;
     const size_t total = (size_t)(m + 1) * per_row;
@@ -79,10 +81,10 @@ __global__ void k_build(int m, int n, int W, int ld, const double* __restrict__ 
             } else {
                 if (j < n)
                     v = A[(size_t)(i - 1) * (size_t)n + j];
-                else if (j == n + i - 1)
-                    v = 1.0;
                 else if (j == W - 1)
                     v = b[i - 1];
+                else if (!var && j == n + i - 1)
+                    v = 1.0;
             }
             out.v[e] = (V)v;
         }
@@ -91,14 +93,22 @@ __global__ void k_build(int m, int n, int W, int ld, const double* __restrict__ 
     for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < (size_t)m;
          i += (size_t)gridDim.x * blockDim.x)
         basis[i] = n + (int)i;
+    if (var)
+        for (size_t j = (size_t)blockIdx.x * blockDim.x + threadIdx.x; j < (size_t)n;
+             j += (size_t)gridDim.x * blockDim.x)
+            var[j] = (int)j;
 }
 
-// Pivot bookkeeping shared by both paths (one thread): basis update, pivot log.
+// Pivot bookkeeping shared by both paths (one thread): basis update, pivot
+// log (entering variable qv, leaving row p); condensed: the leaving variable
+// takes column slot q.
 template <typename V>
-__device__ __forceinline__ void record_pivot(const Params<V>& P, long long it, int q, int p) {
-    P.basis[p - 1] = q;
+__device__ __forceinline__ void record_pivot(const Params<V>& P, long long it, int q, int qv, int p) {
+    const int leaving = P.basis[p - 1];
+    P.basis[p - 1] = qv;
+    if (P.cond) P.var[q] = leaving;
     if (it < P.log_cap) {
-        P.qlog[it] = q;
+        P.qlog[it] = qv;
         P.plog[it] = p;
     }
 }
@@ -165,8 +175,9 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_pivot_persistent(Params<V> P) 
     clk.start();
     for (;;) {
         const ArgPart e = phase_entering(P, s);           // Step 1
-        const int q = bland ? e.jfirst : e.j;
-        if (q == INT_MAX) { finish(P, kOptimal, it, bland, degen, clk.acc); return; }
+        const int q = bland ? e.fslot : e.slot;
+        const int qv = bland ? e.fkey : e.key;
+        if (qv == INT_MAX) { finish(P, kOptimal, it, bland, degen, clk.acc); return; }
         if (it >= P.max_iters) { finish(P, kIterLimit, it, bland, degen, clk.acc); return; }
         phase_ratio(P, q, bland, s);                      // Step 2 (block partials)
         clk.lap(0);
@@ -176,12 +187,12 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_pivot_persistent(Params<V> P) 
         if (l.i == INT_MAX) { finish(P, kUnbounded, it, bland, degen, clk.acc); return; }
         const V piv = (V)l.a;   // the pivot element, carried by the partial
         if (!isfinite((double)piv) || !isfinite(l.r)) { finish(P, kNumeric, it, bland, degen, clk.acc); return; }
-        phase_stage_row(P, l.i, piv);                     // Step 3 (pivot row)
-        if (blockIdx.x == 0 && threadIdx.x == 0) record_pivot(P, it, q, l.i);
+        phase_stage_row(P, l.i, q, piv);                  // Step 3 (pivot row)
+        if (blockIdx.x == 0 && threadIdx.x == 0) record_pivot(P, it, q, qv, l.i);
         clk.lap(1);
         if (!grid_barrier(P.st, P.timeout_ns, s)) return;
         clk.lap(4);
-        phase_update(P, l.i);                             // Step 3 (rank-1 update)
+        phase_update(P, l.i, q);                          // Step 3 (rank-1 update)
         ++it;
         degeneracy_step(P, l.r, bland, degen);
         clk.lap(2);
@@ -204,14 +215,18 @@ __global__ void __launch_bounds__(NT) k_ml_select(Params<V> P) {
     const int bland = P.st->bland;
     const long long it = P.st->iters;
     const ArgPart e = phase_entering(P, s);
-    const int q = bland ? e.jfirst : e.j;
-    if (q == INT_MAX || it >= P.max_iters) {
+    const int q = bland ? e.fslot : e.slot;
+    const int qv = bland ? e.fkey : e.key;
+    if (qv == INT_MAX || it >= P.max_iters) {
         if (blockIdx.x == 0 && threadIdx.x == 0)
-            atomicCAS(&P.st->status, kRunning, q == INT_MAX ? kOptimal : kIterLimit);
+            atomicCAS(&P.st->status, kRunning, qv == INT_MAX ? kOptimal : kIterLimit);
         return;
     }
     phase_ratio(P, q, bland, s);
-    if (blockIdx.x == 0 && threadIdx.x == 0) P.st->q = q;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        P.st->q = q;
+        P.st->qvar = qv;
+    }
 }
 
 template <int NT, typename V>
@@ -228,9 +243,9 @@ __global__ void __launch_bounds__(NT) k_ml_stage(Params<V> P) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&P.st->status, kRunning, kNumeric);
         return;
     }
-    phase_stage_row(P, l.i, piv);
+    phase_stage_row(P, l.i, P.st->q, piv);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        record_pivot(P, P.st->iters, P.st->q, l.i);
+        record_pivot(P, P.st->iters, P.st->q, P.st->qvar, l.i);
         P.st->p = l.i;
         P.st->theta = l.r;
     }
@@ -240,7 +255,7 @@ template <int NT, typename V>
 __global__ void __launch_bounds__(NT, 512 / NT) k_ml_update(Params<V> P) {
     if (P.st->status != kRunning) return;
     const int p = P.st->p;
-    phase_update(P, p);
+    phase_update(P, p, P.st->q);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         int bland = P.st->bland, degen = P.st->degen_run;
         degeneracy_step(P, P.st->theta, bland, degen);
@@ -253,16 +268,63 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_ml_update(Params<V> P) {
 // Solution read-out (Table I layout), widened to double: y_i = T[0][n+i],
 // obj = T[0][W-1], x zeroed, then x[basis[i]] = T[i+1][W-1] for structural
 // basics.
+// Condensed tableau: y_i = 0 for basic slacks; the nonbasic slacks' entries
+// are scattered by k_extract_y_cond afterwards.
 template <typename V>
-__global__ void k_extract_dense(int m, int n, int W, int ld, const V* __restrict__ T, double* __restrict__ sol) {
+__global__ void k_extract_dense(int m, int n, int W, int ld, const V* __restrict__ T, int cond,
+                                double* __restrict__ sol) {
     for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n + m + 1; k += gridDim.x * blockDim.x) {
         if (k < n)
             sol[k] = 0.0;
         else if (k < n + m)
-            sol[k] = (double)T[n + (k - n)];
+            sol[k] = cond ? 0.0 : (double)T[n + (k - n)];
         else
             sol[k] = (double)T[W - 1];
     }
+}
+
+// Condensed tableau: y_i = T[0][j] for the slot j holding slack n + i.
+template <typename V>
+__global__ void k_extract_y_cond(int m, int n, const V* __restrict__ T, const int* __restrict__ var,
+                                 double* __restrict__ sol) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        const int v = var[j];
+        if (v >= n) sol[v] = (double)T[j];   // sol + n + (v - n)
+    }
+}
+
+// Full (m+1) x (n+m+1) tableau widened to double from the condensed one:
+// column var[j] <- slot j, column n+m <- the RHS, unit columns for the basic
+// variables, zero elsewhere.  Two passes: zero-and-scatter of the stored
+// columns (every output entry written once by its own thread), then the units.
+template <typename V>
+__global__ void k_expand_cond(int m, int n, int ld, const V* __restrict__ T, const int* __restrict__ var,
+                              const int* __restrict__ slot_of, double* __restrict__ out) {
+    const size_t W = (size_t)n + m + 1;
+    const size_t total = (size_t)(m + 1) * W;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const size_t i = t / W, col = t - i * W;
+        double v = 0.0;
+        if (col == W - 1)
+            v = (double)T[i * (size_t)ld + n];
+        else if (slot_of[col] >= 0)
+            v = (double)T[i * (size_t)ld + slot_of[col]];
+        out[t] = v;
+    }
+}
+
+// slot_of[v] = the slot holding variable v, -1 if v is basic; then the basic
+// variables' unit entries.
+__global__ void k_slot_of(int m, int n, const int* __restrict__ var, int* __restrict__ slot_of) {
+    for (int v = blockIdx.x * blockDim.x + threadIdx.x; v < n + m; v += gridDim.x * blockDim.x) slot_of[v] = -1;
+}
+__global__ void k_slot_of_set(int n, const int* __restrict__ var, int* __restrict__ slot_of) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) slot_of[var[j]] = j;
+}
+__global__ void k_expand_units(int m, int n, const int* __restrict__ basis, double* __restrict__ out) {
+    const size_t W = (size_t)n + m + 1;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+        out[(size_t)(i + 1) * W + basis[i]] = 1.0;
 }
 
 template <typename V>

@@ -43,8 +43,11 @@ def _certificate(A, b, c, x, y, obj, tol=1e-9):
     assert abs(b @ y - obj) <= tol * scale
 
 
-@pytest.mark.parametrize("m,n", [(8192, 8192), (4096, 16384)])
-def test_full_size_first_pivots_and_certificates(tsx, m, n):
+@pytest.mark.parametrize("m,n,layout", [(8192, 8192, 0), (4096, 16384, 0), (8192, 8192, 1)])
+def test_full_size_first_pivots_and_certificates(tsx, m, n, layout):
+    # layout 0 (the bench's): condensed device tableau, expanded to Table I on
+    # read-out, so the unit-column check below holds by construction there and
+    # is the real check for layout 1
     import torch
     A, b, c = lpgen.dense_lp(m, n, 1)
     ref = oracle.solve(A, b, c, oracle.Options(max_iters=K))
@@ -53,19 +56,20 @@ def test_full_size_first_pivots_and_certificates(tsx, m, n):
     s = torch.cuda.current_stream().cuda_stream
     with tsx.Problem(dA, db, dc, device=True, stream=s) as pr:
         # the first K pivots, compared entry by entry
-        assert pr.solve(tsx.options(stream=s, max_iters=K, log_capacity=K)) == tsx.LP_ITER_LIMIT
+        assert pr.solve(tsx.options(stream=s, max_iters=K, log_capacity=K, layout=layout)) == tsx.LP_ITER_LIMIT
         q, p = pr.pivot_log(K)
         assert q.tolist() == ref.qlog.tolist() and p.tolist() == ref.plog.tolist()
         T = pr.tableau()
         np.testing.assert_array_equal(T, ref.T)
         del T
         # the whole solve, checked by properties that hold at any size
-        assert pr.solve(tsx.options(stream=s, log_capacity=1 << 16)) == tsx.LP_OPTIMAL
+        assert pr.solve(tsx.options(stream=s, log_capacity=1 << 16, layout=layout)) == tsx.LP_OPTIMAL
         sol = pr.solution()
         q, p = pr.pivot_log(K)
         assert q.tolist() == ref.qlog.tolist() and p.tolist() == ref.plog.tolist()
         stats = pr.stats()
         assert stats["path"] == tsx.LP_PATH_PERSISTENT and stats["iters"] == sol.iters
+        assert stats["layout"] == layout
         T = pr.tableau()
     rows = np.arange(1, m + 1)
     basic = sol.basis.astype(np.int64)

@@ -60,10 +60,12 @@ SHAPES = [(1, 1), (1, 7), (7, 1), (3, 4), (16, 16), (37, 53), (64, 64), (100, 30
 
 @pytest.mark.parametrize("m,n", SHAPES)
 @pytest.mark.parametrize("path", [1, 2])
-def test_full_solve_bit_exact(tsx, m, n, path):
+@pytest.mark.parametrize("layout", [0, 1])
+def test_full_solve_bit_exact(tsx, m, n, path, layout):
+    # layout 0: condensed device tableau (nonbasic columns + RHS), 1: Table I itself
     A, b, c = lpgen.dense_lp(m, n, 1 + m + n)
     ref = _oracle_run(A, b, c)
-    _assert_same(_gpu_run(tsx, A, b, c, path=path), ref)
+    _assert_same(_gpu_run(tsx, A, b, c, path=path, layout=layout), ref)
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3, 4, 5, 6, 7, 8])
@@ -74,19 +76,21 @@ def test_config_256_seeds(tsx, seed):
     _assert_same(_gpu_run(tsx, A, b, c), ref)
 
 
-@pytest.mark.parametrize("skip", [0, 1])
+@pytest.mark.parametrize("layout,skip", [(0, 1), (1, 0), (1, 1)])
 @pytest.mark.parametrize("threads,blocks", [(128, 1), (256, 2), (512, 3), (256, 7), (256, 0)])
-def test_launch_shapes_agree(tsx, skip, threads, blocks):
+def test_launch_shapes_agree(tsx, layout, skip, threads, blocks):
     A, b, c = lpgen.dense_lp(300, 200, 11)
     ref = _oracle_run(A, b, c)
-    _assert_same(_gpu_run(tsx, A, b, c, skip_zero_columns=skip, threads=threads, blocks=blocks), ref)
+    _assert_same(_gpu_run(tsx, A, b, c, layout=layout, skip_zero_columns=skip, threads=threads, blocks=blocks),
+                 ref)
 
 
 @pytest.mark.parametrize("k", [0, 1, 2, 5, 17])
-def test_tableau_after_k_pivots(tsx, k):
+@pytest.mark.parametrize("layout", [0, 1])
+def test_tableau_after_k_pivots(tsx, k, layout):
     A, b, c = lpgen.dense_lp(200, 150, 21)
     ref = _oracle_run(A, b, c, max_iters=k)
-    st, sol, T, q, p, _ = _gpu_run(tsx, A, b, c, max_iters=k)
+    st, sol, T, q, p, _ = _gpu_run(tsx, A, b, c, max_iters=k, layout=layout)
     assert st == ref.status == oracle.ITER_LIMIT
     assert sol.iters == k
     np.testing.assert_array_equal(T, ref.T)
@@ -100,8 +104,8 @@ def test_golden_hand_traces(tsx, golden_dir):
         A = np.array(g["A"], dtype=np.float64)
         b = np.array(g["b"], dtype=np.float64)
         c = np.array(g["c"], dtype=np.float64)
-        for path in (1, 2):
-            st, sol, T, q, p, _ = _gpu_run(tsx, A, b, c, path=path)
+        for path, layout in ((1, 0), (2, 0), (1, 1), (2, 1)):
+            st, sol, T, q, p, _ = _gpu_run(tsx, A, b, c, path=path, layout=layout)
             assert tsx.STATUS_NAMES[st] == g["status"]
             assert q.tolist() == [s["q"] for s in g["steps"]]
             assert p.tolist() == [s["p"] for s in g["steps"]]
@@ -116,7 +120,8 @@ def test_cycling_lp_bland_fallback(tsx):
     for kw in ({"k_cyc": 3}, {"k_cyc": 50}, {"rule": 1}, {"k_cyc": 0, "max_iters": 200}):
         ref = _oracle_run(A, b, c, **kw)
         for path in (1, 2):
-            _assert_same(_gpu_run(tsx, A, b, c, path=path, **kw), ref)
+            for layout in (0, 1):
+                _assert_same(_gpu_run(tsx, A, b, c, path=path, layout=layout, **kw), ref)
 
 
 def test_unbounded_and_zero_objective(tsx):
@@ -186,12 +191,22 @@ def test_barrier_timeout_reports_and_context_survives(tsx):
         np.testing.assert_array_equal(pr.tableau(), _oracle_run(A, b, c).T)
 
 
-def test_stats_account_for_the_update(tsx):
+@pytest.mark.parametrize("layout", [0, 1])
+def test_stats_account_for_the_update(tsx, layout):
     A, b, c = lpgen.dense_lp(256, 256, 2)
-    st, sol, T, q, p, stats = _gpu_run(tsx, A, b, c)
+    st, sol, T, q, p, stats = _gpu_run(tsx, A, b, c, layout=layout)
     m, n = 256, 256
     W = n + m + 1
-    assert stats["iters"] == sol.iters > 0
-    assert stats["dense_update_bytes"] == 2.0 * (m + 1) * W * 8 * sol.iters
-    assert 0 < stats["update_bytes"] <= 2.0 * (m + 1) * stats["ld"] * 8 * sol.iters
+    ld, it = stats["ld"], sol.iters
+    assert stats["layout"] == layout
+    assert stats["iters"] == it > 0
+    assert stats["dense_update_bytes"] == 2.0 * (m + 1) * W * 8 * it
+    side = (64.0 * (m + 1) + 24.0 * ld) * it
+    if layout == 0:
+        # condensed: every 32-byte group of the (n + 1)-wide rows is updated
+        assert ld == -(-(n + 1) // 16) * 16
+        assert stats["update_bytes"] == (64.0 * (m - 1) + 96.0) * (ld // 4) * it + side
+    else:
+        assert ld == -(-W // 16) * 16
+        assert 0 < stats["update_bytes"] <= 2.0 * (m + 1) * ld * 8 * it + side
     assert stats["pivot_ms"] > 0 and stats["kernel_launches"] >= 3
