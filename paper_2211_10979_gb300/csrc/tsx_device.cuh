@@ -38,6 +38,9 @@ constexpr int kRunning = 100;      // status while the iteration is in progress
 #ifndef TSX_GRAB
 #define TSX_GRAB 2
 #endif
+#ifndef TSX_ALTERNATE
+#define TSX_ALTERNATE 1   // alternate the update's sweep direction per pivot
+#endif
 constexpr int kRowsInFlight = TSX_ROWS_IN_FLIGHT;   // rows loaded before the first store
 constexpr int kMaxWarps = 32;      // warps per block upper bound (1024 threads)
 
@@ -543,7 +546,7 @@ __device__ __forceinline__ void update_slot(const Params<V>& P, int p, int zq, u
 // registers while the row group is unchanged.  One listed column group per
 // lane.  Groups not listed have R == 0: their update is the identity.
 template <typename V>
-__device__ void phase_update_bulk(const Params<V>& P, int p, int zq, unsigned nact) {
+__device__ void phase_update_bulk(const Params<V>& P, int p, int zq, unsigned nact, int rev) {
     const int lane = threadIdx.x & 31;
     const long long nchunks = ((long long)nact + 31) / 32;
     const long long ngroups = ((long long)P.m + kRowsInFlight - 1) / kRowsInFlight;
@@ -563,8 +566,11 @@ __device__ void phase_update_bulk(const Params<V>& P, int p, int zq, unsigned na
         if (lane == 0) next = atomicAdd(&P.st->next_slot, (unsigned)TSX_GRAB);
         next = __shfl_sync(0xffffffffu, next, 0);
         for (long long u = u0; u < u1; ++u) {
-            const long long g = u / nchunks;
-            const long long c = u - g * nchunks;
+            // odd pivots sweep backwards: they start on the rows the previous
+            // sweep wrote last, which are still in L2
+            const long long ur = rev ? total - 1 - u : u;
+            const long long g = ur / nchunks;
+            const long long c = ur - g * nchunks;
             if (g != gcur) {
                 gcur = g;
                 i0 = 1 + (int)g * kRowsInFlight;
@@ -578,12 +584,12 @@ __device__ void phase_update_bulk(const Params<V>& P, int p, int zq, unsigned na
 }
 
 template <typename V>
-__device__ void phase_update(const Params<V>& P, int p, int q) {
+__device__ void phase_update(const Params<V>& P, int p, int q, long long it) {
     constexpr int E = Lanes<V>::E;
     const unsigned nact = P.cond ? (unsigned)(P.ld / E) : *(volatile const unsigned*)&P.st->nact;
     if (blockIdx.x == 0 && threadIdx.x == 0) P.st->active_sectors += nact;
     phase_update_edge_rows(P, p, q);
-    phase_update_bulk(P, p, P.cond ? q : -1, nact);
+    phase_update_bulk(P, p, P.cond ? q : -1, nact, TSX_ALTERNATE ? (int)(it & 1) : 0);
 }
 
 }  // namespace tsx

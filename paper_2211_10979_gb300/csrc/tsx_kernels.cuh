@@ -192,7 +192,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_pivot_persistent(Params<V> P) 
         clk.lap(1);
         if (!grid_barrier(P.st, P.timeout_ns, s)) return;
         clk.lap(4);
-        phase_update(P, l.i, q);                          // Step 3 (rank-1 update)
+        phase_update(P, l.i, q, it);                      // Step 3 (rank-1 update)
         ++it;
         degeneracy_step(P, l.r, bland, degen);
         clk.lap(2);
@@ -255,7 +255,7 @@ template <int NT, typename V>
 __global__ void __launch_bounds__(NT, 512 / NT) k_ml_update(Params<V> P) {
     if (P.st->status != kRunning) return;
     const int p = P.st->p;
-    phase_update(P, p, P.st->q);
+    phase_update(P, p, P.st->q, P.st->iters);
     if (blockIdx.x == 0 && threadIdx.x == 0) {
         int bland = P.st->bland, degen = P.st->degen_run;
         degeneracy_step(P, P.st->theta, bland, degen);
