@@ -61,6 +61,9 @@ def parse_args(argv=None):
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="serve: length of the stream")
     ap.add_argument("--serve-workers", type=int, default=8)
     ap.add_argument("--serve-blocks", type=int, default=0, help="serve: grid cap per single-lane solve")
+    ap.add_argument("--serve-team", type=int, default=0,
+                    help="serve: blocks per team of the lp_solve_many waves (0 = library default, "
+                         "< 0 = no waves: one LP per worker)")
     ap.add_argument("--serve-path", type=int, default=2,
                     help="serve: single-lane solve path (1 persistent cooperative, 2 one launch per phase)")
     ap.add_argument("--batch-count", type=int, default=4096)
@@ -643,10 +646,10 @@ def run_serve(args, rank, world, local):
     clocks.start()
     served, st, t0 = play_stream(tsx, torch, dev, shapes, arrivals, seeds,
                                  {"workers": args.serve_workers, "blocks_per_lp": args.serve_blocks,
-                                  "path": args.serve_path})
+                                  "path": args.serve_path, "team_blocks": args.serve_team})
     clk = clocks.stop()
     plain, st_plain, t0p = play_stream(tsx, torch, dev, shapes, arrivals, seeds,
-                                       {"workers": 1, "batch_small": 0, "path": 0})
+                                       {"workers": 1, "batch_small": 0, "path": 0, "team_blocks": -1})
 
     def summary(res, t_start):
         lat = np.array([r[1] for r in res])
@@ -667,7 +670,7 @@ def run_serve(args, rank, world, local):
         "steps": 1, "warmup": 1, "ms_per_step": 1e3 * count / s_srv["solves_per_s"],
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64 micro-batches (LPs whose condensed tableau fits one SM's shared memory); "
-                 "f32 tableau + f64 recovery (the others)",
+                 "f32 tableau + f64 recovery in lp_solve_many waves (the others)",
         "data": "synthetic",
         "config": {"workload": f"Poisson stream, {args.rate:.0f} LPs/s for {args.serve_seconds:.1f} s "
                                f"({count} LPs), m and n log-uniform in [32, 4096], inputs generated on "
@@ -675,6 +678,7 @@ def run_serve(args, rank, world, local):
                    "workers": args.serve_workers, "blocks_per_lp": args.serve_blocks or "default",
                    "single_lane_path": args.serve_path,
                    "batches": st["batches"], "batched_lps": st["batched_lps"],
+                   "waves": st["waves"], "wave_lps": st["wave_lps"], "team_blocks": args.serve_team or "default",
                    "peak_admitted_bytes": st["peak_bytes"]},
         "latency": {"p50_ms": s_srv["p50_ms"], "p99_ms": s_srv["p99_ms"], "mean_ms": s_srv["mean_ms"],
                     "max_ms": s_srv["max_ms"], "from": "scheduled arrival to result on the host"},

@@ -53,7 +53,8 @@ typedef enum {
 } lp_status;
 
 enum { LP_RULE_DANTZIG = 0, LP_RULE_BLAND = 1 };
-enum { LP_PATH_AUTO = 0, LP_PATH_PERSISTENT = 1, LP_PATH_MULTILAUNCH = 2 };
+enum { LP_PATH_AUTO = 0, LP_PATH_PERSISTENT = 1, LP_PATH_MULTILAUNCH = 2,
+       LP_PATH_TEAM = 3 /* lp_stats.path of an lp_solve_many solve */ };
 enum { LP_PREC_FP64 = 0, LP_PREC_FP32 = 1 };
 
 /* Solve options.  Initialise with lp_options_init() and change fields. */
@@ -168,6 +169,29 @@ lp_t lp_create_device(int m, int n, const double *dA, const double *db,
  * again: every call starts over from the slack basis.  opt == NULL uses the
  * defaults. */
 lp_status lp_solve(lp_t h, const lp_options *opt);
+
+/* Solve `count` LPs at once, each from its slack basis (the method of
+ * lp_solve: Section III, Initialization Step and Steps 1-3).  One cooperative
+ * launch divides the GPU into teams of opt->blocks thread blocks (default 16);
+ * each team takes the next LP from the list, largest first, and iterates on
+ * its condensed tableau: block b of the team owns a contiguous range of rows,
+ * runs the ratio test on them and updates them, with the scaled pivot row and
+ * its rows' multipliers in shared memory; two team barriers per pivot.  Meant
+ * for many medium LPs, whose pivots are too small to fill the GPU one at a
+ * time.  Every pivot and value equals lp_solve's with the same options.
+ *   handles  count distinct handles on the current device (lp_create*)
+ *   opt      options as lp_solve (NULL = defaults); layout must be
+ *            LP_LAYOUT_CONDENSED, log_capacity 0, threads 0 or 256; blocks =
+ *            blocks per team; precision LP_PREC_FP32 adds the FP64 recovery
+ *            of each LP after the launch
+ *   status   HOST output, count entries: each LP's status as lp_solve returns it
+ * An LP whose pivot row and row multipliers do not fit one block's shared
+ * memory is solved by lp_solve after the launch.  Afterwards each handle
+ * answers lp_get_solution, lp_get_tableau and lp_get_stats as after lp_solve
+ * (stats.path = LP_PATH_TEAM, stats.pivot_ms = the whole launch, no pivot
+ * log).  Returns LP_OPTIMAL when the call ran (per-LP outcomes in status), or
+ * an error (< 0) for invalid arguments or a CUDA failure. */
+lp_status lp_solve_many(lp_t *handles, int count, const lp_options *opt, lp_status *status);
 
 /* Read the solution out of the final tableau (Table I layout): x_j is the
  * right-hand side of the row where x_j is basic, else 0 (n entries); y_i is the
@@ -298,10 +322,11 @@ void lp_batch_destroy(lp_batch_t h);
  * them in arrival order while the device-memory budget allows.  LPs up to a
  * size (shared-memory fit, or batch_max_bytes) are taken together -- every such
  * request waiting at that moment, up to batch_max -- and solved as one
- * micro-batch (FP64, results equal lp_solve's); the others are solved one per
- * worker by lp_create / lp_solve with the given precision (default FP32
- * tableau + FP64 recovery) on a share of the GPU's blocks, so that several run
- * side by side.  Requests arriving while others are on the GPU are
+ * micro-batch (FP64, results equal lp_solve's); the others are solved in
+ * waves by lp_solve_many with the given precision (default FP32 tableau + FP64
+ * recovery): every such request waiting when a wave starts joins it, and the
+ * requests arriving meanwhile form the next wave (or, with team_blocks < 0,
+ * one per worker by lp_create / lp_solve on a share of the GPU's blocks).  Requests arriving while others are on the GPU are
  * admitted as workers and memory free up, and their work overlaps on the
  * device.  The paper has no serving layer; every solve inside is the method of
  * lp_solve.
@@ -331,6 +356,13 @@ typedef struct {
                                      overlap with other workers' solves (the
                                      cooperative launches of the persistent
                                      path largely run one at a time)            */
+    int team_blocks;              /* >= 0 (default 0: lp_solve_many's default
+                                     team of 16 blocks): the requests too
+                                     large for the micro-batches are solved in
+                                     waves by lp_solve_many with teams of this
+                                     many blocks -- every such request waiting
+                                     when a wave starts joins it, one wave at a
+                                     time; < 0: one per worker by lp_solve     */
 } lps_options;
 
 typedef struct {
@@ -340,6 +372,7 @@ typedef struct {
     double queue_p50_ms, queue_p99_ms;                        /* submit -> admit*/
     long long batches, batched_lps;
     long long peak_bytes;         /* largest admitted total                     */
+    long long waves, wave_lps;    /* lp_solve_many waves and the LPs in them   */
 } lps_stats;
 
 void lps_options_init(lps_options *opt);

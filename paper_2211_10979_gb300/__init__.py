@@ -15,11 +15,11 @@ import numpy as np
 from . import abi
 from .abi import (LP_ERR_CUDA, LP_ERR_INVALID, LP_ERR_NOMEM, LP_ERR_NUMERIC, LP_ERR_STATE,
                   LP_ERR_TIMEOUT, LP_ITER_LIMIT, LP_LAYOUT_CONDENSED, LP_LAYOUT_FULL, LP_OPTIMAL,
-                  LP_PATH_AUTO, LP_PATH_MULTILAUNCH,
+                  LP_PATH_AUTO, LP_PATH_MULTILAUNCH, LP_PATH_TEAM,
                   LP_PATH_PERSISTENT, LP_PREC_FP32, LP_PREC_FP64, LP_RULE_BLAND, LP_RULE_DANTZIG, LP_UNBOUNDED, STATUS_NAMES,
                   lp_create, lp_create_device, lp_destroy, lp_get_pivot_log, lp_get_solution,
                   lp_get_stats, lp_get_tableau, lp_last_error, lp_options, lp_options_init,
-                  lp_set_allocator, lp_solve, lp_solve_noalloc, lp_stats, lp_version,
+                  lp_set_allocator, lp_solve, lp_solve_many, lp_solve_noalloc, lp_stats, lp_version,
                   lp_batch_options, lp_batch_options_init, lp_batch_create, lp_batch_create_device,
                   lp_batch_solve, lp_batch_get, lp_batch_get_tableau, lp_batch_get_stats,
                   lp_batch_destroy, LP_PENDING, lps_options, lps_options_init, lps_open, lps_submit,
@@ -141,6 +141,16 @@ class Problem:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def solve_many(problems, opts: lp_options | None = None):
+    """Solves several Problems at once (lp_solve_many: a team of blocks per
+    LP, one launch); returns the per-LP statuses.  Each Problem then answers
+    solution() / tableau() / stats() as after its own solve()."""
+    rc, st = lp_solve_many([p.h for p in problems], opts)
+    if rc != LP_OPTIMAL:
+        raise RuntimeError(f"lp_solve_many failed ({STATUS_NAMES.get(rc, rc)}): {lp_last_error()}")
+    return st
 
 
 def batch_options(**kw) -> lp_batch_options:

@@ -20,13 +20,13 @@ STATUS_NAMES = {0: "OPTIMAL", 1: "UNBOUNDED", 2: "ITER_LIMIT", 3: "NUMERIC", -1:
                 -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE", 100: "PENDING"}
 LP_RULE_DANTZIG, LP_RULE_BLAND = 0, 1
 LP_LAYOUT_CONDENSED, LP_LAYOUT_FULL = 0, 1
-LP_PATH_AUTO, LP_PATH_PERSISTENT, LP_PATH_MULTILAUNCH = 0, 1, 2
+LP_PATH_AUTO, LP_PATH_PERSISTENT, LP_PATH_MULTILAUNCH, LP_PATH_TEAM = 0, 1, 2, 3
 LP_PREC_FP64, LP_PREC_FP32 = 0, 1
 
 # every symbol include/tabsimplex.h declares
 EXPORTS = ("lp_options_init", "lp_create", "lp_create_device", "lp_solve", "lp_get_solution",
            "lp_get_tableau", "lp_get_pivot_log", "lp_get_stats", "lp_destroy", "lp_last_error",
-           "lp_set_allocator", "lp_version", "lp_solve_noalloc", "lp_batch_options_init",
+           "lp_set_allocator", "lp_version", "lp_solve_noalloc", "lp_solve_many", "lp_batch_options_init",
            "lp_batch_create", "lp_batch_create_device", "lp_batch_solve", "lp_batch_get",
            "lp_batch_get_tableau", "lp_batch_get_stats", "lp_batch_destroy", "lps_options_init",
            "lps_open", "lps_submit", "lps_submit_device", "lps_wait", "lps_result", "lps_release",
@@ -134,6 +134,7 @@ class lps_options(ctypes.Structure):
         ("blocks_per_lp", ctypes.c_int),
         ("batch_max_bytes", ctypes.c_longlong),
         ("path", ctypes.c_int),
+        ("team_blocks", ctypes.c_int),
     ]
 
 
@@ -151,6 +152,8 @@ class lps_stats(ctypes.Structure):
         ("batches", ctypes.c_longlong),
         ("batched_lps", ctypes.c_longlong),
         ("peak_bytes", ctypes.c_longlong),
+        ("waves", ctypes.c_longlong),
+        ("wave_lps", ctypes.c_longlong),
     ]
 
     def as_dict(self):
@@ -182,6 +185,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "lp_create": (vp, [ctypes.c_int, ctypes.c_int, vp, vp, vp]),
             "lp_create_device": (vp, [ctypes.c_int, ctypes.c_int, vp, vp, vp, vp]),
             "lp_solve": (ctypes.c_int, [vp, ctypes.POINTER(lp_options)]),
+            "lp_solve_many": (ctypes.c_int, [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(lp_options),
+                                             ctypes.POINTER(ctypes.c_int)]),
             "lp_get_solution": (ctypes.c_int, [vp, vp, vp, vp, vp, llp]),
             "lp_get_tableau": (ctypes.c_int, [vp, vp]),
             "lp_get_pivot_log": (ctypes.c_int, [vp, vp, vp, ctypes.c_longlong, llp]),
@@ -268,6 +273,16 @@ def lp_create_device(m: int, n: int, dA, db, dc, stream=None) -> int:
 
 def lp_solve(h: int, opts: lp_options | None = None) -> int:
     return int(load().lp_solve(h, ctypes.byref(opts) if opts is not None else None))
+
+
+def lp_solve_many(handles, opts: lp_options | None = None):
+    """Solves the LPs of the given handles at once; returns (call status,
+    list of per-LP statuses)."""
+    n = len(handles)
+    arr = (ctypes.c_void_p * max(1, n))(*handles)
+    st = (ctypes.c_int * max(1, n))()
+    rc = load().lp_solve_many(arr, n, ctypes.byref(opts) if opts is not None else None, st)
+    return int(rc), [int(st[k]) for k in range(n)]
 
 
 def lp_get_solution(h: int, x=None, y=None, obj=None, basis=None):

@@ -96,15 +96,18 @@ struct Request {
     bool done = false;
 };
 
-// Device bytes a request holds while it is solved.
+// Device bytes a request holds while it is solved: inputs, the condensed
+// tableau and work vectors, and for FP32 the FP64 recovery's k x 2k and k x k
+// matrices at their largest (k = min(m, n)).
 size_t request_bytes(int m, int n, bool small, int precision) {
     const size_t in = 8ull * ((size_t)m * n + m + n);
     if (small) return 2 * in + 8ull * (size_t)(m + 2) * (n + 3) + 64ull * (m + n) + 4096;
-    const size_t W = (size_t)n + m + 1;
     const size_t elem = precision == LP_PREC_FP32 ? 4 : 8;
-    const size_t ld = (W + 31) / 32 * 32;
+    const size_t ld = ((size_t)n + 1 + 31) / 32 * 32;
     const size_t tab = (size_t)(m + 1) * ld * elem + (size_t)(m + 1 + 2 * ld) * elem;
-    return in + tab + 64ull * (m + n) + (1ull << 20);
+    const size_t k = (size_t)std::min(m, n);
+    const size_t rec = precision == LP_PREC_FP32 ? 24ull * k * k + 128ull * (m + n) : 0;
+    return in + tab + rec + 64ull * (m + n) + (1ull << 20);
 }
 
 }  // namespace
@@ -123,7 +126,9 @@ struct lp_server {
     std::vector<double> lat_ms, queue_ms;
     long long next_id = 0;
     long long used = 0, peak = 0;
-    long long submitted = 0, completed = 0, batches = 0, batched_lps = 0;
+    long long submitted = 0, completed = 0, batches = 0, batched_lps = 0, waves = 0, wave_lps = 0;
+    bool wave_running = false;           // one lp_solve_many wave at a time
+    int team_blocks = 0;                 // blocks per team of a wave, < 0: no waves
     std::string last_error;              // message of the latest failed solve
     bool stopping = false;
     bool started = false;
@@ -142,6 +147,7 @@ void lps_options_init(lps_options* o) {
     o->blocks_per_lp = 0;
     o->batch_max_bytes = 0;
     o->path = LP_PATH_MULTILAUNCH;
+    o->team_blocks = 0;
 }
 
 // Keeps the calling worker's last library error for lps_last_error.
@@ -252,6 +258,47 @@ static void solve_batch(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs
     sv->batched_lps += count;
 }
 
+// Solves the requests too large for the micro-batches together: one
+// lp_solve_many call (a team of blocks per LP) on the calling worker thread.
+static void solve_wave(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs, cudaStream_t s) {
+    std::vector<lp_t> hs;
+    std::vector<Request*> who;
+    for (auto& rp : rs) {
+        Request& r = *rp;
+        lp_t h = r.on_device ? lp_create_device(r.m, r.n, r.dA, r.db, r.dc, (void*)s)
+                             : lp_create(r.m, r.n, r.hA.data(), r.hb.data(), r.hc.data());
+        if (!h) {
+            note_error(sv, "create");
+            r.status = LP_ERR_INVALID;
+            continue;
+        }
+        hs.push_back(h);
+        who.push_back(&r);
+    }
+    lp_options o;
+    lp_options_init(&o);
+    o.precision = sv->opt.precision;
+    o.blocks = sv->team_blocks;
+    o.stream = (void*)s;
+    std::vector<lp_status> st(hs.size(), LP_ERR_STATE);
+    const lp_status rc = hs.empty() ? LP_OPTIMAL : lp_solve_many(hs.data(), (int)hs.size(), &o, st.data());
+    if (rc != LP_OPTIMAL) note_error(sv, "wave");
+    for (size_t k = 0; k < hs.size(); ++k) {
+        Request& r = *who[k];
+        r.status = rc != LP_OPTIMAL ? rc : st[k];
+        if (r.status < 0 && rc == LP_OPTIMAL) note_error(sv, "wave solve");
+        r.x.assign(r.n, 0.0);
+        r.y.assign(r.m, 0.0);
+        long long it = 0;
+        if (r.status >= 0) lp_get_solution(hs[k], r.x.data(), r.y.data(), &r.obj, nullptr, &it);
+        r.iters = it;
+        lp_destroy(hs[k]);
+    }
+    std::lock_guard<std::mutex> lk(sv->mu);
+    ++sv->waves;
+    sv->wave_lps += (long long)rs.size();
+}
+
 static void worker_main(lp_server* sv) {
     cudaSetDevice(sv->device);
     use_default_allocator(true);
@@ -261,21 +308,49 @@ static void worker_main(lp_server* sv) {
         std::vector<std::shared_ptr<Request>> take;
         {
             std::unique_lock<std::mutex> lk(sv->mu);
-            // strict arrival order: the head is admitted first once the budget
-            // allows; small requests queued right behind it join its micro-batch
-            sv->cv_work.wait(lk, [&] {
-                return sv->stopping || (!sv->queue.empty() &&
-                                        sv->used + (long long)sv->queue.front()->bytes <= sv->opt.budget_bytes);
-            });
-            if (sv->queue.empty()) {
-                if (sv->stopping) break;
+            // arrival order: the head is admitted first once the budget allows;
+            // small requests queued behind it join its micro-batch, and with
+            // waves, every large request waiting joins the wave.  While a wave
+            // runs, large requests wait for the next one and the other workers
+            // serve the small ones.
+            const bool waves = sv->team_blocks >= 0;
+            auto pick = [&]() -> std::deque<std::shared_ptr<Request>>::iterator {
+                for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
+                    const bool large = !((*it)->small && sv->opt.batch_small);
+                    if (waves && large && sv->wave_running) continue;
+                    if (sv->used + (long long)(*it)->bytes > sv->opt.budget_bytes) return sv->queue.end();
+                    return it;
+                }
+                return sv->queue.end();
+            };
+            sv->cv_work.wait(lk, [&] { return sv->stopping || pick() != sv->queue.end(); });
+            auto first = pick();
+            if (first == sv->queue.end()) {
+                if (sv->stopping && sv->queue.empty()) break;
+                if (sv->stopping) {
+                    sv->cv_work.wait(lk, [&] { return sv->queue.empty() || pick() != sv->queue.end(); });
+                    continue;
+                }
                 continue;
             }
-            auto head = sv->queue.front();
-            sv->queue.pop_front();
+            auto head = *first;
+            sv->queue.erase(first);
             sv->used += (long long)head->bytes;
             take.push_back(head);
-            if (head->small && sv->opt.batch_small) {
+            const bool head_large = !(head->small && sv->opt.batch_small);
+            if (waves && head_large) {
+                sv->wave_running = true;
+                for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)take.size() < sv->opt.batch_max;) {
+                    const bool large = !((*it)->small && sv->opt.batch_small);
+                    if (large && sv->used + (long long)(*it)->bytes <= sv->opt.budget_bytes) {
+                        sv->used += (long long)(*it)->bytes;
+                        take.push_back(*it);
+                        it = sv->queue.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+            } else if (!head_large) {
                 for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)take.size() < sv->opt.batch_max;) {
                     if ((*it)->small && sv->used + (long long)(*it)->bytes <= sv->opt.budget_bytes) {
                         sv->used += (long long)(*it)->bytes;
@@ -290,12 +365,16 @@ static void worker_main(lp_server* sv) {
             const auto now = Clock::now();
             for (auto& r : take) r->t_admit = now;
         }
-        if (take.size() == 1 && !(take[0]->small && sv->opt.batch_small))
+        const bool large = !(take[0]->small && sv->opt.batch_small);
+        if (large && sv->team_blocks >= 0)
+            solve_wave(sv, take, s);
+        else if (large)
             solve_single(sv, *take[0], s);
         else
             solve_batch(sv, take, s);
         {
             std::lock_guard<std::mutex> lk(sv->mu);
+            if (large && sv->team_blocks >= 0) sv->wave_running = false;
             const auto now = Clock::now();
             for (auto& r : take) {
                 r->t_done = now;
@@ -335,6 +414,7 @@ lps_t lps_open(const lps_options* opt) {
     // the default 8 workers), so that solves of several workers run side by side
     int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, sv->device);
+    sv->team_blocks = sv->opt.team_blocks < 0 ? -1 : sv->opt.team_blocks;
     sv->blocks = sv->opt.blocks_per_lp > 0 ? sv->opt.blocks_per_lp
                                            : std::max(16, 4 * nsm / std::max(1, sv->opt.workers));
     for (int w = 0; w < sv->opt.workers; ++w) sv->workers.emplace_back(worker_main, sv);
@@ -483,6 +563,8 @@ lp_status lps_get_stats(lps_t sv, lps_stats* st) {
     st->queue_p99_ms = percentile(sv->queue_ms, 0.99);
     st->batches = sv->batches;
     st->batched_lps = sv->batched_lps;
+    st->waves = sv->waves;
+    st->wave_lps = sv->wave_lps;
     st->peak_bytes = sv->peak;
     return LP_OPTIMAL;
 }

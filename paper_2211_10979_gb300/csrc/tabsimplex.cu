@@ -12,12 +12,14 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "tabsimplex.h"
 #include "tsx_host.h"
 #include "tsx_kernels.cuh"
 #include "tsx_recover.cuh"
+#include "tsx_team.cuh"
 
 using namespace tsx;
 
@@ -873,6 +875,13 @@ static lp_status solve_nt(lp_handle* h, const lp_options& o, cudaStream_t s) {
     return st;
 }
 
+static bool options_valid(const lp_options& o) {
+    return o.eps_d >= 0.0 && o.eps_p >= 0.0 && o.rule >= 0 && o.rule <= 1 && o.path >= 0 && o.path <= 2 &&
+           o.log_capacity >= 0 && o.precision >= 0 && o.precision <= 1 && o.eps_d_fp32 >= 0.0 &&
+           o.eps_p_fp32 >= 0.0 && o.recover_tol >= 0.0 && o.cleanup_max >= 0 &&
+           (o.layout == LP_LAYOUT_CONDENSED || o.layout == LP_LAYOUT_FULL);
+}
+
 lp_status lp_solve(lp_t h, const lp_options* opt) {
     if (!h) {
         set_error("lp_solve: NULL handle");
@@ -883,10 +892,7 @@ lp_status lp_solve(lp_t h, const lp_options* opt) {
         o = *opt;
     else
         lp_options_init(&o);
-    if (!(o.eps_d >= 0.0) || !(o.eps_p >= 0.0) || o.rule < 0 || o.rule > 1 || o.path < 0 || o.path > 2 ||
-        o.log_capacity < 0 || o.precision < 0 || o.precision > 1 || !(o.eps_d_fp32 >= 0.0) ||
-        !(o.eps_p_fp32 >= 0.0) || !(o.recover_tol >= 0.0) || o.cleanup_max < 0 ||
-        (o.layout != LP_LAYOUT_CONDENSED && o.layout != LP_LAYOUT_FULL)) {
+    if (!options_valid(o)) {
         set_error("lp_solve: invalid options");
         return LP_ERR_INVALID;
     }
@@ -902,6 +908,292 @@ lp_status lp_solve(lp_t h, const lp_options* opt) {
             set_error("lp_solve: threads must be 0, 128, 256 or 512 (got %d)", nt);
             return LP_ERR_INVALID;
     }
+}
+
+// ------------------------------------------------------- many LPs, by teams
+// lp_solve_many: one cooperative launch of k_team_solve over the LPs (largest
+// first), each LP solved by a team of blocks on its condensed tableau; then
+// the per-LP bookkeeping of solve_nt (statistics, and for FP32 the FP64
+// recovery) for each handle.
+
+// The dynamic shared-memory limit of a team kernel is raised once to the
+// device's maximum (process-wide state, never lowered).
+template <int NT, typename V>
+static cudaError_t team_allow_smem(size_t& limit) {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    static size_t lim = 0;
+    std::call_once(once, [] {
+        int dev = 0, optin = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        cudaFuncAttributes fa{};
+        cudaFuncGetAttributes(&fa, k_team_solve<NT, V>);
+        lim = (size_t)std::max(0, optin - (int)fa.sharedSizeBytes);
+        err = cudaFuncSetAttribute(k_team_solve<NT, V>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim);
+    });
+    limit = lim;
+    return err;
+}
+
+// Bookkeeping of one LP after the team launch (as solve_nt): statistics and,
+// for FP32, the FP64 recovery; *status receives the LP's outcome.
+template <typename V>
+static lp_status finish_team_lp(lp_handle* h, const lp_options& o, cudaStream_t s, float ms, int C, int NT,
+                                lp_status* status) {
+    constexpr int elem = (int)sizeof(V);
+    const bool fp32 = elem == 4;
+    DevState ds{};
+    CUDA_TRY(cudaMemcpyAsync(&ds, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
+    CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
+    lp_status st = ds.status == kRunning ? LP_ERR_TIMEOUT : (lp_status)ds.status;
+    if (st == LP_ERR_TIMEOUT) set_error("lp_solve_many: a team barrier wait exceeded its limit");
+    const int m = h->m, ld = h->work.ld, E = 32 / elem;
+    const double nsec = (double)(ld / E);
+    h->stats.iters = ds.iters;
+    h->stats.pivot_ms = ms;
+    h->stats.dense_update_bytes = 2.0 * (double)(m + 1) * (double)h->W * elem * (double)ds.iters;
+    h->stats.update_bytes = ((64.0 * (double)(m - 1) + 96.0) * nsec + 64.0 * (double)(m + 1) +
+                             3.0 * elem * (double)ld) * (double)ds.iters;
+    h->stats.path = LP_PATH_TEAM;
+    h->stats.grid = C;
+    h->stats.block = NT;
+    h->stats.ld = ld;
+    h->stats.layout = LP_LAYOUT_CONDENSED;
+    h->stats.precision = o.precision;
+    h->stats.pivot_status = (int)st;
+    h->stats.kernel_launches = 1;
+    h->iters = ds.iters;
+    if (fp32 && (st == LP_OPTIMAL || st == LP_ITER_LIMIT || st == LP_UNBOUNDED)) {
+        cudaEventRecord(h->ev[3], s);
+        long long rl = 0;
+        lp_status rs = recover(h, o, s, rl);
+        if (rs == LP_ERR_CUDA) return rs;
+        cudaEventRecord(h->ev[2], s);
+        CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
+        float ms_rec = 0.f;
+        cudaEventElapsedTime(&ms_rec, h->ev[3], h->ev[2]);
+        h->stats.recover_ms = ms_rec;
+        h->stats.kernel_launches += rl;
+        st = rs;
+        h->sol_ready = rs == LP_OPTIMAL;
+    }
+    cudaEventRecord(h->ready, s);
+    h->solved = true;
+    h->last_status = st;
+    *status = st;
+    return LP_OPTIMAL;
+}
+
+template <typename V>
+static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, cudaStream_t s,
+                              lp_status* status) {
+    constexpr int NT = 256;
+    constexpr int elem = (int)sizeof(V);
+    const bool fp32 = elem == 4;
+    const int count = (int)hs.size();
+    int device = 0, nsm = 0;
+    CUDA_TRY(cudaGetDevice(&device), LP_ERR_CUDA);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    size_t smem_limit = 0;
+    const cudaError_t se = team_allow_smem<NT, V>(smem_limit);
+    CUDA_TRY(se, LP_ERR_CUDA);
+    int C = o.blocks > 0 ? std::min(o.blocks, kTeamMax) : 16;
+
+    // work buffers and state of every LP (condensed layout)
+    for (lp_handle* h : hs) {
+        CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ready, 0), LP_ERR_CUDA);
+        lp_status st = ensure_work(h, elem, 1);
+        if (st != LP_OPTIMAL) return st;
+        h->stats = lp_stats{};
+        h->sol_ready = false;
+        h->final_basis.clear();
+        k_reset_state<<<1, 32, 0, h->stream>>>(h->st);
+        CUDA_TRY(cudaEventRecord(h->ev[0], h->stream), LP_ERR_CUDA);
+        CUDA_TRY(cudaStreamWaitEvent(s, h->ev[0], 0), LP_ERR_CUDA);
+    }
+    // the list, largest first; LPs whose pivot row and multipliers exceed the
+    // shared memory of one block are solved one at a time afterwards
+    std::vector<TeamJob<V>> jobs;
+    std::vector<int> who, alone;
+    std::vector<double> work;
+    int ld_max = 0, rows_max = 0;
+    for (int k = 0; k < count; ++k) {
+        lp_handle* h = hs[k];
+        const int rows = (h->m + 1 + C - 1) / C;
+        if ((size_t)(h->work.ld + rows) * elem > smem_limit) {
+            alone.push_back(k);
+            continue;
+        }
+        TeamJob<V> J{};
+        J.A = h->A;
+        J.b = h->b;
+        J.c = h->c;
+        J.T = (V*)h->work.T;
+        J.basis = h->basis;
+        J.var = h->work.var;
+        J.st = h->st;
+        J.m = h->m;
+        J.n = h->n;
+        J.ld = h->work.ld;
+        jobs.push_back(J);
+        who.push_back(k);
+        work.push_back((double)(h->m + 1) * h->work.ld * (double)(h->m + h->n));
+        ld_max = std::max(ld_max, h->work.ld);
+        rows_max = std::max(rows_max, rows);
+    }
+    const int njobs = (int)jobs.size();
+    std::vector<int> order(njobs);
+    for (int k = 0; k < njobs; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+
+    float ms = 0.f;
+    if (njobs > 0) {
+        const size_t smem = (size_t)(ld_max + ((rows_max + 31) / 32) * 32) * elem;
+        int per = 0;
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_team_solve<NT, V>, NT, smem);
+        const int cap = per * nsm;
+        if (cap <= 0) {
+            set_error("lp_solve_many: the team kernel cannot be resident (%zu bytes of shared memory)", smem);
+            return LP_ERR_CUDA;
+        }
+        C = std::min(C, cap);
+        const int nteams = std::max(1, std::min(njobs, cap / C));
+        // scratch: jobs | order | counter | team states
+        Carve cv;
+        const size_t o_jobs = cv.take(sizeof(TeamJob<V>) * (size_t)njobs);
+        const size_t o_order = cv.take(sizeof(int) * (size_t)njobs);
+        const size_t o_next = cv.take(sizeof(unsigned));
+        const size_t o_teams = cv.take(sizeof(TeamState) * (size_t)nteams);
+        const size_t bytes = align_up(cv.off, 256);
+        lp_handle* h0 = hs[who[0]];
+        void* scratch = h0->alloc ? h0->alloc(bytes, (void*)s, h0->alloc_ctx) : nullptr;
+        if (!h0->alloc && cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
+            cudaGetLastError();
+            scratch = nullptr;
+        }
+        if (!scratch) {
+            set_error("lp_solve_many: allocation of %zu bytes of scratch failed", bytes);
+            return LP_ERR_NOMEM;
+        }
+        char* base = (char*)scratch;
+        TeamParams<V> P{};
+        P.jobs = (const TeamJob<V>*)(base + o_jobs);
+        P.order = (const int*)(base + o_order);
+        P.njobs = njobs;
+        P.next = (unsigned*)(base + o_next);
+        P.teams = (TeamState*)(base + o_teams);
+        P.team = C;
+        P.eps_d = fp32 ? o.eps_d_fp32 : o.eps_d;
+        P.eps_p = fp32 ? o.eps_p_fp32 : o.eps_p;
+        P.max_iters = o.max_iters;
+        P.k_cyc = o.k_cyc;
+        P.rule = o.rule;
+        P.timeout_ns = std::max(0LL, o.barrier_timeout_ns);
+        cudaError_t e = cudaMemcpyAsync(base + o_jobs, jobs.data(), sizeof(TeamJob<V>) * (size_t)njobs,
+                                        cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(base + o_order, order.data(), sizeof(int) * (size_t)njobs, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(base + o_next, 0, bytes - o_next, s);
+        cudaEvent_t e0 = hs[who[0]]->ev[1], e1 = hs[who[0]]->ev[2];
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        int ldm = ld_max;
+        void* args[] = {(void*)&P, (void*)&ldm};
+        if (e == cudaSuccess)
+            e = cudaLaunchCooperativeKernel((const void*)k_team_solve<NT, V>, nteams * C, NT, args, smem, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);
+        if (h0->dealloc)
+            h0->dealloc(scratch, bytes, (void*)s, h0->alloc_ctx);
+        else
+            cudaFreeAsync(scratch, s);
+        if (e != cudaSuccess) {
+            set_error("lp_solve_many: team launch failed: %s", cudaGetErrorString(e));
+            return LP_ERR_CUDA;
+        }
+    }
+    // per-LP bookkeeping (as solve_nt) and the FP64 recovery of FP32 results,
+    // spread over host threads with a stream each (the recovery is a chain of
+    // small kernels and host decisions per LP)
+    const int nthreads = fp32 ? std::max(1, std::min(njobs, 8)) : 1;
+    std::vector<lp_status> fail(nthreads, LP_OPTIMAL);
+    auto finish = [&](int tid, cudaStream_t ss) -> lp_status {
+        for (int t = tid; t < njobs; t += nthreads) {
+            const lp_status st = finish_team_lp<V>(hs[who[t]], o, ss, ms, C, NT, status + who[t]);
+            if (st == LP_ERR_CUDA) return st;
+        }
+        return LP_OPTIMAL;
+    };
+    if (nthreads == 1) {
+        fail[0] = finish(0, s);
+    } else {
+        std::vector<std::thread> th;
+        for (int k = 0; k < nthreads; ++k)
+            th.emplace_back([&, k] {
+                cudaSetDevice(device);
+                cudaStream_t ss = nullptr;
+                if (cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking) != cudaSuccess) {
+                    fail[k] = LP_ERR_CUDA;
+                    return;
+                }
+                fail[k] = finish(k, ss);
+                cudaStreamSynchronize(ss);
+                cudaStreamDestroy(ss);
+            });
+        for (auto& t : th) t.join();
+    }
+    for (lp_status f : fail)
+        if (f != LP_OPTIMAL) return f;
+    // the rest, one at a time
+    for (int k : alone) {
+        lp_options oa = o;
+        oa.blocks = 0;
+        status[k] = solve_nt<NT>(hs[k], oa, s);
+    }
+    return LP_OPTIMAL;
+}
+
+lp_status lp_solve_many(lp_t* handles, int count, const lp_options* opt, lp_status* status) {
+    if (!handles || !status || count < 0) {
+        set_error("lp_solve_many: NULL argument or count < 0");
+        return LP_ERR_INVALID;
+    }
+    lp_options o;
+    if (opt)
+        o = *opt;
+    else
+        lp_options_init(&o);
+    if (!options_valid(o) || o.layout != LP_LAYOUT_CONDENSED || o.log_capacity != 0 ||
+        (o.threads != 0 && o.threads != 256) || o.blocks < 0) {
+        set_error("lp_solve_many: invalid options (condensed layout, no pivot log, threads 0 or 256)");
+        return LP_ERR_INVALID;
+    }
+    if (count == 0) return LP_OPTIMAL;
+    std::vector<lp_handle*> hs(handles, handles + count);
+    for (int k = 0; k < count; ++k) {
+        status[k] = LP_ERR_STATE;
+        if (!hs[k]) {
+            set_error("lp_solve_many: handle %d is NULL", k);
+            return LP_ERR_INVALID;
+        }
+        if (hs[k]->device != hs[0]->device) {
+            set_error("lp_solve_many: handle %d lives on another device", k);
+            return LP_ERR_INVALID;
+        }
+    }
+    {
+        std::vector<lp_handle*> sorted(hs);
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
+            set_error("lp_solve_many: a handle appears twice");
+            return LP_ERR_INVALID;
+        }
+    }
+    CUDA_TRY(cudaSetDevice(hs[0]->device), LP_ERR_CUDA);
+    cudaStream_t s = o.stream ? (cudaStream_t)o.stream : hs[0]->stream;
+    return o.precision == LP_PREC_FP32 ? solve_many_t<float>(hs, o, s, status)
+                                       : solve_many_t<double>(hs, o, s, status);
 }
 
 lp_status lp_get_solution(lp_t h, double* x, double* y, double* obj, int* basis, long long* iters) {

@@ -1,0 +1,308 @@
+// Team solve: many LPs at once, each by a team of C thread blocks (the
+// full-tableau simplex of arXiv 2211.10979, Section III, Steps 1-3), for LPs
+// too large for one block's shared memory and too small to fill the GPU.
+//
+// One cooperative launch holds every team; a team takes the next LP from a
+// list (largest first) and solves it on its condensed tableau in global
+// memory.  Block b of the team owns a contiguous range of rows: it runs the
+// ratio test on its rows (keeping their column-q entries, the multipliers, in
+// shared memory), stages the whole scaled pivot row R in its own shared memory
+// (each block divides row p by the pivot itself), and updates its rows.  Block
+// 0 owns row 0 and finds the next entering column while it updates it.  Two
+// team barriers per pivot: after the ratio test (every block learns p) and
+// after the update (every block learns the next entering column, and every
+// block has read row p, so its owner may now overwrite it with R).  The
+// arithmetic and the tie rules are those of the single-LP kernels, so every
+// pivot and value equals lp_solve's.
+#pragma once
+
+#include "tsx_device.cuh"
+
+namespace tsx {
+
+constexpr int kTeamMax = 64;   // blocks per team, upper bound
+
+template <typename V>
+struct TeamJob {
+    const double* A;           // inputs (device), m x n row-major, m, n
+    const double* b;
+    const double* c;
+    V* T;                      // condensed tableau (m+1) x ld
+    int* basis;                // m
+    int* var;                  // n
+    DevState* st;              // the LP's state words: status, iters, bland, degen_run
+    int m, n, ld;
+    int pad;
+};
+
+struct __align__(256) TeamState {   // one per team
+    unsigned bar_count;
+    unsigned bar_gen;
+    int job;
+    int fail;                  // set when a team barrier wait ran out
+    ArgPart ent;               // next entering candidate (block 0)
+    RatPart rat[kTeamMax];     // ratio-test partial of each block
+};
+
+template <typename V>
+struct TeamParams {
+    const TeamJob<V>* jobs;
+    const int* order;          // job indices, largest first
+    int njobs;
+    unsigned* next;            // list position counter
+    TeamState* teams;
+    int team;                  // blocks per team
+    double eps_d, eps_p;
+    long long max_iters;       // < 0: 50 (m + n)
+    int k_cyc, rule;
+    long long timeout_ns;
+};
+
+// Barrier of the C blocks of one team; bounded like grid_barrier.  Returns
+// false (in every thread) if the wait ran out or another block of the team
+// gave up.
+__device__ inline bool team_barrier(TeamState* ts, unsigned C, long long timeout_ns, int& sok) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned gen = ld_acquire(&ts->bar_gen);
+        const unsigned arrived = atom_add_acq_rel(&ts->bar_count, 1u);
+        if (arrived == C - 1) {
+            ts->bar_count = 0;
+            st_release(&ts->bar_gen, gen + 1);
+        } else {
+            const long long t0 = global_ns();
+            const unsigned long long max_spins = (unsigned long long)(timeout_ns > 0 ? timeout_ns : 0) + 4096ull;
+            unsigned long long spins = 0;
+            while (ld_acquire(&ts->bar_gen) == gen) {
+                ++spins;
+                if ((spins & 31ull) == 1) {
+                    if (ld_relaxed(&ts->fail) != 0) { ok = 0; break; }
+                    if (global_ns() - t0 >= timeout_ns || spins > max_spins) {
+                        atomicExch(&ts->fail, 1);
+                        ok = 0;
+                        break;
+                    }
+                }
+            }
+        }
+        __threadfence();
+        sok = ok;
+    }
+    __syncthreads();
+    return sok != 0;
+}
+
+// Rows of block bt among C: [r0, r1) of 0..m.
+__device__ __forceinline__ void team_rows(int m, int C, int bt, int& r0, int& r1) {
+    const int per = (m + 1 + C - 1) / C;
+    r0 = min(m + 1, bt * per);
+    r1 = min(m + 1, r0 + per);
+}
+
+// Condensed Table I rows [r0, r1) (slack basis): row 0 = [-c | 0], row i =
+// [A_i | b_i], padding zero; the LP's basis words of those rows; var[] by block 0.
+template <typename V>
+__device__ void team_build(const TeamJob<V>& J, int r0, int r1, int bt) {
+    constexpr int E = Lanes<V>::E;
+    const int n = J.n, ld = J.ld;
+    const long long per_row = ld / E;
+    const long long total = (long long)(r1 - r0) * per_row;
+    for (long long g = threadIdx.x; g < total; g += blockDim.x) {
+        const int i = r0 + (int)(g / per_row);
+        const int j0 = (int)(g - (long long)(i - r0) * per_row) * E;
+        Sector<V> out;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int j = j0 + e;
+            double v = 0.0;
+            if (i == 0) {
+                if (j < n) v = -J.c[j];
+            } else if (j < n) {
+                v = J.A[(size_t)(i - 1) * (size_t)n + j];
+            } else if (j == n) {
+                v = J.b[i - 1];
+            }
+            out.v[e] = (V)v;
+        }
+        st_sector(J.T + (size_t)i * (size_t)ld + j0, out);
+    }
+    for (int i = max(r0, 1) + threadIdx.x; i < r1; i += blockDim.x) J.basis[i - 1] = n + i - 1;
+    if (bt == 0)
+        for (int j = threadIdx.x; j < n; j += blockDim.x) J.var[j] = j;
+}
+
+// Objective row (block 0): T[0][j] = fma(-f0, R[j], T[0][j]) (q: from the
+// leaving variable's unit column, 0 off row p) when R != null, then the
+// entering candidate of the new row over all slots, posted to the team.
+template <typename V>
+__device__ void team_row0(const TeamJob<V>& J, const V* R, V f0, int q, const TeamParams<V>& P, TeamState* ts,
+                          BlockScratch& s) {
+    constexpr int E = Lanes<V>::E;
+    const int nsec = J.ld / E;
+    ArgPart a = arg_none();
+    for (int g = threadIdx.x; g < nsec; g += blockDim.x) {
+        const int j = g * E;
+        Sector<V> o = ld_sector_cg(J.T + j);
+        if (R) {
+            const Sector<V> r = *reinterpret_cast<const Sector<V>*>(R + j);
+#pragma unroll
+            for (int e = 0; e < E; ++e) o.v[e] = fma_rn(-f0, r.v[e], j + e == q ? V(0) : o.v[e]);
+            st_sector(J.T + j, o);
+        }
+        arg_consider_sector(a, o, j, J.n, P.eps_d, J.var);
+    }
+    a = block_arg(a, s);
+    if (threadIdx.x == 0) store_arg(&ts->ent, a);
+}
+
+// Rank-1 update of the block's rows [lo, r1) except p, R and the multipliers
+// (Floc, indexed from r0) in shared memory; slots of 8 rows x 32 column
+// groups, one group per lane.
+template <typename V>
+__device__ void team_update(const TeamJob<V>& J, const V* R, const V* Floc, int r0, int lo, int r1, int p, int q) {
+    constexpr int E = Lanes<V>::E;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int nsec = J.ld / E;
+    const int nchunks = (nsec + 31) / 32;
+    const int nrg = (r1 - lo + kRowsInFlight - 1) / kRowsInFlight;
+    const long long total = (long long)nrg * nchunks;
+    for (long long u = warp; u < total; u += nw) {
+        const int rg = (int)(u / nchunks), ch = (int)(u - (long long)rg * nchunks);
+        const int i0 = lo + rg * kRowsInFlight;
+        const int nrows = min(kRowsInFlight, r1 - i0);
+        const int gidx = ch * 32 + lane;
+        if (gidx >= nsec) continue;
+        const size_t col = (size_t)E * (size_t)gidx;
+        const Sector<V> r = *reinterpret_cast<const Sector<V>*>(R + col);
+        const int eq = q - (int)col;
+        Sector<V> v[kRowsInFlight];
+#pragma unroll
+        for (int k = 0; k < kRowsInFlight; ++k) {
+            const int i = i0 + k;
+            if (k < nrows && i != p) v[k] = ld_sector_stream(J.T + (size_t)i * (size_t)J.ld + col);
+        }
+#pragma unroll
+        for (int k = 0; k < kRowsInFlight; ++k) {
+            const int i = i0 + k;
+            if (k < nrows && i != p) {
+                const V f = Floc[i - r0];
+#pragma unroll
+                for (int e2 = 0; e2 < E; ++e2) v[k].v[e2] = fma_rn(-f, r.v[e2], e2 == eq ? V(0) : v[k].v[e2]);
+                st_sector(J.T + (size_t)i * (size_t)J.ld + col, v[k]);
+            }
+        }
+    }
+}
+
+// Solves one LP with the team; false if a team barrier failed.
+template <typename V>
+__device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, TeamState* ts, int bt,
+                               V* R, V* Floc, BlockScratch& s, int& sok) {
+    const unsigned C = (unsigned)P.team;
+    const int m = J.m, n = J.n, ld = J.ld;
+    int r0, r1;
+    team_rows(m, (int)C, bt, r0, r1);
+    team_build(J, r0, r1, bt);
+    __syncthreads();
+    if (bt == 0) team_row0(J, (const V*)nullptr, V(0), -1, P, ts, s);   // Step 1 of the first pivot
+    if (!team_barrier(ts, C, P.timeout_ns, sok)) return false;
+    const long long cap = P.max_iters < 0 ? 50LL * ((long long)m + n) : P.max_iters;
+    long long it = 0;
+    int bland = P.rule == 1, degen = 0;
+    int status = kRunning;
+    const int lo = max(r0, 1);
+    for (;;) {
+        const ArgPart e = load_arg(&ts->ent);                // Step 1
+        const int q = bland ? e.fslot : e.slot;
+        const int qv = bland ? e.fkey : e.key;
+        if (qv == INT_MAX) { status = kOptimal; break; }
+        if (it >= cap) { status = kIterLimit; break; }
+        // Step 2 on the block's rows; their column-q entries become the multipliers
+        RatPart best = rat_none();
+        if (bt == 0 && threadIdx.x == 0) Floc[0] = __ldcg(J.T + q);
+        for (int i = lo + threadIdx.x; i < r1; i += blockDim.x) {
+            const V* row = J.T + (size_t)i * (size_t)ld;
+            const V a = __ldcg(row + q);
+            Floc[i - r0] = a;
+            if ((double)a > P.eps_p) {
+                RatPart c;
+                c.r = (double)div_rn(__ldcg(row + n), a);
+                c.i = i;
+                c.key = bland ? __ldcg(J.basis + (i - 1)) : i;
+                c.a = (double)a;
+                c.pad = 0.0;
+                rat_merge(best, c);
+            }
+        }
+        best = block_rat(best, s);
+        if (threadIdx.x == 0) store_rat(&ts->rat[bt], best);
+        if (!team_barrier(ts, C, P.timeout_ns, sok)) return false;
+        RatPart l = rat_none();
+        if (threadIdx.x < (int)C) l = load_rat(&ts->rat[threadIdx.x]);
+        l = block_rat(l, s);
+        if (l.i == INT_MAX) { status = kUnbounded; break; }
+        const int p = l.i;
+        const V piv = (V)l.a;
+        if (!isfinite((double)piv) || !isfinite(l.r)) { status = kNumeric; break; }
+        // Step 3: every block scales row p itself; the leaving variable takes slot q
+        const V* rowp = J.T + (size_t)p * (size_t)ld;
+        for (int j = threadIdx.x; j < ld; j += blockDim.x) R[j] = div_rn(j == q ? V(1) : __ldcg(rowp + j), piv);
+        if (bt == 0 && threadIdx.x == 0) {
+            const int leaving = J.basis[p - 1];
+            J.basis[p - 1] = qv;
+            J.var[q] = leaving;
+        }
+        if (P.rule == 0) {
+            if (l.r <= 0.0) {
+                ++degen;
+                if (P.k_cyc > 0 && degen >= P.k_cyc) bland = 1;
+            } else {
+                degen = 0;
+                bland = 0;
+            }
+        }
+        __syncthreads();
+        if (bt == 0) team_row0(J, R, Floc[0], q, P, ts, s);   // the next Step 1 on the new row 0
+        team_update(J, R, Floc, r0, lo, r1, p, q);
+        ++it;
+        if (!team_barrier(ts, C, P.timeout_ns, sok)) return false;
+        if (p >= r0 && p < r1) {   // every block has read row p: its owner stores R there
+            for (int j = threadIdx.x; j < ld; j += blockDim.x) J.T[(size_t)p * (size_t)ld + j] = R[j];
+            __syncthreads();
+        }
+    }
+    if (bt == 0 && threadIdx.x == 0) {
+        J.st->status = status;
+        J.st->iters = it;
+        J.st->bland = bland;
+        J.st->degen_run = degen;
+    }
+    return true;
+}
+
+// One cooperative launch: team t = blocks [t C, (t+1) C) takes list entries
+// until none is left.  Dynamic shared memory per block: R (ld_max entries)
+// then the multipliers (rows per block, max over the list).
+template <int NT, typename V>
+__global__ void __launch_bounds__(NT, 512 / NT) k_team_solve(TeamParams<V> P, int ld_max) {
+    extern __shared__ __align__(32) unsigned char team_smem[];
+    __shared__ BlockScratch s;
+    __shared__ int sok;
+    const int C = P.team;
+    const int t = blockIdx.x / C, bt = blockIdx.x - t * C;
+    TeamState* ts = P.teams + t;
+    V* R = reinterpret_cast<V*>(team_smem);
+    V* Floc = R + ld_max;
+    for (;;) {
+        if (bt == 0 && threadIdx.x == 0) ts->job = (int)atomicAdd(P.next, 1u);
+        if (!team_barrier(ts, (unsigned)C, P.timeout_ns, sok)) return;
+        const int k = *(volatile const int*)&ts->job;
+        if (k >= P.njobs) return;
+        const TeamJob<V> J = P.jobs[P.order[k]];
+        if (!team_solve_one(P, J, ts, bt, R, Floc, s, sok)) return;
+    }
+}
+
+}  // namespace tsx

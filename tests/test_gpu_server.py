@@ -73,6 +73,7 @@ def test_results_same_alone_and_in_the_mix(tsx):
             results.append(sv.result(t))
         st = sv.stats()
     assert st["completed"] == len(problems) and st["batched_lps"] > 0
+    assert st["waves"] > 0 and st["wave_lps"] + st["batched_lps"] == len(problems)
     for k, ((m, n), (A, b, c), r) in enumerate(zip(shapes, problems, results)):
         ref = oracle.solve(A, b, c)
         if (m + 1) * (n + 2) * 8 < 200_000:
@@ -130,6 +131,22 @@ def test_global_memory_micro_batches(tsx):
         ref = oracle.solve(A, b, c)
         assert code == tsx.LP_OPTIMAL and r.obj == ref.obj and r.iters == ref.iters
         np.testing.assert_array_equal(r.x, ref.x)
+
+
+def test_one_per_worker_without_waves(tsx):
+    # team_blocks < 0: the large requests are solved one per worker by lp_solve
+    shapes = [(300, 250), (256, 700), (600, 300)] * 2
+    problems = [lpgen.dense_lp(m, n, 900 + k) for k, (m, n) in enumerate(shapes)]
+    with tsx.Server(workers=3, team_blocks=-1) as sv:
+        tickets = [sv.submit(*p) for p in problems]
+        res = [(sv.wait(t, 120.0), sv.result(t)) for t in tickets]
+        st = sv.stats()
+    assert st["waves"] == 0 and st["completed"] == len(problems)
+    for (A, b, c), (code, r) in zip(problems, res):
+        st1, alone = _alone_fp32(tsx, A, b, c)
+        assert code == st1 == tsx.LP_OPTIMAL
+        assert r.obj == alone.obj and r.iters == alone.iters
+        np.testing.assert_array_equal(r.x, alone.x)
 
 
 def test_plain_mode_and_stats(tsx):
