@@ -54,7 +54,7 @@ def parse_args(argv=None):
     ap.add_argument("--path", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--blocks", type=int, default=0)
-    ap.add_argument("--workload", choices=["single", "batch", "serve"], default="single",
+    ap.add_argument("--workload", choices=["single", "batch", "serve", "many"], default="single",
                     help="batch: 4096 small LPs (m, n uniform in [16, 128]) per step; serve: a "
                          "Poisson stream of LPs (m, n log-uniform in [32, 4096]) through the server")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
@@ -67,6 +67,8 @@ def parse_args(argv=None):
     ap.add_argument("--serve-path", type=int, default=2,
                     help="serve: single-lane solve path (1 persistent cooperative, 2 one launch per phase)")
     ap.add_argument("--batch-count", type=int, default=4096)
+    ap.add_argument("--many-count", type=int, default=300, help="many: LPs drawn before the size filter")
+    ap.add_argument("--many-team", type=int, default=0, help="many: blocks per team (0 = default)")
     ap.add_argument("--batch-threads", type=int, default=0,
                     help="batch: threads per LP (32/64/128/256); 0 = autotuned per size class")
     ap.add_argument("--plain-sample", type=int, default=256,
@@ -598,6 +600,110 @@ def run_batch(args, rank, world, local):
     return 0
 
 
+def many_shapes(count, seed):
+    """The LPs of the serving distribution (m, n log-uniform in [32, 4096])
+    whose condensed FP64 tableau exceeds one SM's shared memory: the ones the
+    server solves in lp_solve_many waves."""
+    shapes = lpgen.loguniform_shapes(count, 32, 4096, seed)
+    return [(m, n) for m, n in shapes if (m + 1) * (n + 2) * 8 > 232_448]
+
+
+def run_many(args, rank, world, local):
+    """lp_solve_many on the medium and large LPs of the serving distribution,
+    inputs resident in HBM; plain = the same LPs one at a time by lp_solve."""
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2211_10979_gb300 as tsx
+    from paper_2211_10979_gb300 import build as tsx_build
+    tsx_build.build()
+    tsx.use_torch_allocator()
+    shapes = many_shapes(args.many_count, 5 + rank)
+    seeds = [1000 + k for k in range(len(shapes))]
+    stream = torch.cuda.current_stream(dev)
+    sptr = stream.cuda_stream
+    prec = tsx.LP_PREC_FP32 if args.precision == "fp32" else tsx.LP_PREC_FP64
+    inputs = []
+    for (m, n), sd in zip(shapes, seeds):
+        dA = torch.empty(m * n, dtype=torch.float64, device=dev)
+        db = torch.empty(m, dtype=torch.float64, device=dev)
+        dc = torch.empty(n, dtype=torch.float64, device=dev)
+        tsx.lp_generate_dense(m, n, sd, dA, db, dc, sptr)
+        inputs.append((dA.view(m, n), db, dc))
+    torch.cuda.synchronize(dev)
+    prs = [tsx.Problem(dA, db, dc, device=True, stream=sptr) for dA, db, dc in inputs]
+    opts = tsx.options(precision=prec, blocks=args.many_team, stream=sptr)
+    for _ in range(args.warmup):
+        tsx.solve_many(prs, opts)
+    torch.cuda.synchronize(dev)
+    clocks = ClockSampler(local)
+    clocks.start()
+    walls, kernel_ms, upd = [], [], []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st = tsx.solve_many(prs, opts)
+        walls.append(time.perf_counter() - t0)
+        stats = [pr.stats() for pr in prs]
+        kernel_ms.append(stats[0]["pivot_ms"])
+        upd.append(sum(x["update_bytes"] for x in stats))
+    clk = clocks.stop()
+    bad = sum(1 for v in st if v != tsx.LP_OPTIMAL)
+    pivots = sum(x["iters"] for x in stats)
+    value = len(prs) * args.steps / sum(walls)
+    k_ms = statistics.median(kernel_ms)
+    achieved = statistics.median(upd) / (k_ms / 1000.0) / 1e9
+    peak, peak_src = measured_peaks()
+    # plain: every LP once through lp_solve (default persistent path)
+    po = tsx.options(precision=prec, stream=sptr)
+    t0 = time.perf_counter()
+    for pr in prs:
+        pr.solve(po)
+    plain = len(prs) / (time.perf_counter() - t0)
+    # e2e: host inputs, handles created and results read back inside the timed region
+    host = [tuple(t.cpu().numpy() for t in inp) for inp in inputs]
+    e2e_steps = max(1, min(args.steps, 2))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        hp = [tsx.Problem(A, b, c) for A, b, c in host]
+        tsx.solve_many(hp, opts)
+        for pr in hp:
+            pr.solution()
+            pr.close()
+    e2e = len(prs) * e2e_steps / (time.perf_counter() - t0)
+    for pr in prs:
+        pr.close()
+    cpu = None if args.no_cpu_baseline else oracle_batch_sample(host, args.cpu_seconds)
+    line = {
+        "metric": "LPs/s", "value": value, "unit": "LPs/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1000.0 * sum(walls) / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 tableau + f64 recovery" if prec == tsx.LP_PREC_FP32 else "f64",
+        "data": "synthetic",
+        "config": {"workload": f"lp_solve_many over the {len(prs)} LPs of {args.many_count} drawn from the "
+                               "serving distribution (m, n log-uniform in [32, 4096]) whose condensed tableau "
+                               "exceeds one SM's shared memory; one call per step, inputs resident in HBM",
+                   "team_blocks": args.many_team or 32, "pivots_per_step": pivots,
+                   "l2": "tableaux of the step total well above L2"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)", "traffic": None,
+                     "kernel": "k_team_solve", "kernel_ms_per_launch": k_ms,
+                     "bytes_per_launch": statistics.median(upd)},
+        "plain": {"value": plain, "unit": "LPs/s", "path": "the same LPs one at a time through lp_solve",
+                  "speedup": value / plain},
+        "non_optimal": bad,
+        "e2e": {"value": e2e, "unit": "LPs/s",
+                "h2d_bytes_per_step": int(sum(8 * (m * n + m + n) for m, n in shapes)),
+                "d2h_bytes_per_step": int(sum(8 * (m + n + 1) for m, n in shapes)),
+                "note": "lp_create from host arrays, lp_solve_many, lp_get_solution, lp_destroy"},
+        "gpu_launches": int(sum(x["kernel_launches"] for x in stats)) * args.steps,
+        "clocks": clk,
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def play_stream(tsx, torch, dev, shapes, arrivals, seeds, server_kw):
     """Submits each request at its arrival time (inputs generated on the device
     just before), waits for all, returns per-request (status, latency s, obj)
@@ -705,6 +811,10 @@ def main(argv=None):
         return run_reference(args, rank, world)
     if args.workload == "batch":
         return run_batch(args, rank, world, local)
+    if args.workload == "many":
+        if rank != 0:
+            return 0
+        return run_many(args, rank, world, local)
     if args.workload == "serve":
         if rank != 0:
             return 0

@@ -172,7 +172,7 @@ lp_status lp_solve(lp_t h, const lp_options *opt);
 
 /* Solve `count` LPs at once, each from its slack basis (the method of
  * lp_solve: Section III, Initialization Step and Steps 1-3).  One cooperative
- * launch divides the GPU into teams of opt->blocks thread blocks (default 16);
+ * launch divides the GPU into teams of opt->blocks thread blocks (default 32);
  * each team takes the next LP from the list, largest first, and iterates on
  * its condensed tableau: block b of the team owns a contiguous range of rows,
  * runs the ratio test on them and updates them, with the scaled pivot row and
@@ -357,7 +357,7 @@ typedef struct {
                                      cooperative launches of the persistent
                                      path largely run one at a time)            */
     int team_blocks;              /* >= 0 (default 0: lp_solve_many's default
-                                     team of 16 blocks): the requests too
+                                     team of 32 blocks): the requests too
                                      large for the micro-batches are solved in
                                      waves by lp_solve_many with teams of this
                                      many blocks -- every such request waiting

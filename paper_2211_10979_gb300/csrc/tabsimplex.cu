@@ -998,7 +998,7 @@ static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, 
     size_t smem_limit = 0;
     const cudaError_t se = team_allow_smem<NT, V>(smem_limit);
     CUDA_TRY(se, LP_ERR_CUDA);
-    int C = o.blocks > 0 ? std::min(o.blocks, kTeamMax) : 16;
+    int C = o.blocks > 0 ? std::min(o.blocks, kTeamMax) : 32;
 
     // work buffers and state of every LP (condensed layout)
     for (lp_handle* h : hs) {
