@@ -76,10 +76,11 @@ typedef struct {
     int path;                     /* LP_PATH_AUTO: persistent cooperative kernel
                                      when it can be launched, else one launch
                                      per phase                                  */
-    int skip_zero_columns;        /* 1 (default): Step 3 leaves untouched every
-                                     32-byte group of columns whose scaled pivot
-                                     row entries are all zero (their update is
-                                     the identity); 0: update every column      */
+    int skip_zero_columns;        /* full layout only: 1 (default): Step 3
+                                     leaves untouched every 32-byte group of
+                                     columns whose scaled pivot row entries are
+                                     all zero (their update is the identity);
+                                     0: update every column                     */
     int threads;                  /* threads per block, 0 = default (256)       */
     int blocks;                   /* grid size cap, 0 = all co-resident blocks  */
     long long log_capacity;       /* pivots whose (q, p) pair is recorded;
@@ -206,12 +207,15 @@ lp_status lp_get_solution(lp_t h, double *x, double *y, double *obj, int *basis,
                           long long *iters);
 
 /* Copy the current tableau to HOST memory T ((m + 1) x (n + m + 1) row-major,
- * float64, without the padding; a float tableau is widened).  Returns
+ * float64, without the padding; a float tableau is widened; a condensed
+ * tableau is expanded on the device: its slots go to their variables'
+ * columns and the basic variables get their unit columns).  Returns
  * LP_ERR_STATE before any solve. */
 lp_status lp_get_tableau(lp_t h, double *T);
 
-/* Copy the recorded (q, p) pairs of the last solve (q = entering column,
- * p = leaving row in 1..m) to HOST arrays of `cap` entries; *count receives the
+/* Copy the recorded (q, p) pairs of the last solve (q = entering variable,
+ * i.e. its Table I column, p = leaving row in 1..m) to HOST arrays of `cap`
+ * entries; *count receives the
  * number of pivots recorded (min(iters, log_capacity)). */
 lp_status lp_get_pivot_log(lp_t h, int *q, int *p, long long cap, long long *count);
 

@@ -2,23 +2,29 @@
 // Section III Steps 1-3; Section IV Steps 1-4 for one GPU).
 //
 // One pivot is four phases over the row-major tableau T ((m+1) x ld entries of
-// type V = double or float, W = n + m + 1 logical columns, the last one the
-// right-hand side):
-//   P1  entering column q: reduce the per-strip (value, index) partials of the
-//       objective row left by the previous P4 (Section III Step 1, Dantzig's
-//       most negative coefficient; Section IV Step 1's local-then-global
-//       reduction, here warp -> strip -> block).
+// type V = double or float; the last logical column W-1 is the right-hand
+// side).  The full layout holds Table I itself (W = n + m + 1 columns); the
+// condensed layout holds the n nonbasic columns and the right-hand side
+// (W = n + 1) with var[j] = the variable of column slot j -- the basic columns
+// are exact unit vectors, and the leaving variable takes the entering slot:
+//   P1  entering column q: reduce the per-strip (value, variable, slot)
+//       partials of the objective row left by the previous P4 (Section III
+//       Step 1, Dantzig's most negative coefficient, lowest variable on ties;
+//       Section IV Step 1's local-then-global reduction, here warp -> strip ->
+//       block).
 //   P2  minimum-ratio test on column q (Section III Step 2, Section IV Step 2):
 //       every block scans a share of the rows, copies column q into F and keeps
-//       its best (ratio, key, row) -> one partial per block.
+//       its best (ratio, key, row, pivot element) -> one partial per block.
 //   P3  leaving row p = reduce of the P2 partials; pivot-row staging
-//       R[j] = T[p][j] / T[p][q] (Section III Step 3's pivot row) and the list
-//       of 32-byte column groups of row p holding a nonzero entry.
-//   P4  rank-1 update T[i][j] = fma(-F[i], R[j], T[i][j]) for i != p and
-//       T[p][j] = R[j] (Section III Step 3, Section IV Step 4), streamed with
-//       256-bit accesses; the objective row is updated first, one warp per strip,
-//       each emitting that strip's argmin partial of the new objective row (the
-//       next P1's input).
+//       R[j] = T[p][j] / T[p][q] (Section III Step 3's pivot row; condensed:
+//       R[q] = 1 / T[p][q], the leaving variable's new column) and, in the
+//       full layout, the list of 32-byte column groups of row p holding a
+//       nonzero entry.
+//   P4  rank-1 update T[i][j] = fma(-F[i], R[j], T[i][j]) for i != p (condensed:
+//       slot q starts from 0) and T[p][j] = R[j] (Section III Step 3, Section
+//       IV Step 4), streamed with 256-bit accesses; the objective row is
+//       updated first, one warp per strip, each emitting that strip's argmin
+//       partial of the new objective row (the next P1's input).
 // Between phases every block of the grid passes a device-wide barrier whose
 // wait is bounded in time (the paper's per-iteration synchronisation,
 // Section IV Iterate/Finalization).

@@ -2,10 +2,12 @@
 // tableau of doubles or floats (V):
 //   k_reset_state         zero the per-solve state word block
 //   k_validate            inputs finite, b >= 0 (create)
-//   k_build<V>            Initialization Step: Table I tableau, slack basis
+//   k_build<V>            Initialization Step: Table I tableau (full or
+//                         condensed), slack basis
 //   k_pivot_persistent    Steps 1-3 iterated inside one cooperative launch
 //   k_ml_*                the same phases, one launch each (fallback, profiling)
 //   k_extract_*<V>        read-out of x, y, objective from the tableau
+//   k_expand_cond<V> etc. Table I rebuilt from a condensed tableau
 #pragma once
 
 #include "tsx_device.cuh"
