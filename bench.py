@@ -682,7 +682,7 @@ def run_many(args, rank, world, local):
         "config": {"workload": f"lp_solve_many over the {len(prs)} LPs of {args.many_count} drawn from the "
                                "serving distribution (m, n log-uniform in [32, 4096]) whose condensed tableau "
                                "exceeds one SM's shared memory; one call per step, inputs resident in HBM",
-                   "team_blocks": args.many_team or 32, "pivots_per_step": pivots,
+                   "team_blocks": args.many_team or 16, "pivots_per_step": pivots,
                    "l2": "tableaux of the step total well above L2"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)", "traffic": None,

@@ -173,8 +173,11 @@ lp_status lp_solve(lp_t h, const lp_options *opt);
 
 /* Solve `count` LPs at once, each from its slack basis (the method of
  * lp_solve: Section III, Initialization Step and Steps 1-3).  One cooperative
- * launch divides the GPU into teams of opt->blocks thread blocks (default 32);
- * each team takes the next LP from the list, largest first, and iterates on
+ * launch divides the GPU into teams of opt->blocks thread blocks (default 16)
+ * -- and, when some LPs carry more than a team's share of the list's work, up
+ * to half of the GPU into wide teams of four times as many blocks that take
+ * those LPs first; each team takes the next LP from its list, largest first
+ * (then helps with the other list), and iterates on
  * its condensed tableau: block b of the team owns a contiguous range of rows,
  * runs the ratio test on them and updates them, with the scaled pivot row and
  * its rows' multipliers in shared memory; two team barriers per pivot.  Meant
@@ -361,7 +364,7 @@ typedef struct {
                                      cooperative launches of the persistent
                                      path largely run one at a time)            */
     int team_blocks;              /* >= 0 (default 0: lp_solve_many's default
-                                     team of 32 blocks): the requests too
+                                     team of 16 blocks): the requests too
                                      large for the micro-batches are solved in
                                      waves by lp_solve_many with teams of this
                                      many blocks -- every such request waiting

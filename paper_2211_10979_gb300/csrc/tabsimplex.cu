@@ -985,6 +985,10 @@ static lp_status finish_team_lp(lp_handle* h, const lp_options& o, cudaStream_t 
     return LP_OPTIMAL;
 }
 
+#ifndef TSX_TEAM_WIDE
+#define TSX_TEAM_WIDE 1   // wide teams for the LPs heavier than a team's share
+#endif
+
 template <typename V>
 static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, cudaStream_t s,
                               lp_status* status) {
@@ -998,7 +1002,7 @@ static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, 
     size_t smem_limit = 0;
     const cudaError_t se = team_allow_smem<NT, V>(smem_limit);
     CUDA_TRY(se, LP_ERR_CUDA);
-    int C = o.blocks > 0 ? std::min(o.blocks, kTeamMax) : 32;
+    int C = o.blocks > 0 ? std::min(o.blocks, kTeamMax) : 16;
 
     // work buffers and state of every LP (condensed layout)
     for (lp_handle* h : hs) {
@@ -1058,12 +1062,46 @@ static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, 
             return LP_ERR_CUDA;
         }
         C = std::min(C, cap);
-        const int nteams = std::max(1, std::min(njobs, cap / C));
-        // scratch: jobs | order | counter | team states
+        // Teams: the LPs heavier than a team's fair share of the whole list
+        // would outlast it on C blocks, so up to half the grid forms wide teams
+        // (4 C blocks) that take those first; the narrow teams take the rest.
+        // Each team drains its own list, then helps with the other.
+        double total = 0.0;
+        for (double w : work) total += w;
+        const int narrow_all = std::max(1, cap / C);
+        const double share = total / narrow_all;
+        std::vector<int> heavy, light;
+        for (int k : order) (work[k] > share ? heavy : light).push_back(k);
+        const int CB = std::min(std::min(4 * C, kTeamMax), std::max(C, cap / 2));
+        int nwide = heavy.empty() || CB <= C || !TSX_TEAM_WIDE ? 0
+                                                               : std::min((int)heavy.size(), std::max(1, (cap / 2) / CB));
+        if (nwide == 0) {   // one list
+            light.insert(light.begin(), heavy.begin(), heavy.end());
+            heavy.clear();
+        }
+        std::vector<int> first, size, list, team_of;
+        for (int t = 0; t < nwide; ++t) {
+            first.push_back((int)team_of.size());
+            size.push_back(CB);
+            list.push_back(1);
+            team_of.insert(team_of.end(), CB, (int)first.size() - 1);
+        }
+        const int nnarrow = std::max(1, std::min((cap - nwide * CB) / C, njobs));
+        for (int t = 0; t < nnarrow && (int)team_of.size() + C <= cap; ++t) {
+            first.push_back((int)team_of.size());
+            size.push_back(C);
+            list.push_back(0);
+            team_of.insert(team_of.end(), C, (int)first.size() - 1);
+        }
+        const int nteams = (int)first.size();
+        const int grid = (int)team_of.size();
+        // scratch: jobs | lists | counters | team tables | team states
         Carve cv;
         const size_t o_jobs = cv.take(sizeof(TeamJob<V>) * (size_t)njobs);
-        const size_t o_order = cv.take(sizeof(int) * (size_t)njobs);
-        const size_t o_next = cv.take(sizeof(unsigned));
+        const size_t o_l0 = cv.take(sizeof(int) * (size_t)std::max<size_t>(1, light.size()));
+        const size_t o_l1 = cv.take(sizeof(int) * (size_t)std::max<size_t>(1, heavy.size()));
+        const size_t o_tab = cv.take(sizeof(int) * (size_t)(grid + 3 * nteams));
+        const size_t o_next = cv.take(2 * sizeof(unsigned));
         const size_t o_teams = cv.take(sizeof(TeamState) * (size_t)nteams);
         const size_t bytes = align_up(cv.off, 256);
         lp_handle* h0 = hs[who[0]];
@@ -1077,13 +1115,22 @@ static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, 
             return LP_ERR_NOMEM;
         }
         char* base = (char*)scratch;
+        std::vector<int> tab(team_of);
+        tab.insert(tab.end(), first.begin(), first.end());
+        tab.insert(tab.end(), size.begin(), size.end());
+        tab.insert(tab.end(), list.begin(), list.end());
         TeamParams<V> P{};
         P.jobs = (const TeamJob<V>*)(base + o_jobs);
-        P.order = (const int*)(base + o_order);
-        P.njobs = njobs;
+        P.order[0] = (const int*)(base + o_l0);
+        P.order[1] = (const int*)(base + o_l1);
+        P.count[0] = (int)light.size();
+        P.count[1] = (int)heavy.size();
         P.next = (unsigned*)(base + o_next);
         P.teams = (TeamState*)(base + o_teams);
-        P.team = C;
+        P.team_of = (const int*)(base + o_tab);
+        P.first = P.team_of + grid;
+        P.size = P.first + nteams;
+        P.list = P.size + nteams;
         P.eps_d = fp32 ? o.eps_d_fp32 : o.eps_d;
         P.eps_p = fp32 ? o.eps_p_fp32 : o.eps_p;
         P.max_iters = o.max_iters;
@@ -1092,15 +1139,19 @@ static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, 
         P.timeout_ns = std::max(0LL, o.barrier_timeout_ns);
         cudaError_t e = cudaMemcpyAsync(base + o_jobs, jobs.data(), sizeof(TeamJob<V>) * (size_t)njobs,
                                         cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && !light.empty())
+            e = cudaMemcpyAsync(base + o_l0, light.data(), sizeof(int) * light.size(), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess && !heavy.empty())
+            e = cudaMemcpyAsync(base + o_l1, heavy.data(), sizeof(int) * heavy.size(), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(base + o_order, order.data(), sizeof(int) * (size_t)njobs, cudaMemcpyHostToDevice, s);
+            e = cudaMemcpyAsync(base + o_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(base + o_next, 0, bytes - o_next, s);
         cudaEvent_t e0 = hs[who[0]]->ev[1], e1 = hs[who[0]]->ev[2];
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
         int ldm = ld_max;
         void* args[] = {(void*)&P, (void*)&ldm};
         if (e == cudaSuccess)
-            e = cudaLaunchCooperativeKernel((const void*)k_team_solve<NT, V>, nteams * C, NT, args, smem, s);
+            e = cudaLaunchCooperativeKernel((const void*)k_team_solve<NT, V>, grid, NT, args, smem, s);
         if (e == cudaSuccess) e = cudaEventRecord(e1, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e == cudaSuccess) cudaEventElapsedTime(&ms, e0, e1);

@@ -20,7 +20,7 @@
 
 namespace tsx {
 
-constexpr int kTeamMax = 64;   // blocks per team, upper bound
+constexpr int kTeamMax = 160;  // blocks per team, upper bound
 
 template <typename V>
 struct TeamJob {
@@ -47,11 +47,14 @@ struct __align__(256) TeamState {   // one per team
 template <typename V>
 struct TeamParams {
     const TeamJob<V>* jobs;
-    const int* order;          // job indices, largest first
-    int njobs;
-    unsigned* next;            // list position counter
+    const int* order[2];       // job indices of the two lists, largest first
+    int count[2];              // their lengths
+    unsigned* next;            // list position counters (2)
     TeamState* teams;
-    int team;                  // blocks per team
+    const int* team_of;        // grid: the team of each block
+    const int* first;          // teams: first block, size, own list (0 or 1)
+    const int* size;
+    const int* list;
     double eps_d, eps_p;
     long long max_iters;       // < 0: 50 (m + n)
     int k_cyc, rule;
@@ -196,11 +199,10 @@ __device__ void team_update(const TeamJob<V>& J, const V* R, const V* Floc, int 
     }
 }
 
-// Solves one LP with the team; false if a team barrier failed.
+// Solves one LP with the team of C blocks; false if a team barrier failed.
 template <typename V>
-__device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, TeamState* ts, int bt,
+__device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, TeamState* ts, int bt, unsigned C,
                                V* R, V* Floc, BlockScratch& s, int& sok) {
-    const unsigned C = (unsigned)P.team;
     const int m = J.m, n = J.n, ld = J.ld;
     int r0, r1;
     team_rows(m, (int)C, bt, r0, r1);
@@ -282,26 +284,37 @@ __device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, Team
     return true;
 }
 
-// One cooperative launch: team t = blocks [t C, (t+1) C) takes list entries
-// until none is left.  Dynamic shared memory per block: R (ld_max entries)
-// then the multipliers (rows per block, max over the list).
+// One cooperative launch: team t (blocks first[t] .. first[t] + size[t] - 1)
+// takes entries of its own list, then of the other one, until both are empty.
+// Dynamic shared memory per block: R (ld_max entries) then the multipliers
+// (rows per block, max over the lists for the smallest team).
 template <int NT, typename V>
 __global__ void __launch_bounds__(NT, 512 / NT) k_team_solve(TeamParams<V> P, int ld_max) {
     extern __shared__ __align__(32) unsigned char team_smem[];
     __shared__ BlockScratch s;
     __shared__ int sok;
-    const int C = P.team;
-    const int t = blockIdx.x / C, bt = blockIdx.x - t * C;
+    const int t = P.team_of[blockIdx.x];
+    const int bt = blockIdx.x - P.first[t];
+    const unsigned C = (unsigned)P.size[t];
     TeamState* ts = P.teams + t;
     V* R = reinterpret_cast<V*>(team_smem);
     V* Floc = R + ld_max;
+    int li = P.list[t];
     for (;;) {
-        if (bt == 0 && threadIdx.x == 0) ts->job = (int)atomicAdd(P.next, 1u);
-        if (!team_barrier(ts, (unsigned)C, P.timeout_ns, sok)) return;
+        if (bt == 0 && threadIdx.x == 0) {
+            int k = -1;
+            for (int pass = 0; pass < 2 && k < 0; ++pass) {
+                const int l = pass == 0 ? li : 1 - li;
+                const int pos = (int)atomicAdd(P.next + l, 1u);
+                if (pos < P.count[l]) k = P.order[l][pos];
+            }
+            ts->job = k;
+        }
+        if (!team_barrier(ts, C, P.timeout_ns, sok)) return;
         const int k = *(volatile const int*)&ts->job;
-        if (k >= P.njobs) return;
-        const TeamJob<V> J = P.jobs[P.order[k]];
-        if (!team_solve_one(P, J, ts, bt, R, Floc, s, sok)) return;
+        if (k < 0) return;
+        const TeamJob<V> J = P.jobs[k];
+        if (!team_solve_one(P, J, ts, bt, C, R, Floc, s, sok)) return;
     }
 }
 
