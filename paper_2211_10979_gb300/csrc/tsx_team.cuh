@@ -275,6 +275,10 @@ __device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, Team
             __syncthreads();
         }
     }
+    // commit: the status is written only once every block of the team has
+    // finished its part (a block that gave up at a barrier never gets here,
+    // and the LP stays unfinished)
+    if (!team_barrier(ts, C, P.timeout_ns, sok)) return false;
     if (bt == 0 && threadIdx.x == 0) {
         J.st->status = status;
         J.st->iters = it;

@@ -136,3 +136,40 @@ def test_invalid_calls(tsx):
         assert rc == tsx.LP_OPTIMAL and st == []
     finally:
         p.close()
+
+
+def test_team_barrier_timeout_reports_and_context_survives(tsx):
+    # a zero wait budget: the teams give up at their first barrier (no hang);
+    # every LP reports LP_ERR_TIMEOUT, and the next call on the same context is exact
+    problems = [lpgen.dense_lp(m, n, 40 + k) for k, (m, n) in enumerate([(300, 200), (120, 500), (64, 900)])]
+    refs = [oracle.solve(*p) for p in problems]
+    prs = [tsx.Problem(*p) for p in problems]
+    try:
+        st = tsx.solve_many(prs, tsx.options(blocks=4, barrier_timeout_ns=0))
+        assert all(s in (tsx.LP_ERR_TIMEOUT, tsx.LP_OPTIMAL) for s in st)
+        assert tsx.LP_ERR_TIMEOUT in st
+        st = tsx.solve_many(prs, tsx.options(blocks=4))
+        assert st == [r.status for r in refs]
+        for pr, ref in zip(prs, refs):
+            _check(tsx, pr, ref)
+    finally:
+        for pr in prs:
+            pr.close()
+
+
+def test_device_inputs(tsx):
+    import torch
+    shapes = [(250, 300), (400, 180)]
+    problems = [lpgen.dense_lp(m, n, 60 + k) for k, (m, n) in enumerate(shapes)]
+    refs = [oracle.solve(*p) for p in problems]
+    s = torch.cuda.current_stream().cuda_stream
+    dev = [tuple(torch.from_numpy(v).cuda() for v in p) for p in problems]
+    prs = [tsx.Problem(A, b, c, device=True, stream=s) for A, b, c in dev]
+    try:
+        st = tsx.solve_many(prs, tsx.options(stream=s))
+        assert st == [r.status for r in refs]
+        for pr, ref in zip(prs, refs):
+            _check(tsx, pr, ref)
+    finally:
+        for pr in prs:
+            pr.close()
