@@ -42,7 +42,7 @@ constexpr int kRunning = 100;      // status while the iteration is in progress
 #define TSX_ROWS_IN_FLIGHT 8
 #endif
 #ifndef TSX_GRAB
-#define TSX_GRAB 2
+#define TSX_GRAB 0     // work slots per grab of the update; 0: 1 for double, 2 for float
 #endif
 #ifndef TSX_ALTERNATE
 #define TSX_ALTERNATE 1   // alternate the update's sweep direction per pivot
@@ -560,16 +560,20 @@ __device__ void phase_update_bulk(const Params<V>& P, int p, int zq, unsigned na
     long long gcur = -1;
     V f[kRowsInFlight];
     int i0 = 1, nrows = 0;
-    // Slots are handed out TSX_GRAB at a time from a counter (a static split
+    // Slots are handed out `grab` at a time from a counter (a static split
     // leaves the slowest blocks ~15% behind the mean); the next grab is
     // requested before the current one is processed.
+    // (measured: single slots shorten the tail of the double update; the
+    // float update has twice the slots per pivot, and pairs keep the counter's
+    // atomics off its critical path)
+    constexpr unsigned grab = TSX_GRAB > 0 ? (unsigned)TSX_GRAB : (sizeof(V) == 8 ? 1u : 2u);
     unsigned next = 0;
-    if (lane == 0) next = atomicAdd(&P.st->next_slot, (unsigned)TSX_GRAB);
+    if (lane == 0) next = atomicAdd(&P.st->next_slot, grab);
     next = __shfl_sync(0xffffffffu, next, 0);
     while ((long long)next < total) {
         const long long u0 = next;
-        const long long u1 = min(total, u0 + TSX_GRAB);
-        if (lane == 0) next = atomicAdd(&P.st->next_slot, (unsigned)TSX_GRAB);
+        const long long u1 = min(total, u0 + (long long)grab);
+        if (lane == 0) next = atomicAdd(&P.st->next_slot, grab);
         next = __shfl_sync(0xffffffffu, next, 0);
         for (long long u = u0; u < u1; ++u) {
             // odd pivots sweep backwards: they start on the rows the previous
