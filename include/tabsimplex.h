@@ -258,7 +258,7 @@ const char *lp_version(void);
 typedef struct lp_batch *lp_batch_t;
 
 typedef struct {
-    int threads;                  /* threads per LP (32, 64, 128, 256);
+    int threads;                  /* threads per LP (32, 64, 128, 256, 512);
                                      0 = autotune: each shared-memory size class
                                      times the candidates once per device; the
                                      choice is reused by later solves and

@@ -27,7 +27,7 @@ constexpr int kGlobal = kClasses - 1;
 // The shared-memory classes hold LPs of which 8, 3, 2 and 1 fit one SM at a
 // time (bounds from the device's shared memory per SM, see class_bounds).
 constexpr int kPerSm[kClasses - 1] = {8, 3, 2, 1};
-constexpr int kCandidates[4] = {32, 64, 128, 256};
+constexpr int kCandidates[5] = {32, 64, 128, 256, 512};
 
 struct DBlock {
     void* ptr = nullptr;
@@ -164,7 +164,7 @@ size_t tsx::batch_smem_limit() {
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
     size_t stat = 0;
     for (size_t v : {kernel_static_smem<32>(), kernel_static_smem<64>(), kernel_static_smem<128>(),
-                     kernel_static_smem<256>()})
+                     kernel_static_smem<256>(), kernel_static_smem<512>()})
         stat = std::max(stat, v);
     return optin > 0 ? (size_t)optin - stat - 256 : 0;
 }
@@ -179,7 +179,7 @@ static void class_bounds(size_t* bound) {
     cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device);
     size_t stat = 0;
     for (size_t v : {kernel_static_smem<32>(), kernel_static_smem<64>(), kernel_static_smem<128>(),
-                     kernel_static_smem<256>()})
+                     kernel_static_smem<256>(), kernel_static_smem<512>()})
         stat = std::max(stat, v);
     const size_t limit = tsx::batch_smem_limit();
     for (int q = 0; q < kClasses - 1; ++q) {
@@ -412,7 +412,8 @@ static cudaError_t launch_class_nt(lp_batch* h, const BatchParams& P, int q, int
         case 32: return launch_class<32>(h, P, q, s);
         case 64: return launch_class<64>(h, P, q, s);
         case 128: return launch_class<128>(h, P, q, s);
-        default: return launch_class<256>(h, P, q, s);
+        case 256: return launch_class<256>(h, P, q, s);
+        default: return launch_class<512>(h, P, q, s);
     }
 }
 
@@ -460,8 +461,9 @@ lp_status lp_batch_solve(lp_batch_t h, const lp_batch_options* opt) {
     else
         lp_batch_options_init(&o);
     if (!(o.eps_d >= 0.0) || !(o.eps_p >= 0.0) || o.rule < 0 || o.rule > 1 ||
-        (o.threads != 0 && o.threads != 32 && o.threads != 64 && o.threads != 128 && o.threads != 256)) {
-        set_error("lp_batch_solve: invalid options (threads must be 0, 32, 64, 128 or 256)");
+        (o.threads != 0 && o.threads != 32 && o.threads != 64 && o.threads != 128 && o.threads != 256 &&
+         o.threads != 512)) {
+        set_error("lp_batch_solve: invalid options (threads must be 0, 32, 64, 128, 256 or 512)");
         return LP_ERR_INVALID;
     }
     TSX_CUDA_TRY(cudaSetDevice(h->device), LP_ERR_CUDA);
@@ -561,7 +563,8 @@ lp_status lp_batch_solve(lp_batch_t h, const lp_batch_options* opt) {
                     case 32: e = allow_max_smem<32>(); break;
                     case 64: e = allow_max_smem<64>(); break;
                     case 128: e = allow_max_smem<128>(); break;
-                    default: e = allow_max_smem<256>(); break;
+                    case 256: e = allow_max_smem<256>(); break;
+                    default: e = allow_max_smem<512>(); break;
                 }
                 TSX_CUDA_TRY(e, LP_ERR_CUDA);
             }

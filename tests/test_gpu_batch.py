@@ -42,7 +42,7 @@ MIXED = [(1, 1), (1, 9), (9, 1), (3, 4), (16, 16), (17, 31), (31, 17), (40, 64),
          (100, 128), (128, 100), (128, 128), (77, 91), (5, 120), (120, 5)]
 
 
-@pytest.mark.parametrize("threads", [0, 32, 64, 128, 256])
+@pytest.mark.parametrize("threads", [0, 32, 64, 128, 256, 512])
 def test_mixed_batch_equals_oracle(tsx, threads):
     problems = _problems(MIXED, 500)
     refs = [oracle.solve(*p) for p in problems]
@@ -80,7 +80,7 @@ def test_config_4096_small_lps(tsx):
     _check(sol, problems, refs)
     st = sol.stats
     assert sum(st["lps_per_class"]) == 4096
-    assert all(t in (0, 32, 64, 128, 256) for t in st["threads"])
+    assert all(t in (0, 32, 64, 128, 256, 512) for t in st["threads"])
 
 
 def test_special_lps_inside_a_batch(tsx):
@@ -118,7 +118,7 @@ def test_device_inputs(tsx):
         _check(bt.results(), problems, refs)
 
 
-@pytest.mark.parametrize("threads", [0, 64, 256])
+@pytest.mark.parametrize("threads", [0, 64, 256, 512])
 def test_lps_beyond_shared_memory_use_global_workspace(tsx, threads):
     # condensed tableaux above the shared-memory limit (m = n = 200: 323 KB)
     # are solved from a global workspace slice, mixed with shared-memory ones
