@@ -11,10 +11,13 @@
  * until no negative coefficient is left (optimal) or column q has no positive
  * entry (unbounded) (Section III, Iterate/Finalization Step).
  *
- * Tableau layout on the device (one per handle): (m + 1) rows x W = n + m + 1
- * logical columns, row-major with a padded leading dimension.  Row 0 is the
- * objective row [-c, 0 | z]; rows 1..m are [A, I_m | b].  The constant z column
- * of Table I is not stored (it never changes).  Variable indices are 0-based:
+ * Tableau (Table I): (m + 1) rows x W = n + m + 1 logical columns.  Row 0 is
+ * the objective row [-c, 0 | z]; rows 1..m are [A, I_m | b].  The constant z
+ * column of Table I is not stored (it never changes).  On the device a handle
+ * keeps it row-major with a padded leading dimension, either condensed (the
+ * default: the n nonbasic columns and the right-hand side, the basic columns
+ * being exact unit vectors; see lp_options.layout) or whole.  Every value,
+ * pivot and result is the same in both.  Variable indices are 0-based:
  * 0..n-1 are x_1..x_n, n..n+m-1 are the slacks of constraints 1..m.
  *
  * Threads: calls on one handle are not thread-safe; distinct handles are
@@ -73,16 +76,19 @@ typedef struct {
     long long barrier_timeout_ns; /* limit of one device-wide barrier wait
                                      (default 2e9 ns); on expiry the solve ends
                                      with LP_ERR_TIMEOUT                        */
-    int path;                     /* LP_PATH_AUTO: persistent cooperative kernel
-                                     when it can be launched, else one launch
-                                     per phase                                  */
+    int path;                     /* LP_PATH_AUTO (default): the persistent
+                                     cooperative kernel when it can be
+                                     launched, else one launch per phase;
+                                     LP_PATH_PERSISTENT or LP_PATH_MULTILAUNCH
+                                     force one of them                          */
     int skip_zero_columns;        /* full layout only: 1 (default): Step 3
                                      leaves untouched every 32-byte group of
                                      columns whose scaled pivot row entries are
                                      all zero (their update is the identity);
                                      0: update every column                     */
     int threads;                  /* threads per block, 0 = default (256)       */
-    int blocks;                   /* grid size cap, 0 = all co-resident blocks  */
+    int blocks;                   /* grid size cap, 0 = all co-resident blocks
+                                     (lp_solve_many: blocks per team)           */
     long long log_capacity;       /* pivots whose (q, p) pair is recorded;
                                      0 = none                                   */
     void *stream;                 /* cudaStream_t to run on; NULL = the
@@ -125,8 +131,10 @@ typedef struct {
                                      kernels have to move: 64 bytes per row and
                                      32-byte column group Step 3 updates (read +
                                      write), plus Steps 1-2 and the staging     */
-    int path;                     /* LP_PATH_PERSISTENT or LP_PATH_MULTILAUNCH  */
-    int grid;                     /* blocks of the pivot kernels                */
+    int path;                     /* LP_PATH_PERSISTENT, LP_PATH_MULTILAUNCH or
+                                     LP_PATH_TEAM (lp_solve_many)               */
+    int grid;                     /* blocks of the pivot kernels (team: the
+                                     narrow team size)                          */
     int block;                    /* threads per block                          */
     int ld;                       /* leading dimension of the tableau (elems)   */
     double phase_ms[6];           /* persistent path, as seen by block 0: work
@@ -253,7 +261,9 @@ const char *lp_version(void);
  * n + 2, odd), e.g. m = n = 128 needs 134 KB.  In shared memory when it fits
  * the device's opt-in block limit (227 KB on GB300), otherwise in a global
  * workspace slice allocated with the batch (one block per LP either way, so
- * large LPs are better served by lp_solve).
+ * larger LPs are better served by lp_solve_many or lp_solve).  The LPs are
+ * grouped in size classes (of which 8, 3, 2 and 1 fit one SM's shared memory
+ * side by side), one persistent launch per class.
  * ------------------------------------------------------------------------ */
 typedef struct lp_batch *lp_batch_t;
 
