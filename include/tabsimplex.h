@@ -390,6 +390,9 @@ typedef struct {
     long long batches, batched_lps;
     long long peak_bytes;         /* largest admitted total                     */
     long long waves, wave_lps;    /* lp_solve_many waves and the LPs in them   */
+    double wave_ms;               /* wall time of the waves (create, solve,
+                                     recovery, read-out), summed                */
+    double wave_kernel_ms;        /* device time of their team launches, summed */
 } lps_stats;
 
 void lps_options_init(lps_options *opt);

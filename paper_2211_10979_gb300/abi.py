@@ -154,6 +154,8 @@ class lps_stats(ctypes.Structure):
         ("peak_bytes", ctypes.c_longlong),
         ("waves", ctypes.c_longlong),
         ("wave_lps", ctypes.c_longlong),
+        ("wave_ms", ctypes.c_double),
+        ("wave_kernel_ms", ctypes.c_double),
     ]
 
     def as_dict(self):

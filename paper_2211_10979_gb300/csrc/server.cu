@@ -127,7 +127,9 @@ struct lp_server {
     long long next_id = 0;
     long long used = 0, peak = 0;
     long long submitted = 0, completed = 0, batches = 0, batched_lps = 0, waves = 0, wave_lps = 0;
-    bool wave_running = false;           // one lp_solve_many wave at a time
+    double wave_ms = 0.0, wave_kernel_ms = 0.0;
+    bool wave_running = false;           // a wave's team launch holds the GPU
+    bool wave_pending = false;           // a wave is being prepared or waits to launch
     int team_blocks = 0;                 // blocks per team of a wave, < 0: no waves
     std::string last_error;              // message of the latest failed solve
     bool stopping = false;
@@ -258,9 +260,14 @@ static void solve_batch(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs
     sv->batched_lps += count;
 }
 
+// Blocks a wave's team launch leaves free (8 SMs' worth on GB300) for the
+// previous wave's recovery and the micro-batches.
+constexpr int kWaveReserve = 16;
+
 // Solves the requests too large for the micro-batches together: one
 // lp_solve_many call (a team of blocks per LP) on the calling worker thread.
 static void solve_wave(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs, cudaStream_t s) {
+    const auto t0 = Clock::now();
     std::vector<lp_t> hs;
     std::vector<Request*> who;
     for (auto& rp : rs) {
@@ -281,8 +288,37 @@ static void solve_wave(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs,
     o.blocks = sv->team_blocks;
     o.stream = (void*)s;
     std::vector<lp_status> st(hs.size(), LP_ERR_STATE);
-    const lp_status rc = hs.empty() ? LP_OPTIMAL : lp_solve_many(hs.data(), (int)hs.size(), &o, st.data());
+    // the team launch runs when the previous wave's launch has completed; the
+    // previous wave's recovery and read-out overlap this launch on the blocks
+    // it leaves free, and the next wave is prepared meanwhile
+    {
+        std::unique_lock<std::mutex> lk(sv->mu);
+        sv->cv_work.wait(lk, [&] { return !sv->wave_running; });
+        sv->wave_running = true;
+        sv->wave_pending = false;
+    }
+    sv->cv_work.notify_all();
+    bool released = false;
+    auto release = [&] {
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->wave_running = false;
+        }
+        released = true;
+        sv->cv_work.notify_all();
+    };
+    const lp_status rc = hs.empty() ? LP_OPTIMAL
+                                    : solve_many_hooked(hs.data(), (int)hs.size(), &o, st.data(), kWaveReserve, release);
+    if (!released) release();
     if (rc != LP_OPTIMAL) note_error(sv, "wave");
+    double kernel_ms = 0.0;
+    for (size_t k = 0; k < hs.size() && rc == LP_OPTIMAL; ++k) {
+        lp_stats ls;
+        if (lp_get_stats(hs[k], &ls) == LP_OPTIMAL && ls.path == LP_PATH_TEAM) {
+            kernel_ms = ls.pivot_ms;
+            break;
+        }
+    }
     for (size_t k = 0; k < hs.size(); ++k) {
         Request& r = *who[k];
         r.status = rc != LP_OPTIMAL ? rc : st[k];
@@ -297,6 +333,8 @@ static void solve_wave(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs,
     std::lock_guard<std::mutex> lk(sv->mu);
     ++sv->waves;
     sv->wave_lps += (long long)rs.size();
+    sv->wave_ms += 1e3 * std::chrono::duration<double>(Clock::now() - t0).count();
+    sv->wave_kernel_ms += kernel_ms;
 }
 
 static void worker_main(lp_server* sv) {
@@ -311,13 +349,14 @@ static void worker_main(lp_server* sv) {
             // arrival order: the head is admitted first once the budget allows;
             // small requests queued behind it join its micro-batch, and with
             // waves, every large request waiting joins the wave.  While a wave
-            // runs, large requests wait for the next one and the other workers
-            // serve the small ones.
+            // is being prepared or waits for the previous one's launch, large
+            // requests wait for the wave after it and the other workers serve
+            // the small ones.
             const bool waves = sv->team_blocks >= 0;
             auto pick = [&]() -> std::deque<std::shared_ptr<Request>>::iterator {
                 for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
                     const bool large = !((*it)->small && sv->opt.batch_small);
-                    if (waves && large && sv->wave_running) continue;
+                    if (waves && large && sv->wave_pending) continue;
                     if (sv->used + (long long)(*it)->bytes > sv->opt.budget_bytes) return sv->queue.end();
                     return it;
                 }
@@ -339,7 +378,7 @@ static void worker_main(lp_server* sv) {
             take.push_back(head);
             const bool head_large = !(head->small && sv->opt.batch_small);
             if (waves && head_large) {
-                sv->wave_running = true;
+                sv->wave_pending = true;
                 for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)take.size() < sv->opt.batch_max;) {
                     const bool large = !((*it)->small && sv->opt.batch_small);
                     if (large && sv->used + (long long)(*it)->bytes <= sv->opt.budget_bytes) {
@@ -374,7 +413,6 @@ static void worker_main(lp_server* sv) {
             solve_batch(sv, take, s);
         {
             std::lock_guard<std::mutex> lk(sv->mu);
-            if (large && sv->team_blocks >= 0) sv->wave_running = false;
             const auto now = Clock::now();
             for (auto& r : take) {
                 r->t_done = now;
@@ -565,6 +603,8 @@ lp_status lps_get_stats(lps_t sv, lps_stats* st) {
     st->batched_lps = sv->batched_lps;
     st->waves = sv->waves;
     st->wave_lps = sv->wave_lps;
+    st->wave_ms = sv->wave_ms;
+    st->wave_kernel_ms = sv->wave_kernel_ms;
     st->peak_bytes = sv->peak;
     return LP_OPTIMAL;
 }

@@ -636,7 +636,8 @@ static lp_status recover_factor(lp_handle* h, const lp_options& o, cudaStream_t 
             return LP_ERR_INVALID;
         }
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rec_gauss_jordan<256>, 256, bits);
-        const int g = std::max(1, std::min(nsm * std::max(per, 1), grid_for((long long)(2 * kk * kk), 256, 1 << 20)));
+        int g = std::max(1, std::min(nsm * std::max(per, 1), grid_for((long long)(2 * kk * kk), 256, 1 << 20)));
+        if (o.blocks > 0) g = std::min(g, o.blocks);   // blocks per LP
         int* sg = r.singular;
         int* pv = r.pivrow;
         double* Mx = r.M;
@@ -991,7 +992,7 @@ static lp_status finish_team_lp(lp_handle* h, const lp_options& o, cudaStream_t 
 
 template <typename V>
 static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, cudaStream_t s,
-                              lp_status* status) {
+                              lp_status* status, int reserve_blocks, const std::function<void()>& after_kernel) {
     constexpr int NT = 256;
     constexpr int elem = (int)sizeof(V);
     const bool fp32 = elem == 4;
@@ -1056,7 +1057,7 @@ static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, 
         const size_t smem = (size_t)(ld_max + ((rows_max + 31) / 32) * 32) * elem;
         int per = 0;
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_team_solve<NT, V>, NT, smem);
-        const int cap = per * nsm;
+        const int cap = per * nsm - std::max(0, reserve_blocks);
         if (cap <= 0) {
             set_error("lp_solve_many: the team kernel cannot be resident (%zu bytes of shared memory)", smem);
             return LP_ERR_CUDA;
@@ -1164,6 +1165,10 @@ static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, 
             return LP_ERR_CUDA;
         }
     }
+    if (after_kernel) after_kernel();
+    // the recovery's cooperative refactorisation fits in the reserved blocks
+    lp_options of = o;
+    of.blocks = std::max(0, reserve_blocks);
     // per-LP bookkeeping (as solve_nt) and the FP64 recovery of FP32 results,
     // spread over host threads with a stream each (the recovery is a chain of
     // small kernels and host decisions per LP)
@@ -1171,7 +1176,7 @@ static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, 
     std::vector<lp_status> fail(nthreads, LP_OPTIMAL);
     auto finish = [&](int tid, cudaStream_t ss) -> lp_status {
         for (int t = tid; t < njobs; t += nthreads) {
-            const lp_status st = finish_team_lp<V>(hs[who[t]], o, ss, ms, C, NT, status + who[t]);
+            const lp_status st = finish_team_lp<V>(hs[who[t]], of, ss, ms, C, NT, status + who[t]);
             if (st == LP_ERR_CUDA) return st;
         }
         return LP_OPTIMAL;
@@ -1206,6 +1211,11 @@ static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, 
 }
 
 lp_status lp_solve_many(lp_t* handles, int count, const lp_options* opt, lp_status* status) {
+    return tsx::solve_many_hooked(handles, count, opt, status, 0, std::function<void()>());
+}
+
+lp_status tsx::solve_many_hooked(lp_t* handles, int count, const lp_options* opt, lp_status* status,
+                                 int reserve_blocks, const std::function<void()>& after_kernel) {
     if (!handles || !status || count < 0) {
         set_error("lp_solve_many: NULL argument or count < 0");
         return LP_ERR_INVALID;
@@ -1243,8 +1253,8 @@ lp_status lp_solve_many(lp_t* handles, int count, const lp_options* opt, lp_stat
     }
     CUDA_TRY(cudaSetDevice(hs[0]->device), LP_ERR_CUDA);
     cudaStream_t s = o.stream ? (cudaStream_t)o.stream : hs[0]->stream;
-    return o.precision == LP_PREC_FP32 ? solve_many_t<float>(hs, o, s, status)
-                                       : solve_many_t<double>(hs, o, s, status);
+    return o.precision == LP_PREC_FP32 ? solve_many_t<float>(hs, o, s, status, reserve_blocks, after_kernel)
+                                       : solve_many_t<double>(hs, o, s, status, reserve_blocks, after_kernel);
 }
 
 lp_status lp_get_solution(lp_t h, double* x, double* y, double* obj, int* basis, long long* iters) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <functional>
 
 #include "tabsimplex.h"
 
@@ -24,6 +25,13 @@ void use_default_allocator(bool on);
 // and whether an m x n LP fits in them.
 size_t batch_smem_limit();
 bool batch_fits(int m, int n, size_t limit);
+
+// lp_solve_many for callers that overlap its parts: the team launch leaves
+// `reserve_blocks` of the co-resident blocks free for other work, and
+// `after_kernel` (may be empty) runs on the calling thread as soon as the
+// launch has completed, before the per-LP bookkeeping and FP64 recovery.
+lp_status solve_many_hooked(lp_t* handles, int count, const lp_options* opt, lp_status* status,
+                            int reserve_blocks, const std::function<void()>& after_kernel);
 
 }  // namespace tsx
 
