@@ -341,9 +341,11 @@ void lp_batch_destroy(lp_batch_t h);
  * request waiting at that moment, up to batch_max -- and solved as one
  * micro-batch (FP64, results equal lp_solve's); the others are solved in
  * waves by lp_solve_many with the given precision (default FP32 tableau + FP64
- * recovery): every such request waiting when a wave starts joins it, and the
- * requests arriving meanwhile form the next wave (or, with team_blocks < 0,
- * one per worker by lp_create / lp_solve on a share of the GPU's blocks).  Requests arriving while others are on the GPU are
+ * recovery): every such request waiting when a wave is formed joins it; the
+ * next wave is formed while the current one's team launch runs, and the
+ * finished wave's recovery and read-out overlap the next launch (or, with
+ * team_blocks < 0, one per worker by lp_create / lp_solve on a share of the
+ * GPU's blocks).  Requests arriving while others are on the GPU are
  * admitted as workers and memory free up, and their work overlaps on the
  * device.  The paper has no serving layer; every solve inside is the method of
  * lp_solve.
