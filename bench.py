@@ -786,6 +786,8 @@ def run_serve(args, rank, world, local):
                    "batches": st["batches"], "batched_lps": st["batched_lps"],
                    "waves": st["waves"], "wave_lps": st["wave_lps"], "team_blocks": args.serve_team or "default",
                    "wave_ms": round(st["wave_ms"], 1), "wave_kernel_ms": round(st["wave_kernel_ms"], 1),
+                   "wave_create_ms": round(st["wave_create_ms"], 1), "wave_wait_ms": round(st["wave_wait_ms"], 1),
+                   "wave_launch_ms": round(st["wave_launch_ms"], 1),
                    "peak_admitted_bytes": st["peak_bytes"]},
         "latency": {"p50_ms": s_srv["p50_ms"], "p99_ms": s_srv["p99_ms"], "mean_ms": s_srv["mean_ms"],
                     "max_ms": s_srv["max_ms"], "from": "scheduled arrival to result on the host"},

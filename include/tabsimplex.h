@@ -25,7 +25,9 @@
  * lp_last_error() on the calling thread.
  *
  * Device memory comes from the allocator installed with lp_set_allocator()
- * (default: cudaMallocAsync/cudaFreeAsync on the handle's stream).
+ * (default: stream-ordered allocation on the handle's stream from a memory
+ * pool per device that the library creates and that keeps freed memory for
+ * reuse until the process exits).
  */
 #ifndef TABSIMPLEX_H
 #define TABSIMPLEX_H
@@ -242,7 +244,7 @@ const char *lp_last_error(void);
 /* Install the device allocator used by later lp_create* calls (process-wide).
  * alloc(bytes, stream, ctx) returns a device pointer or NULL; free(ptr, bytes,
  * stream, ctx) releases it.  Passing NULL for both restores the default
- * (cudaMallocAsync / cudaFreeAsync).  Returns 0, or -1 if only one is NULL. */
+ * (the library's stream-ordered pool).  Returns 0, or -1 if only one is NULL. */
 typedef void *(*lp_alloc_fn)(size_t bytes, void *stream, void *ctx);
 typedef void (*lp_free_fn)(void *ptr, size_t bytes, void *stream, void *ctx);
 int lp_set_allocator(lp_alloc_fn alloc_fn, lp_free_fn free_fn, void *ctx);
@@ -395,6 +397,9 @@ typedef struct {
     double wave_ms;               /* wall time of the waves (create, solve,
                                      recovery, read-out), summed                */
     double wave_kernel_ms;        /* device time of their team launches, summed */
+    double wave_create_ms;        /* of wave_ms: handle creation               */
+    double wave_wait_ms;          /* of wave_ms: waiting for the launch token  */
+    double wave_launch_ms;        /* of wave_ms: set-up and team launch (host) */
 } lps_stats;
 
 void lps_options_init(lps_options *opt);

@@ -156,6 +156,9 @@ class lps_stats(ctypes.Structure):
         ("wave_lps", ctypes.c_longlong),
         ("wave_ms", ctypes.c_double),
         ("wave_kernel_ms", ctypes.c_double),
+        ("wave_create_ms", ctypes.c_double),
+        ("wave_wait_ms", ctypes.c_double),
+        ("wave_launch_ms", ctypes.c_double),
     ]
 
     def as_dict(self):

@@ -89,7 +89,7 @@ static void* bdev_alloc(lp_batch* h, size_t bytes) {
     if (bytes == 0) bytes = 256;
     if (h->alloc) return h->alloc(bytes, (void*)h->stream, h->actx);
     void* p = nullptr;
-    if (cudaMallocAsync(&p, bytes, h->stream) != cudaSuccess) {
+    if (pool_alloc(&p, bytes, h->stream) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }

@@ -127,7 +127,7 @@ struct lp_server {
     long long next_id = 0;
     long long used = 0, peak = 0;
     long long submitted = 0, completed = 0, batches = 0, batched_lps = 0, waves = 0, wave_lps = 0;
-    double wave_ms = 0.0, wave_kernel_ms = 0.0;
+    double wave_ms = 0.0, wave_kernel_ms = 0.0, wave_create_ms = 0.0, wave_wait_ms = 0.0, wave_launch_ms = 0.0;
     bool wave_running = false;           // a wave's team launch holds the GPU
     bool wave_pending = false;           // a wave is being prepared or waits to launch
     int team_blocks = 0;                 // blocks per team of a wave, < 0: no waves
@@ -201,7 +201,7 @@ static void solve_batch(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs
     auto fail = [&](int st) {
         for (auto& r : rs) r->status = st;
     };
-    if (cudaMallocAsync((void**)&pack, bytes, s) != cudaSuccess) {
+    if (pool_alloc((void**)&pack, bytes, s) != cudaSuccess) {
         cudaGetLastError();
         fail(LP_ERR_NOMEM);
         return;
@@ -272,7 +272,8 @@ static void solve_wave(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs,
     std::vector<Request*> who;
     for (auto& rp : rs) {
         Request& r = *rp;
-        lp_t h = r.on_device ? lp_create_device(r.m, r.n, r.dA, r.db, r.dc, (void*)s)
+        // device inputs: the team kernel checks them while building the tableau
+        lp_t h = r.on_device ? create_device_unchecked(r.m, r.n, r.dA, r.db, r.dc, s)
                              : lp_create(r.m, r.n, r.hA.data(), r.hb.data(), r.hc.data());
         if (!h) {
             note_error(sv, "create");
@@ -291,6 +292,7 @@ static void solve_wave(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs,
     // the team launch runs when the previous wave's launch has completed; the
     // previous wave's recovery and read-out overlap this launch on the blocks
     // it leaves free, and the next wave is prepared meanwhile
+    const auto t1 = Clock::now();
     {
         std::unique_lock<std::mutex> lk(sv->mu);
         sv->cv_work.wait(lk, [&] { return !sv->wave_running; });
@@ -298,8 +300,11 @@ static void solve_wave(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs,
         sv->wave_pending = false;
     }
     sv->cv_work.notify_all();
+    const auto t2 = Clock::now();
+    auto t3 = t2;
     bool released = false;
     auto release = [&] {
+        t3 = Clock::now();
         {
             std::lock_guard<std::mutex> lk(sv->mu);
             sv->wave_running = false;
@@ -311,6 +316,9 @@ static void solve_wave(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs,
                                     : solve_many_hooked(hs.data(), (int)hs.size(), &o, st.data(), kWaveReserve, release);
     if (!released) release();
     if (rc != LP_OPTIMAL) note_error(sv, "wave");
+    auto ms_of = [](Clock::time_point a, Clock::time_point b) {
+        return 1e3 * std::chrono::duration<double>(b - a).count();
+    };
     double kernel_ms = 0.0;
     for (size_t k = 0; k < hs.size() && rc == LP_OPTIMAL; ++k) {
         lp_stats ls;
@@ -333,8 +341,11 @@ static void solve_wave(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs,
     std::lock_guard<std::mutex> lk(sv->mu);
     ++sv->waves;
     sv->wave_lps += (long long)rs.size();
-    sv->wave_ms += 1e3 * std::chrono::duration<double>(Clock::now() - t0).count();
+    sv->wave_ms += ms_of(t0, Clock::now());
     sv->wave_kernel_ms += kernel_ms;
+    sv->wave_create_ms += ms_of(t0, t1);
+    sv->wave_wait_ms += ms_of(t1, t2);
+    sv->wave_launch_ms += ms_of(t2, t3);
 }
 
 static void worker_main(lp_server* sv) {
@@ -605,6 +616,9 @@ lp_status lps_get_stats(lps_t sv, lps_stats* st) {
     st->wave_lps = sv->wave_lps;
     st->wave_ms = sv->wave_ms;
     st->wave_kernel_ms = sv->wave_kernel_ms;
+    st->wave_create_ms = sv->wave_create_ms;
+    st->wave_wait_ms = sv->wave_wait_ms;
+    st->wave_launch_ms = sv->wave_launch_ms;
     st->peak_bytes = sv->peak;
     return LP_OPTIMAL;
 }

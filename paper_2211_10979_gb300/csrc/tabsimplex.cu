@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -138,6 +139,7 @@ struct lp_handle {
     long long log_cap = 0;
     int max_grid = 0;                // rpart capacity
     bool solved = false;
+    bool checked = true;             // inputs validated (false: create_device_unchecked)
     int last_status = LP_ERR_STATE;
     bool sol_ready = false;          // sol already holds the read-out (float path)
     std::vector<int> final_basis;    // float path: basic variables after the recovery
@@ -145,11 +147,39 @@ struct lp_handle {
     lp_stats stats{};
 };
 
+cudaError_t tsx::pool_alloc(void** ptr, size_t bytes, cudaStream_t stream) {
+    constexpr int kMaxPoolDevices = 64;
+    static std::mutex mu;
+    static cudaMemPool_t pools[kMaxPoolDevices] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxPoolDevices) return cudaMallocAsync(ptr, bytes, stream);
+    cudaMemPool_t pool = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!pools[dev]) {
+            cudaMemPoolProps props{};
+            props.allocType = cudaMemAllocationTypePinned;
+            props.location.type = cudaMemLocationTypeDevice;
+            props.location.id = dev;
+            cudaMemPool_t p = nullptr;
+            e = cudaMemPoolCreate(&p, &props);
+            if (e != cudaSuccess) return e;
+            unsigned long long keep = ~0ull;   // keep freed memory in the pool
+            cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+            pools[dev] = p;
+        }
+        pool = pools[dev];
+    }
+    return cudaMallocFromPoolAsync(ptr, bytes, pool, stream);
+}
+
 static void* dev_alloc(lp_handle* h, size_t bytes) {
     if (bytes == 0) bytes = 256;
     if (h->alloc) return h->alloc(bytes, (void*)h->stream, h->alloc_ctx);
     void* p = nullptr;
-    if (cudaMallocAsync(&p, bytes, h->stream) != cudaSuccess) {
+    if (pool_alloc(&p, bytes, h->stream) != cudaSuccess) {
         cudaGetLastError();
         return nullptr;
     }
@@ -238,6 +268,17 @@ static void destroy_impl(lp_handle* h) {
 
 void lp_destroy(lp_t h) { destroy_impl(h); }
 
+// The handle's timing events, created on first use (a server creates and
+// destroys many handles; most never time anything).
+static bool ensure_events(lp_handle* h) {
+    for (auto& e : h->ev)
+        if (!e && cudaEventCreate(&e) != cudaSuccess) {
+            set_error("cudaEventCreate failed: %s", cudaGetErrorString(cudaGetLastError()));
+            return false;
+        }
+    return true;
+}
+
 // Common part of the two create calls: sizes, stream, events, state block.
 static lp_handle* create_common(int m, int n, cudaStream_t stream, bool own_stream) {
     if (m <= 0 || n <= 0) {
@@ -264,8 +305,7 @@ static lp_handle* create_common(int m, int n, cudaStream_t stream, bool own_stre
     } else {
         h->stream = stream;
     }
-    bool ok = cudaEventCreateWithFlags(&h->ready, cudaEventDisableTiming) == cudaSuccess;
-    for (auto& e : h->ev) ok = ok && cudaEventCreate(&e) == cudaSuccess;
+    const bool ok = cudaEventCreateWithFlags(&h->ready, cudaEventDisableTiming) == cudaSuccess;
     if (!ok) {
         set_error("lp_create: cudaEventCreate failed");
         destroy_impl(h);
@@ -341,6 +381,22 @@ lp_t lp_create(int m, int n, const double* A, const double* b, const double* c) 
         destroy_impl(h);
         return nullptr;
     }
+    cudaEventRecord(h->ready, h->stream);
+    return h;
+}
+
+lp_t tsx::create_device_unchecked(int m, int n, const double* dA, const double* db, const double* dc,
+                                 cudaStream_t stream) {
+    if (!dA || !db || !dc) {
+        set_error("lp_create_device: NULL input pointer");
+        return nullptr;
+    }
+    lp_handle* h = create_common(m, n, stream, false);
+    if (!h) return nullptr;
+    h->A = dA;
+    h->b = db;
+    h->c = dc;
+    h->checked = false;
     cudaEventRecord(h->ready, h->stream);
     return h;
 }
@@ -799,6 +855,15 @@ static lp_status recover(lp_handle* h, const lp_options& o, cudaStream_t s, long
 
 template <int NT>
 static lp_status solve_nt(lp_handle* h, const lp_options& o, cudaStream_t s) {
+    if (!ensure_events(h)) return LP_ERR_CUDA;
+    if (!h->checked) {   // created without the input check: run it now
+        if (!validate_inputs(h)) {
+            h->solved = true;
+            h->last_status = LP_ERR_INVALID;
+            return LP_ERR_INVALID;
+        }
+        h->checked = true;
+    }
     const int m = h->m;
     // pivot log buffers
     if (o.log_capacity > 0 && o.log_capacity != h->log_cap) {
@@ -949,6 +1014,15 @@ static lp_status finish_team_lp(lp_handle* h, const lp_options& o, cudaStream_t 
     CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
     lp_status st = ds.status == kRunning ? LP_ERR_TIMEOUT : (lp_status)ds.status;
     if (st == LP_ERR_TIMEOUT) set_error("lp_solve_many: a team barrier wait exceeded its limit");
+    if (st == LP_ERR_INVALID) {
+        set_error("lp_solve_many: inputs must be finite with b >= 0");
+        h->solved = true;
+        h->last_status = st;
+        *status = st;
+        cudaEventRecord(h->ready, s);
+        return LP_OPTIMAL;
+    }
+    h->checked = true;
     const int m = h->m, ld = h->work.ld, E = 32 / elem;
     const double nsec = (double)(ld / E);
     h->stats.iters = ds.iters;
@@ -966,15 +1040,14 @@ static lp_status finish_team_lp(lp_handle* h, const lp_options& o, cudaStream_t 
     h->stats.kernel_launches = 1;
     h->iters = ds.iters;
     if (fp32 && (st == LP_OPTIMAL || st == LP_ITER_LIMIT || st == LP_UNBOUNDED)) {
-        cudaEventRecord(h->ev[3], s);
+        // timed on the host: recovery ends with a synchronisation anyway, and
+        // creating events on many threads at once contends in the driver
+        const auto t0 = std::chrono::steady_clock::now();
         long long rl = 0;
         lp_status rs = recover(h, o, s, rl);
         if (rs == LP_ERR_CUDA) return rs;
-        cudaEventRecord(h->ev[2], s);
         CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
-        float ms_rec = 0.f;
-        cudaEventElapsedTime(&ms_rec, h->ev[3], h->ev[2]);
-        h->stats.recover_ms = ms_rec;
+        h->stats.recover_ms = 1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         h->stats.kernel_launches += rl;
         st = rs;
         h->sol_ready = rs == LP_OPTIMAL;
@@ -1014,8 +1087,11 @@ static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, 
         h->sol_ready = false;
         h->final_basis.clear();
         k_reset_state<<<1, 32, 0, h->stream>>>(h->st);
-        CUDA_TRY(cudaEventRecord(h->ev[0], h->stream), LP_ERR_CUDA);
-        CUDA_TRY(cudaStreamWaitEvent(s, h->ev[0], 0), LP_ERR_CUDA);
+        if (h->stream != s) {   // the launch on s waits for the handle's stream
+            if (!ensure_events(h)) return LP_ERR_CUDA;
+            CUDA_TRY(cudaEventRecord(h->ev[0], h->stream), LP_ERR_CUDA);
+            CUDA_TRY(cudaStreamWaitEvent(s, h->ev[0], 0), LP_ERR_CUDA);
+        }
     }
     // the list, largest first; LPs whose pivot row and multipliers exceed the
     // shared memory of one block are solved one at a time afterwards
@@ -1107,7 +1183,7 @@ static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, 
         const size_t bytes = align_up(cv.off, 256);
         lp_handle* h0 = hs[who[0]];
         void* scratch = h0->alloc ? h0->alloc(bytes, (void*)s, h0->alloc_ctx) : nullptr;
-        if (!h0->alloc && cudaMallocAsync(&scratch, bytes, s) != cudaSuccess) {
+        if (!h0->alloc && pool_alloc(&scratch, bytes, s) != cudaSuccess) {
             cudaGetLastError();
             scratch = nullptr;
         }
@@ -1147,7 +1223,8 @@ static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, 
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(base + o_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(base + o_next, 0, bytes - o_next, s);
-        cudaEvent_t e0 = hs[who[0]]->ev[1], e1 = hs[who[0]]->ev[2];
+        if (!ensure_events(h0)) return LP_ERR_CUDA;
+        cudaEvent_t e0 = h0->ev[1], e1 = h0->ev[2];
         if (e == cudaSuccess) e = cudaEventRecord(e0, s);
         int ldm = ld_max;
         void* args[] = {(void*)&P, (void*)&ldm};

@@ -51,7 +51,7 @@ constexpr int kRowsInFlight = TSX_ROWS_IN_FLIGHT;   // rows loaded before the fi
 constexpr int kMaxWarps = 32;      // warps per block upper bound (1024 threads)
 
 // status codes (same values as lp_status in tabsimplex.h)
-constexpr int kOptimal = 0, kUnbounded = 1, kIterLimit = 2, kNumeric = 3, kTimeout = -4;
+constexpr int kOptimal = 0, kUnbounded = 1, kIterLimit = 2, kNumeric = 3, kInvalid = -1, kTimeout = -4;
 
 struct __align__(16) ArgPart {   // best entering candidate of a column range
     double v;         // most negative objective-row entry (< -eps_d), +inf if none

@@ -21,10 +21,23 @@ void current_allocator(lp_alloc_fn* alloc_fn, lp_free_fn* free_fn, void** ctx);
 // cudaMallocAsync / cudaFreeAsync (the request server's worker threads).
 void use_default_allocator(bool on);
 
+// Stream-ordered device allocation of the default allocator: a memory pool
+// per device, owned by the library, that keeps freed memory for reuse (the
+// device's default pool hands freed memory back at every synchronisation, and
+// mapping it again made each new handle of a busy server cost ~0.5 ms).
+cudaError_t pool_alloc(void** ptr, size_t bytes, cudaStream_t stream);
+
 // Shared-memory bytes the batched solver has for one LP on the current device,
 // and whether an m x n LP fits in them.
 size_t batch_smem_limit();
 bool batch_fits(int m, int n, size_t limit);
+
+// lp_create_device without the input check: the check (finite data, b >= 0)
+// runs during the first solve instead -- in the team kernel's build for
+// lp_solve_many, or as lp_create's own check before any other solve.  For
+// callers that create many handles at once (the server's waves).
+lp_t create_device_unchecked(int m, int n, const double* dA, const double* db, const double* dc,
+                             cudaStream_t stream);
 
 // lp_solve_many for callers that overlap its parts: the team launch leaves
 // `reserve_blocks` of the co-resident blocks free for other work, and

@@ -40,6 +40,7 @@ struct __align__(256) TeamState {   // one per team
     unsigned bar_gen;
     int job;
     int fail;                  // set when a team barrier wait ran out
+    int bad;                   // the current LP's inputs are not finite or b < 0
     ArgPart ent;               // next entering candidate (block 0)
     RatPart rat[kTeamMax];     // ratio-test partial of each block
 };
@@ -105,13 +106,16 @@ __device__ __forceinline__ void team_rows(int m, int C, int bt, int& r0, int& r1
 }
 
 // Condensed Table I rows [r0, r1) (slack basis): row 0 = [-c | 0], row i =
-// [A_i | b_i], padding zero; the LP's basis words of those rows; var[] by block 0.
+// [A_i | b_i], padding zero; the LP's basis words of those rows; var[] by block
+// 0.  Inputs that are not finite, or b_i < 0, mark the LP bad in the team state
+// (the input check of lp_create, done while the data pass by).
 template <typename V>
-__device__ void team_build(const TeamJob<V>& J, int r0, int r1, int bt) {
+__device__ void team_build(const TeamJob<V>& J, int r0, int r1, int bt, TeamState* ts) {
     constexpr int E = Lanes<V>::E;
     const int n = J.n, ld = J.ld;
     const long long per_row = ld / E;
     const long long total = (long long)(r1 - r0) * per_row;
+    int bad = 0;
     for (long long g = threadIdx.x; g < total; g += blockDim.x) {
         const int i = r0 + (int)(g / per_row);
         const int j0 = (int)(g - (long long)(i - r0) * per_row) * E;
@@ -126,11 +130,14 @@ __device__ void team_build(const TeamJob<V>& J, int r0, int r1, int bt) {
                 v = J.A[(size_t)(i - 1) * (size_t)n + j];
             } else if (j == n) {
                 v = J.b[i - 1];
+                bad |= !(v >= 0.0);
             }
+            bad |= !isfinite(v);
             out.v[e] = (V)v;
         }
         st_sector(J.T + (size_t)i * (size_t)ld + j0, out);
     }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ts->bad, 1);
     for (int i = max(r0, 1) + threadIdx.x; i < r1; i += blockDim.x) J.basis[i - 1] = n + i - 1;
     if (bt == 0)
         for (int j = threadIdx.x; j < n; j += blockDim.x) J.var[j] = j;
@@ -206,16 +213,16 @@ __device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, Team
     const int m = J.m, n = J.n, ld = J.ld;
     int r0, r1;
     team_rows(m, (int)C, bt, r0, r1);
-    team_build(J, r0, r1, bt);
+    team_build(J, r0, r1, bt, ts);
     __syncthreads();
     if (bt == 0) team_row0(J, (const V*)nullptr, V(0), -1, P, ts, s);   // Step 1 of the first pivot
     if (!team_barrier(ts, C, P.timeout_ns, sok)) return false;
     const long long cap = P.max_iters < 0 ? 50LL * ((long long)m + n) : P.max_iters;
     long long it = 0;
     int bland = P.rule == 1, degen = 0;
-    int status = kRunning;
+    int status = ld_relaxed(&ts->bad) ? kInvalid : kRunning;
     const int lo = max(r0, 1);
-    for (;;) {
+    while (status == kRunning) {
         const ArgPart e = load_arg(&ts->ent);                // Step 1
         const int q = bland ? e.fslot : e.slot;
         const int qv = bland ? e.fkey : e.key;
@@ -306,6 +313,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_team_solve(TeamParams<V> P, in
     int li = P.list[t];
     for (;;) {
         if (bt == 0 && threadIdx.x == 0) {
+            ts->bad = 0;   // read after the next barrier; set during the build
             int k = -1;
             for (int pass = 0; pass < 2 && k < 0; ++pass) {
                 const int l = pass == 0 ? li : 1 - li;

@@ -162,3 +162,29 @@ def test_plain_mode_and_stats(tsx):
     with pytest.raises(ValueError, match="budget"):
         with tsx.Server(budget_bytes=1 << 20) as sv:
             sv.submit(*lpgen.dense_lp(500, 500, 1))
+
+
+def test_invalid_device_request_in_a_wave(tsx):
+    # device inputs are checked in the team kernel's build: a request with
+    # b_i < 0 ends LP_ERR_INVALID, the others of its wave are unaffected
+    import torch
+    shapes = [(400, 300), (350, 420), (500, 250)]
+    reqs = []
+    s = torch.cuda.current_stream().cuda_stream
+    for k, (m, n) in enumerate(shapes):
+        A, b, c = lpgen.dense_lp(m, n, 910 + k)
+        if k == 1:
+            b = b.copy()
+            b[7] = -1.0
+        reqs.append((m, n, *(torch.from_numpy(v).cuda() for v in (A.ravel(), b, c))))
+    torch.cuda.synchronize()
+    with tsx.Server(workers=2) as sv:
+        tickets = [sv.submit_device(m, n, dA, db, dc) for (m, n, dA, db, dc) in reqs]
+        codes = [sv.wait(t, 120.0) for t in tickets]
+        res = [sv.result(t) for t in tickets]
+    assert codes[1] == tsx.LP_ERR_INVALID
+    for k in (0, 2):
+        A, b, c = lpgen.dense_lp(*shapes[k], 910 + k)
+        ref = oracle.solve(A, b, c)
+        assert codes[k] == tsx.LP_OPTIMAL
+        assert abs(res[k].obj - ref.obj) <= 1e-9 * abs(ref.obj)
