@@ -279,8 +279,10 @@ typedef struct {
     double eps_d, eps_p;          /* as lp_options (defaults 1e-9)              */
     long long max_iters;          /* per LP; < 0: 50 (m + n)                    */
     int k_cyc;                    /* as lp_options (default 50)                 */
-    int use_graph;                /* 1 (default): the launches of a solve are
-                                     captured once in a CUDA graph and replayed */
+    int use_graph;                /* 1 (default): from the batch's second solve
+                                     on, the launches of a solve are captured
+                                     once in a CUDA graph and replayed (the
+                                     first solve launches them directly)        */
     int keep_tableaux;            /* 1: keep every LP's final tableau for
                                      lp_batch_get_tableau (default 0)           */
     void *stream;                 /* cudaStream_t; NULL = the batch's stream    */
