@@ -49,6 +49,10 @@ def parse_args(argv=None):
     ap.add_argument("--seeds", type=int, default=3, help="distinct LPs cycled through the steps")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--skip-zero", type=int, default=1)
+    ap.add_argument("--max-iters", type=int, default=-1,
+                    help="pivot cap per solve (a truncated solve; default: to the end)")
+    ap.add_argument("--device-gen", action="store_true",
+                    help="draw the inputs on the device (no e2e, no oracle sample)")
     ap.add_argument("--layout", choices=["condensed", "full"], default="condensed",
                     help="device tableau: nonbasic columns + RHS (condensed) or the whole Table I (full)")
     ap.add_argument("--path", type=int, default=0)
@@ -258,14 +262,29 @@ def run_gpu(args, rank, world, local):
 
     m, n = args.m, args.n
     seeds = rank_seeds(rank, args.seeds)
-    host = {s: lpgen.dense_lp(m, n, s) for s in seeds}
-    resident = {s: tuple(torch.from_numpy(v).to(dev) for v in host[s]) for s in seeds}
     stream = torch.cuda.current_stream(dev)
     sptr = stream.cuda_stream
+    if args.device_gen:   # inputs drawn on the device (sizes whose A does not fit host memory)
+        host = {}
+        resident = {}
+        for s in seeds:
+            dA = torch.empty(m * n, dtype=torch.float64, device=dev)
+            db = torch.empty(m, dtype=torch.float64, device=dev)
+            dc = torch.empty(n, dtype=torch.float64, device=dev)
+            tsx.lp_generate_dense(m, n, s, dA, db, dc, sptr)
+            resident[s] = (dA, db, dc)
+        torch.cuda.synchronize(dev)
+        args.e2e_steps = 0
+        args.no_cpu_baseline = True
+    else:
+        host = {s: lpgen.dense_lp(m, n, s) for s in seeds}
+        resident = {s: tuple(torch.from_numpy(v).to(dev) for v in host[s]) for s in seeds}
     prec = tsx.LP_PREC_FP32 if args.precision == "fp32" else tsx.LP_PREC_FP64
     layout = tsx.LP_LAYOUT_FULL if args.layout == "full" else tsx.LP_LAYOUT_CONDENSED
     opts = tsx.options(stream=sptr, skip_zero_columns=args.skip_zero, path=args.path,
-                       threads=args.threads, blocks=args.blocks, precision=prec, layout=layout)
+                       threads=args.threads, blocks=args.blocks, precision=prec, layout=layout,
+                       max_iters=args.max_iters)
+    done_ok = (tsx.LP_OPTIMAL, tsx.LP_ITER_LIMIT) if args.max_iters >= 0 else (tsx.LP_OPTIMAL,)
 
     x = np.empty(n)
     y = np.empty(m)
@@ -277,7 +296,7 @@ def run_gpu(args, rank, world, local):
         h = tsx.lp_create_device(m, n, dA, db, dc, sptr)
         try:
             st = tsx.lp_solve(h, opts)
-            if st != tsx.LP_OPTIMAL:
+            if st not in done_ok:
                 raise RuntimeError(f"solve ended {tsx.STATUS_NAMES.get(st, st)}: {tsx.lp_last_error()}")
             tsx.lp_get_solution(h, x, y, obj, basis)
             return tsx.lp_get_stats(h).as_dict()
@@ -308,7 +327,7 @@ def run_gpu(args, rank, world, local):
 
     # e2e: the public API from pinned host buffers, copies inside the timed region
     pinned = {}
-    for s in seeds:
+    for s in seeds if args.e2e_steps > 0 else ():
         A, b, c = host[s]
         pinned[s] = tuple(torch.from_numpy(v).pin_memory() for v in (A, b, c))
     xo = torch.empty(n, dtype=torch.float64).pin_memory()
@@ -343,7 +362,7 @@ def run_gpu(args, rank, world, local):
     # FP32 path: objective error of each timed seed against the FP64 path
     # (untimed), which equals the FP64 oracle step by step
     prec_info = None
-    if args.precision == "fp32":
+    if args.precision == "fp32" and args.max_iters < 0:
         errs = []
         for sd in seeds:
             dA, db, dc = resident[sd]
@@ -399,8 +418,9 @@ def run_gpu(args, rank, world, local):
             "dtype": "f64" if args.precision == "fp64" else "f32 tableau + f64 recovery",
             "data": "synthetic",
             "config": {
-                "workload": f"dense LP m={m} n={n} {args.precision.upper()}, full solve per step (seeded "
-                            "A~U[1,10), b~U[100,1000), c~U[1,10); slack basis; Dantzig)",
+                "workload": f"dense LP m={m} n={n} {args.precision.upper()}, "
+                            + ("full solve" if args.max_iters < 0 else f"first {args.max_iters} pivots")
+                            + " per step (seeded A~U[1,10), b~U[100,1000), c~U[1,10); slack basis; Dantzig)",
                 "m": m, "n": n, "seeds_per_rank": len(seeds),
                 "pivots_per_step": pivots / args.steps,
                 "l2": f"inputs larger than L2 (tableau {(m + 1) * stats[0]['ld'] * elem / 1e9:.2f} GB)",
