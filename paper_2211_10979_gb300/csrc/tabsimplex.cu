@@ -458,17 +458,36 @@ static lp_status ensure_work(lp_handle* h, int elem, int cond) {
     return LP_OPTIMAL;
 }
 
+// Dynamic shared memory of the persistent kernel: the update's bulk-copy
+// rings (one per warp).
+template <int NT>
+static size_t persistent_smem() {
+    return tma_smem_bytes(NT);
+}
+
+template <int NT, typename V>
+static void allow_persistent_smem() {
+    static std::once_flag once;
+    std::call_once(once, [] {
+        cudaFuncSetAttribute((const void*)k_pivot_persistent<NT, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)persistent_smem<NT>());
+    });
+}
+
 template <int NT, typename V>
 static cudaError_t launch_persistent(const Params<V>& P, int grid, cudaStream_t s) {
+    allow_persistent_smem<NT, V>();
     void* args[] = {(void*)&P};
-    return cudaLaunchCooperativeKernel((const void*)k_pivot_persistent<NT, V>, grid, NT, args, 0, s);
+    return cudaLaunchCooperativeKernel((const void*)k_pivot_persistent<NT, V>, grid, NT, args, persistent_smem<NT>(),
+                                       s);
 }
 
 template <int NT, typename V>
 static int max_coresident(int device) {
+    allow_persistent_smem<NT, V>();
     int nsm = 0, per = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pivot_persistent<NT, V>, NT, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_pivot_persistent<NT, V>, NT, persistent_smem<NT>());
     return nsm * per;
 }
 
@@ -526,18 +545,33 @@ static Params<V> make_params(int m, int n, int ld, V* T, V* F, V* R, int* act, A
     return P;
 }
 
-// Grid of the pivot kernels: enough warps for the update slots, at most the
-// co-resident blocks.
+// Grid of the pivot kernels: enough warps for the update slots (`rows` rows
+// each), at most `resident` blocks.
 template <int NT, typename V>
-static int pivot_grid(int device, int m, int ld, int max_grid, int user_blocks, int& coresident) {
+static int update_grid(int m, int ld, int rows, int resident, int max_grid, int user_blocks) {
     constexpr int E = Lanes<V>::E;
-    const long long slots = (long long)((ld / E + 31) / 32) * (((long long)m + kRowsInFlight - 1) / kRowsInFlight);
+    const long long slots = (long long)((ld / E + 31) / 32) * (((long long)m + rows - 1) / rows);
     const long long want = (slots + NT / 32 - 1) / (NT / 32);
-    coresident = max_coresident<NT, V>(device);
-    int grid = (int)std::min<long long>(std::max<long long>(1, want), std::max(1, coresident));
+    int grid = (int)std::min<long long>(std::max<long long>(1, want), std::max(1, resident));
     grid = std::min(grid, max_grid);
     if (user_blocks > 0) grid = std::min(grid, user_blocks);
     return grid;
+}
+
+template <int NT, typename V>
+static int pivot_grid(int device, int m, int ld, int max_grid, int user_blocks, int& coresident) {
+    coresident = max_coresident<NT, V>(device);
+    return update_grid<NT, V>(m, ld, persistent_rows(NT), coresident, max_grid, user_blocks);
+}
+
+// Grid of the one-launch-per-phase path: its update kernel keeps two blocks
+// of 256 threads on an SM.
+template <int NT, typename V>
+static int multilaunch_grid(int device, int m, int ld, int max_grid, int user_blocks) {
+    int nsm = 0, per = 0;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ml_update<NT, V>, NT, 0);
+    return update_grid<NT, V>(m, ld, kRowsInFlight, std::max(1, nsm * per), max_grid, user_blocks);
 }
 
 // Runs the pivot phase (build + Steps 1-3) on the handle's tableau of V.
@@ -592,14 +626,16 @@ static lp_status pivot_phase(lp_handle* h, const lp_options& o, cudaStream_t s, 
             ++launches;
         }
     }
+    int grid_run = grid;
     if (path == LP_PATH_MULTILAUNCH) {
-        if (run_multilaunch<NT, V>(P, grid, s, launches) == LP_ERR_CUDA) return LP_ERR_CUDA;
+        grid_run = multilaunch_grid<NT, V>(h->device, m, ld, h->max_grid, o.blocks);
+        if (run_multilaunch<NT, V>(P, grid_run, s, launches) == LP_ERR_CUDA) return LP_ERR_CUDA;
     }
     cudaEventRecord(h->ev[2], s);
     CUDA_TRY(cudaMemcpyAsync(&hs, h->st, sizeof(DevState), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);
     CUDA_TRY(cudaStreamSynchronize(s), LP_ERR_CUDA);
     path_used = path;
-    grid_used = grid;
+    grid_used = grid_run;
     if (hs.status == kRunning) {
         set_error("lp_solve: kernel ended without a status");
         return LP_ERR_CUDA;
@@ -1564,7 +1600,8 @@ static lp_status noalloc_nt(int m, int n, const double* dA, const double* db, co
     }
     if (path == LP_PATH_MULTILAUNCH) {
         long long launches = 0;
-        if (run_multilaunch<NT, double>(P, grid, s, launches) == LP_ERR_CUDA) return LP_ERR_CUDA;
+        const int g = multilaunch_grid<NT, double>(device, m, ld, kNoAllocMaxGrid, o.blocks);
+        if (run_multilaunch<NT, double>(P, g, s, launches) == LP_ERR_CUDA) return LP_ERR_CUDA;
     }
     DevState hs{};
     CUDA_TRY(cudaMemcpyAsync(&hs, st, sizeof(DevState), cudaMemcpyDeviceToHost, s), LP_ERR_CUDA);

@@ -39,15 +39,39 @@ namespace tsx {
 
 constexpr int kRunning = 100;      // status while the iteration is in progress
 #ifndef TSX_ROWS_IN_FLIGHT
-#define TSX_ROWS_IN_FLIGHT 8
+#define TSX_ROWS_IN_FLIGHT 0   // rows in flight of the persistent update; 0: by registers per thread
 #endif
 #ifndef TSX_GRAB
 #define TSX_GRAB 0     // work slots per grab of the update; 0: 1 for double, 2 for float
 #endif
+#ifndef TSX_SM_THREADS
+#define TSX_SM_THREADS 256   // threads per SM the persistent kernel is compiled for
+#endif
+#ifndef TSX_TMA
+#define TSX_TMA 0          // 1: condensed persistent update through bulk copies into shared memory
+#endif
+#ifndef TSX_TMA_ROWS
+#define TSX_TMA_ROWS 4
+#endif
+#ifndef TSX_TMA_STAGES
+#define TSX_TMA_STAGES 3
+#endif
+#ifndef TSX_TMA_BATCH
+#define TSX_TMA_BATCH 4    // rows of a stage read from shared memory before their FMAs
+#endif
 #ifndef TSX_ALTERNATE
 #define TSX_ALTERNATE 1   // alternate the update's sweep direction per pivot
 #endif
-constexpr int kRowsInFlight = TSX_ROWS_IN_FLIGHT;   // rows loaded before the first store
+constexpr int kRowsInFlight = 8;   // rows a warp loads before its first store (128 registers a thread)
+
+// Threads per SM of the persistent kernel with blocks of nt threads, and the
+// rows a warp of its update keeps in flight: 16 where a thread may hold 255
+// registers (at most 256 threads per SM), else 8.  A warp's bytes in flight
+// set the update's bandwidth once the tableau outgrows L2.
+__host__ __device__ constexpr int persistent_sm_threads(int nt) { return nt > TSX_SM_THREADS ? nt : TSX_SM_THREADS; }
+__host__ __device__ constexpr int persistent_rows(int nt) {
+    return TSX_ROWS_IN_FLIGHT > 0 ? TSX_ROWS_IN_FLIGHT : persistent_sm_threads(nt) <= 256 ? 16 : kRowsInFlight;
+}
 constexpr int kMaxWarps = 32;      // warps per block upper bound (1024 threads)
 
 // status codes (same values as lp_status in tabsimplex.h)
@@ -518,7 +542,7 @@ __device__ void phase_update_edge_rows(const Params<V>& P, int p, int q) {
 
 // One work slot: rows i0 .. i0+nrows-1 (row p excluded) of the column group
 // listed at entry c*32 + lane.
-template <typename V>
+template <typename V, int R>
 __device__ __forceinline__ void update_slot(const Params<V>& P, int p, int zq, unsigned nact, long long c, int i0,
                                             int nrows, const V* f) {
     constexpr int E = Lanes<V>::E;
@@ -528,14 +552,14 @@ __device__ __forceinline__ void update_slot(const Params<V>& P, int p, int zq, u
     const Sector<V> r = ld_sector_cg(P.R + col);
     // condensed: the entry of slot q starts from the leaving variable's unit column (0 off row p)
     const int eq = zq - (int)col;
-    Sector<V> v[kRowsInFlight];
+    Sector<V> v[R];
 #pragma unroll
-    for (int k = 0; k < kRowsInFlight; ++k) {
+    for (int k = 0; k < R; ++k) {
         const int i = i0 + k;
         if (k < nrows && i != p) v[k] = ld_sector_stream(P.T + (size_t)i * (size_t)P.ld + col);
     }
 #pragma unroll
-    for (int k = 0; k < kRowsInFlight; ++k) {
+    for (int k = 0; k < R; ++k) {
         const int i = i0 + k;
         if (k < nrows && i != p) {
 #pragma unroll
@@ -551,14 +575,14 @@ __device__ __forceinline__ void update_slot(const Params<V>& P, int p, int zq, u
 // consecutive slots stream along the same rows and the rows' F values stay in
 // registers while the row group is unchanged.  One listed column group per
 // lane.  Groups not listed have R == 0: their update is the identity.
-template <typename V>
+template <typename V, int R>
 __device__ void phase_update_bulk(const Params<V>& P, int p, int zq, unsigned nact, int rev) {
     const int lane = threadIdx.x & 31;
     const long long nchunks = ((long long)nact + 31) / 32;
-    const long long ngroups = ((long long)P.m + kRowsInFlight - 1) / kRowsInFlight;
+    const long long ngroups = ((long long)P.m + R - 1) / R;
     const long long total = nchunks * ngroups;
     long long gcur = -1;
-    V f[kRowsInFlight];
+    V f[R];
     int i0 = 1, nrows = 0;
     // Slots are handed out `grab` at a time from a counter (a static split
     // leaves the slowest blocks ~15% behind the mean); the next grab is
@@ -583,23 +607,322 @@ __device__ void phase_update_bulk(const Params<V>& P, int p, int zq, unsigned na
             const long long c = ur - g * nchunks;
             if (g != gcur) {
                 gcur = g;
-                i0 = 1 + (int)g * kRowsInFlight;
-                nrows = min(kRowsInFlight, P.m + 1 - i0);
+                i0 = 1 + (int)g * R;
+                nrows = min(R, P.m + 1 - i0);
 #pragma unroll
-                for (int k = 0; k < kRowsInFlight; ++k) f[k] = k < nrows ? __ldcg(P.F + i0 + k) : V(0);
+                for (int k = 0; k < R; ++k) f[k] = k < nrows ? __ldcg(P.F + i0 + k) : V(0);
             }
-            update_slot(P, p, zq, nact, c, i0, nrows, f);
+            update_slot<V, R>(P, p, zq, nact, c, i0, nrows, f);
         }
     }
 }
 
+// ------------------------------------------- P4b with bulk copies (TMA)
+// Condensed layout: a slot's rows are contiguous 1 KB pieces of the tableau
+// (32 sectors of one chunk), so each warp streams its slots into a ring of
+// shared-memory stages with cp.async.bulk and an mbarrier per stage.  The
+// loads of the next stages are in flight while the warp runs the FMAs and
+// stores of the current one, without holding registers for them.
+constexpr int kTmaRows = TSX_TMA_ROWS;       // rows per slot
+constexpr int kTmaBatch = TSX_TMA_BATCH;
+constexpr int kChunkBytes = 32 * 32;          // one chunk of one row: 32 sectors
+constexpr int kTmaSmPerSm = 200 * 1024;       // ring bytes per SM (of 228 KB)
+
+// Stages per warp for blocks of nt threads: TSX_TMA_STAGES, fewer where the
+// rings of all resident warps would not fit the budget; 0 (no ring: the
+// register path) where fewer than two fit.
+__host__ __device__ constexpr int tma_fit(int nt) {
+    return kTmaSmPerSm / (((nt > TSX_SM_THREADS ? nt : TSX_SM_THREADS) / 32) * (kTmaRows * kChunkBytes + 8));
+}
+__host__ __device__ constexpr int tma_stages(int nt) {
+    return !TSX_TMA ? 0 : tma_fit(nt) >= TSX_TMA_STAGES ? TSX_TMA_STAGES : tma_fit(nt) >= 2 ? tma_fit(nt) : 0;
+}
+__host__ __device__ constexpr size_t tma_smem_bytes(int nt) {
+    return (size_t)(nt / 32) * tma_stages(nt) * ((size_t)kTmaRows * kChunkBytes + 8);
+}
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(unsigned bar) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned bar, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+        : "=r"(ok) : "r"(bar), "r"(parity) : "memory");
+    return ok != 0;
+}
+// Waits for the phase with the given parity to complete; bounded by the
+// solve's barrier timeout (globaltimer) and a spin count.
+__device__ inline bool mbar_wait(unsigned bar, unsigned parity, long long timeout_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = global_ns();
+    const unsigned long long max_spins = (unsigned long long)(timeout_ns > 0 ? timeout_ns : 0) + 4096ull;
+    for (unsigned long long spins = 1;; ++spins) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if ((spins & 15ull) == 0 && (global_ns() - t0 >= timeout_ns || spins > max_spins)) return false;
+    }
+}
+__device__ __forceinline__ void bulk_load(unsigned dst, const void* src, unsigned bytes, unsigned bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(dst), "l"(src), "r"(bytes), "r"(bar) : "memory");
+}
+// Orders this thread's view of global memory (generic proxy: the stores of
+// the previous pivot, published by the grid barrier) before its bulk copies.
+__device__ __forceinline__ void fence_proxy_async_global() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// 16-byte pieces: a lane takes bytes [16 lane, 16 lane + 16) and
+// [512 + 16 lane, 528 + 16 lane) of a chunk, so its shared-memory reads are
+// conflict-free and its stores coalesce per warp instruction.
 template <typename V>
-__device__ void phase_update(const Params<V>& P, int p, int q, long long it) {
+struct Piece {
+    static constexpr int N = 16 / (int)sizeof(V);
+    V v[N];
+};
+__device__ __forceinline__ Piece<double> ld_piece_cg(const double* p) {
+    Piece<double> x;
+    asm volatile("ld.global.cg.v2.f64 {%0,%1}, [%2];" : "=d"(x.v[0]), "=d"(x.v[1]) : "l"(p));
+    return x;
+}
+__device__ __forceinline__ Piece<float> ld_piece_cg(const float* p) {
+    Piece<float> x;
+    asm volatile("ld.global.cg.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(x.v[0]), "=f"(x.v[1]), "=f"(x.v[2]), "=f"(x.v[3]) : "l"(p));
+    return x;
+}
+template <typename V>
+__device__ Piece<V> ld_piece_smem(unsigned a);
+template <>
+__device__ __forceinline__ Piece<double> ld_piece_smem<double>(unsigned a) {
+    Piece<double> x;
+    asm volatile("ld.shared.v2.f64 {%0,%1}, [%2];" : "=d"(x.v[0]), "=d"(x.v[1]) : "r"(a) : "memory");
+    return x;
+}
+template <>
+__device__ __forceinline__ Piece<float> ld_piece_smem<float>(unsigned a) {
+    Piece<float> x;
+    asm volatile("ld.shared.v4.f32 {%0,%1,%2,%3}, [%4];"
+                 : "=f"(x.v[0]), "=f"(x.v[1]), "=f"(x.v[2]), "=f"(x.v[3]) : "r"(a) : "memory");
+    return x;
+}
+__device__ __forceinline__ void st_piece(double* p, const Piece<double>& x) {
+    asm volatile("st.global.v2.f64 [%0], {%1,%2};" ::"l"(p), "d"(x.v[0]), "d"(x.v[1]) : "memory");
+}
+__device__ __forceinline__ void st_piece(float* p, const Piece<float>& x) {
+    asm volatile("st.global.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(x.v[0]), "f"(x.v[1]), "f"(x.v[2]),
+                 "f"(x.v[3]) : "memory");
+}
+
+// A warp's ring: kTmaStages stages of kTmaRows x 1 KB and one mbarrier each.
+// `phase` bit s is the parity of stage s's next completion; it persists
+// across pivots (every issued stage is consumed before the phase ends).
+template <int S>
+struct TmaRing {
+    static_assert(S >= 2, "a ring needs two stages");
+    unsigned data;    // shared address of stage 0
+    unsigned bar;     // shared address of stage 0's mbarrier
+    unsigned phase;
+};
+
+template <int NT>
+__device__ inline TmaRing<tma_stages(NT)> tma_ring_init(unsigned char* dyn) {
+    constexpr int S = tma_stages(NT), nw = NT / 32;
+    const int w = threadIdx.x >> 5;
+    TmaRing<S> r;
+    r.data = smem_u32(dyn) + (unsigned)(w * S * kTmaRows * kChunkBytes);
+    r.bar = smem_u32(dyn) + (unsigned)(nw * S * kTmaRows * kChunkBytes + w * S * 8);
+    r.phase = 0;
+    if ((threadIdx.x & 31) == 0) {
+        for (int s = 0; s < S; ++s) mbar_init(r.bar + 8 * s);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    }
+    __syncwarp();
+    return r;
+}
+
+// Slot u of a pivot's update (same numbering as phase_update_bulk with
+// kTmaRows rows per group): rows i0 .. i0+nrows-1, chunk c.  Slot numbers
+// fit 32 bits: the slot counter is 32 bits wide and a slot covers 4 KB or
+// more of the tableau.
+struct TmaSlot {
+    unsigned c;
+    int i0, nrows;
+    unsigned bytes;   // bytes of each row's piece of the chunk (32 per sector)
+};
+
+__device__ __forceinline__ TmaSlot tma_slot(unsigned u, unsigned total, unsigned nchunks, unsigned nact, int m,
+                                            int rev) {
+    const unsigned ur = rev ? total - 1 - u : u;
+    const unsigned g = ur / nchunks;
+    TmaSlot t;
+    t.c = ur - g * nchunks;
+    t.i0 = 1 + (int)g * kTmaRows;
+    t.nrows = min(kTmaRows, m + 1 - t.i0);
+    t.bytes = 32u * min(32u, nact - t.c * 32u);
+    return t;
+}
+
+// Lane 0: the stage's expected bytes, then one bulk copy per row (row p is
+// skipped: the edge-row phase rewrites it meanwhile).
+template <typename V>
+__device__ __forceinline__ void tma_issue(const Params<V>& P, int p, const TmaSlot& t, unsigned dst, unsigned bar) {
+    constexpr int E = Lanes<V>::E;
+    const int skip = (p >= t.i0 && p < t.i0 + t.nrows) ? 1 : 0;
+    mbar_arrive_expect_tx(bar, t.bytes * (unsigned)(t.nrows - skip));
+    for (int k = 0; k < t.nrows; ++k) {
+        const int i = t.i0 + k;
+        if (i != p) bulk_load(dst + k * kChunkBytes, P.T + (size_t)i * (size_t)P.ld + (size_t)t.c * 32 * E, t.bytes, bar);
+    }
+}
+
+template <typename V>
+struct TmaOperands {   // a lane's R pieces and the slot's F values
+    Piece<V> r0, r1;
+    V f[kTmaRows];
+};
+
+template <typename V>
+__device__ __forceinline__ TmaOperands<V> tma_operands(const Params<V>& P, const TmaSlot& t) {
+    constexpr int E = Lanes<V>::E, N = Piece<V>::N;
+    const int lane = threadIdx.x & 31;
+    TmaOperands<V> o;
+    const size_t col = (size_t)t.c * 32 * E + (size_t)lane * N;
+    if ((unsigned)(16 * lane) < t.bytes) o.r0 = ld_piece_cg(P.R + col);
+    if ((unsigned)(512 + 16 * lane) < t.bytes) o.r1 = ld_piece_cg(P.R + col + 32 * N);
+#pragma unroll
+    for (int k = 0; k < kTmaRows; ++k) o.f[k] = k < t.nrows ? __ldcg(P.F + t.i0 + k) : V(0);
+    return o;
+}
+
+// All lanes: the FMAs and stores of one staged slot.
+template <typename V>
+__device__ __forceinline__ void tma_compute(const Params<V>& P, int p, int zq, const TmaSlot& t,
+                                            const TmaOperands<V>& o, unsigned src) {
+    constexpr int E = Lanes<V>::E, N = Piece<V>::N;
+    const int lane = threadIdx.x & 31;
+    const int col0 = (int)t.c * 32 * E + lane * N;
+    const bool h0 = (unsigned)(16 * lane) < t.bytes, h1 = (unsigned)(512 + 16 * lane) < t.bytes;
+    const int eq0 = zq - col0, eq1 = zq - (col0 + 32 * N);
+    // the reads of kTmaBatch rows first, then their FMAs and stores
+    constexpr int B = kTmaBatch < kTmaRows ? kTmaBatch : kTmaRows;
+#pragma unroll
+    for (int k0 = 0; k0 < kTmaRows; k0 += B) {
+    Piece<V> x0[B], x1[B];
+#pragma unroll
+    for (int kk = 0; kk < B; ++kk) {
+        const int k = k0 + kk;
+        if (k < t.nrows && h0) x0[kk] = ld_piece_smem<V>(src + k * kChunkBytes + 16 * lane);
+        if (k < t.nrows && h1) x1[kk] = ld_piece_smem<V>(src + k * kChunkBytes + 512 + 16 * lane);
+    }
+#pragma unroll
+    for (int kk = 0; kk < B; ++kk) {
+        const int k = k0 + kk;
+        const int i = t.i0 + k;
+        if (k < t.nrows && i != p) {
+            V* row = P.T + (size_t)i * (size_t)P.ld + col0;
+            const V f = -o.f[k];
+            if (h0) {
+#pragma unroll
+                for (int e = 0; e < N; ++e) x0[kk].v[e] = fma_rn(f, o.r0.v[e], e == eq0 ? V(0) : x0[kk].v[e]);
+                st_piece(row, x0[kk]);
+            }
+            if (h1) {
+#pragma unroll
+                for (int e = 0; e < N; ++e) x1[kk].v[e] = fma_rn(f, o.r1.v[e], e == eq1 ? V(0) : x1[kk].v[e]);
+                st_piece(row + 32 * N, x1[kk]);
+            }
+        }
+    }
+    }
+}
+
+// P4b through the ring.  Slots come from the same counter as in
+// phase_update_bulk: the prologue takes kTmaStages consecutive slots, each
+// consumed stage is refilled with a slot requested one stage earlier.  Slot
+// numbers grow in the order the stages are consumed, so the first stage with
+// no slot ends the phase with nothing left in flight.
+template <typename V, int kTmaStages>
+__device__ void phase_update_bulk_tma(const Params<V>& P, int p, int zq, unsigned nact, int rev,
+                                      TmaRing<kTmaStages>& ring) {
+    const int lane = threadIdx.x & 31;
+    const unsigned nchunks = (nact + 31) / 32;
+    const unsigned ngroups = (unsigned)((P.m + kTmaRows - 1) / kTmaRows);
+    const unsigned total = nchunks * ngroups;
+    constexpr unsigned kStageBytes = kTmaRows * kChunkBytes;
+    unsigned u[kTmaStages];
+    unsigned base = 0;
+    if (lane == 0) {
+        fence_proxy_async_global();
+        base = atomicAdd(&P.st->next_slot, (unsigned)kTmaStages);
+    }
+    base = __shfl_sync(0xffffffffu, base, 0);
+#pragma unroll
+    for (int s = 0; s < kTmaStages; ++s) {
+        u[s] = base + s;
+        if (lane == 0 && u[s] < total)
+            tma_issue(P, p, tma_slot(u[s], total, nchunks, nact, P.m, rev), ring.data + s * kStageBytes, ring.bar + 8 * s);
+    }
+    if (u[0] >= total) return;
+    TmaSlot t = tma_slot(u[0], total, nchunks, nact, P.m, rev);
+    TmaOperands<V> o = tma_operands(P, t);
+    for (;;) {
+#pragma unroll
+        for (int s = 0; s < kTmaStages; ++s) {
+            const int sn = (s + 1) % kTmaStages;
+            unsigned req = 0;
+            if (lane == 0) req = atomicAdd(&P.st->next_slot, 1u);   // the refill of stage s
+            const bool more = u[sn] < total;
+            TmaSlot tn = t;
+            TmaOperands<V> on = o;
+            if (more) {   // the next stage's operands, loaded ahead
+                tn = tma_slot(u[sn], total, nchunks, nact, P.m, rev);
+                on = tma_operands(P, tn);
+            }
+            const bool ok = mbar_wait(ring.bar + 8 * s, (ring.phase >> s) & 1u, P.timeout_ns);
+            if (!__all_sync(0xffffffffu, ok)) goto drain;
+            ring.phase ^= 1u << s;
+            tma_compute(P, p, zq, t, o, ring.data + s * kStageBytes);
+            __syncwarp();
+            u[s] = __shfl_sync(0xffffffffu, req, 0);
+            if (lane == 0 && u[s] < total)
+                tma_issue(P, p, tma_slot(u[s], total, nchunks, nact, P.m, rev), ring.data + s * kStageBytes,
+                          ring.bar + 8 * s);
+            if (!more) return;
+            t = tn;
+            o = on;
+        }
+    }
+drain:
+    // a wait ran out: mark the solve, wait (bounded) for the stages' copies
+    // so that none lands after the block exits
+    if (lane == 0) atomicCAS(&P.st->status, kRunning, kTimeout);
+#pragma unroll
+    for (int s = 0; s < kTmaStages; ++s) {
+        if (u[s] < total) {
+            mbar_wait(ring.bar + 8 * s, (ring.phase >> s) & 1u, 1000000);
+            ring.phase ^= 1u << s;
+        }
+    }
+}
+
+template <typename V, int R = kRowsInFlight, int S = 2>
+__device__ void phase_update(const Params<V>& P, int p, int q, long long it, TmaRing<S>* ring = nullptr) {
     constexpr int E = Lanes<V>::E;
     const unsigned nact = P.cond ? (unsigned)(P.ld / E) : *(volatile const unsigned*)&P.st->nact;
     if (blockIdx.x == 0 && threadIdx.x == 0) P.st->active_sectors += nact;
     phase_update_edge_rows(P, p, q);
-    phase_update_bulk(P, p, P.cond ? q : -1, nact, TSX_ALTERNATE ? (int)(it & 1) : 0);
+    const int rev = TSX_ALTERNATE ? (int)(it & 1) : 0;
+    if (ring && P.cond)
+        phase_update_bulk_tma(P, p, q, nact, rev, *ring);
+    else
+        phase_update_bulk<V, R>(P, p, P.cond ? q : -1, nact, rev);
 }
 
 }  // namespace tsx

@@ -165,9 +165,13 @@ struct PhaseClock {
 // pivot (after P2, after P3, after P4).  Every block takes the same decisions
 // from the same reduced values, so all leave the loop together.
 template <int NT, typename V>
-__global__ void __launch_bounds__(NT, 512 / NT) k_pivot_persistent(Params<V> P) {
+__global__ void __launch_bounds__(NT, persistent_sm_threads(NT) / NT) k_pivot_persistent(Params<V> P) {
     __shared__ BlockScratch s;
     __shared__ PhaseClock clk;
+    extern __shared__ __align__(128) unsigned char tsx_dyn[];
+    TmaRing<(tma_stages(NT) >= 2 ? tma_stages(NT) : 2)> ring;
+    auto* ringp = tma_stages(NT) >= 2 ? &ring : nullptr;
+    if constexpr (tma_stages(NT) >= 2) ring = tma_ring_init<NT>(tsx_dyn);
     clk.start();
     phase_init_argmin(P);
     if (!grid_barrier(P.st, P.timeout_ns, s)) return;
@@ -194,7 +198,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_pivot_persistent(Params<V> P) 
         clk.lap(1);
         if (!grid_barrier(P.st, P.timeout_ns, s)) return;
         clk.lap(4);
-        phase_update(P, l.i, q, it);                      // Step 3 (rank-1 update)
+        phase_update<V, persistent_rows(NT)>(P, l.i, q, it, ringp);   // Step 3 (rank-1 update)
         ++it;
         degeneracy_step(P, l.r, bland, degen);
         clk.lap(2);

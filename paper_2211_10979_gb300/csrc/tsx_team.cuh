@@ -21,6 +21,13 @@
 namespace tsx {
 
 constexpr int kTeamMax = 160;  // blocks per team, upper bound
+#ifndef TSX_TEAM_SM_THREADS
+#define TSX_TEAM_SM_THREADS 512   // threads per SM the team kernel is compiled for
+#endif
+// Threads per SM of the team kernel with blocks of nt threads, and the rows a
+// warp of its update keeps in flight (16 where a thread may hold 255 registers).
+__host__ __device__ constexpr int team_sm_threads(int nt) { return nt > TSX_TEAM_SM_THREADS ? nt : TSX_TEAM_SM_THREADS; }
+__host__ __device__ constexpr int team_rows_in_flight(int nt) { return team_sm_threads(nt) <= 256 ? 16 : kRowsInFlight; }
 
 template <typename V>
 struct TeamJob {
@@ -168,33 +175,33 @@ __device__ void team_row0(const TeamJob<V>& J, const V* R, V f0, int q, const Te
 }
 
 // Rank-1 update of the block's rows [lo, r1) except p, R and the multipliers
-// (Floc, indexed from r0) in shared memory; slots of 8 rows x 32 column
+// (Floc, indexed from r0) in shared memory; slots of RF rows x 32 column
 // groups, one group per lane.
-template <typename V>
+template <typename V, int RF>
 __device__ void team_update(const TeamJob<V>& J, const V* R, const V* Floc, int r0, int lo, int r1, int p, int q) {
     constexpr int E = Lanes<V>::E;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int nsec = J.ld / E;
     const int nchunks = (nsec + 31) / 32;
-    const int nrg = (r1 - lo + kRowsInFlight - 1) / kRowsInFlight;
+    const int nrg = (r1 - lo + RF - 1) / RF;
     const long long total = (long long)nrg * nchunks;
     for (long long u = warp; u < total; u += nw) {
         const int rg = (int)(u / nchunks), ch = (int)(u - (long long)rg * nchunks);
-        const int i0 = lo + rg * kRowsInFlight;
-        const int nrows = min(kRowsInFlight, r1 - i0);
+        const int i0 = lo + rg * RF;
+        const int nrows = min(RF, r1 - i0);
         const int gidx = ch * 32 + lane;
         if (gidx >= nsec) continue;
         const size_t col = (size_t)E * (size_t)gidx;
         const Sector<V> r = *reinterpret_cast<const Sector<V>*>(R + col);
         const int eq = q - (int)col;
-        Sector<V> v[kRowsInFlight];
+        Sector<V> v[RF];
 #pragma unroll
-        for (int k = 0; k < kRowsInFlight; ++k) {
+        for (int k = 0; k < RF; ++k) {
             const int i = i0 + k;
             if (k < nrows && i != p) v[k] = ld_sector_stream(J.T + (size_t)i * (size_t)J.ld + col);
         }
 #pragma unroll
-        for (int k = 0; k < kRowsInFlight; ++k) {
+        for (int k = 0; k < RF; ++k) {
             const int i = i0 + k;
             if (k < nrows && i != p) {
                 const V f = Floc[i - r0];
@@ -207,7 +214,7 @@ __device__ void team_update(const TeamJob<V>& J, const V* R, const V* Floc, int 
 }
 
 // Solves one LP with the team of C blocks; false if a team barrier failed.
-template <typename V>
+template <int RF, typename V>
 __device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, TeamState* ts, int bt, unsigned C,
                                V* R, V* Floc, BlockScratch& s, int& sok) {
     const int m = J.m, n = J.n, ld = J.ld;
@@ -274,7 +281,7 @@ __device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, Team
         }
         __syncthreads();
         if (bt == 0) team_row0(J, R, Floc[0], q, P, ts, s);   // the next Step 1 on the new row 0
-        team_update(J, R, Floc, r0, lo, r1, p, q);
+        team_update<V, RF>(J, R, Floc, r0, lo, r1, p, q);
         ++it;
         if (!team_barrier(ts, C, P.timeout_ns, sok)) return false;
         if (p >= r0 && p < r1) {   // every block has read row p: its owner stores R there
@@ -300,7 +307,7 @@ __device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, Team
 // Dynamic shared memory per block: R (ld_max entries) then the multipliers
 // (rows per block, max over the lists for the smallest team).
 template <int NT, typename V>
-__global__ void __launch_bounds__(NT, 512 / NT) k_team_solve(TeamParams<V> P, int ld_max) {
+__global__ void __launch_bounds__(NT, team_sm_threads(NT) / NT) k_team_solve(TeamParams<V> P, int ld_max) {
     extern __shared__ __align__(32) unsigned char team_smem[];
     __shared__ BlockScratch s;
     __shared__ int sok;
@@ -326,7 +333,7 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_team_solve(TeamParams<V> P, in
         const int k = *(volatile const int*)&ts->job;
         if (k < 0) return;
         const TeamJob<V> J = P.jobs[k];
-        if (!team_solve_one(P, J, ts, bt, C, R, Floc, s, sok)) return;
+        if (!team_solve_one<team_rows_in_flight(NT)>(P, J, ts, bt, C, R, Floc, s, sok)) return;
     }
 }
 
