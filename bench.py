@@ -175,18 +175,19 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def profile_traffic(m, n):
-    """ncu DRAM bytes per pivot of the update kernel, if a summary for this
-    exact kernel build and workload is committed under profiles/."""
+def profile_traffic(m, n, max_iters=-1, layout="condensed"):
+    """ncu DRAM bytes per launch of the pivot kernel, if a summary for this
+    exact kernel build and workload (FP64; a full solve, or the first
+    max_iters pivots) is committed under profiles/."""
     path = os.path.join(ROOT, "profiles", "traffic_k_pivot_persistent.txt")
     try:
         with open(path) as fh:
             d = json.load(fh)
     except (OSError, ValueError):
         return None
-    key = f"{m}x{n}"
+    key = f"{m}x{n}" + (f"@{max_iters}" if max_iters >= 0 else "")
     ent = d.get(key)
-    if not ent:
+    if not ent or ent.get("layout") != layout:
         return None
     from paper_2211_10979_gb300 import build as b
     if ent.get("source_digest") != b.source_digest(b.PIVOT_SOURCES):
@@ -402,7 +403,7 @@ def run_gpu(args, rank, world, local):
         upd_bytes = sum(s["update_bytes"] for s in stats) / len(stats)
         dense_bytes = sum(s["dense_update_bytes"] for s in stats) / len(stats)
         achieved = upd_bytes / (kernel_ms / 1000.0) / 1e9
-        traffic = profile_traffic(m, n)
+        traffic = profile_traffic(m, n, args.max_iters, args.layout)
         launches = sum(s["kernel_launches"] + 4 for s in stats)   # + validate/reset + 2 extract
         cpu = None
         if not args.no_cpu_baseline:
