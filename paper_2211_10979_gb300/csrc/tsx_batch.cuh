@@ -62,8 +62,33 @@ __host__ __device__ inline size_t batch_smem_bytes(int m, int n, int ldc) {
 
 constexpr int kRc = 4;        // scaled-pivot-row entries per lane kept in registers
 
+// The reductions of Steps 1-2 compare 64-bit integer keys with the order of
+// the doubles they stand for: on GB300 every FP64 comparison occupies the
+// SM's FP64 pipe (16 cycles a warp instruction), the pipe that also runs the
+// update's DFMAs, while integer compares run on the ALU pipes.  For doubles
+// that are not NaN, x < y iff dkey(x) < dkey(y), and x == y iff
+// dkey(x) == dkey(y) (-0 and +0 share the key of +0), so every decision and
+// tie is the one the floating-point comparisons take.  NaN values never win
+// a floating-point `<` or `==` comparison; the kernel keeps them out of the
+// candidates instead.  The map is its own inverse up to the sign of zero.
+__device__ __forceinline__ long long dkey(double x) {
+    long long b = __double_as_longlong(x);
+    if (b == (long long)0x8000000000000000ULL) b = 0;
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dkey_value(long long k) {
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+__device__ __forceinline__ bool dbits_nan(double x) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool dbits_finite(double x) {
+    return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+constexpr long long kKeyInf = 0x7ff0000000000000LL;   // dkey(+inf)
+
 struct BArg {                 // entering candidate
-    double v;                 // objective-row entry
+    long long vk;             // dkey of its objective-row entry
     int var;                  // its variable (tie-break), INT_MAX if none
     int slot;
     int fvar;                 // Bland: lowest candidate variable
@@ -71,15 +96,41 @@ struct BArg {                 // entering candidate
 };
 
 __device__ __forceinline__ void barg_merge(BArg& a, const BArg& b) {
-    if (b.v < a.v || (b.v == a.v && b.var < a.var)) { a.v = b.v; a.var = b.var; a.slot = b.slot; }
+    if (b.vk < a.vk || (b.vk == a.vk && b.var < a.var)) { a.vk = b.vk; a.var = b.var; a.slot = b.slot; }
     if (b.fvar < a.fvar) { a.fvar = b.fvar; a.fslot = b.fslot; }
+}
+
+struct BRat {                 // leaving candidate
+    long long rk;             // dkey of the ratio rhs_i / T[i][q]; dkey(+inf) if none
+    int key;                  // tie-break key: row (Dantzig) or basic variable (Bland)
+    int i;                    // its row, INT_MAX if none
+    double a;                 // its pivot element
+};
+
+__device__ __forceinline__ BRat brat_none() { return BRat{kKeyInf, INT_MAX, INT_MAX, 0.0}; }
+
+__device__ __forceinline__ void brat_merge(BRat& a, const BRat& b) {
+    if (b.rk < a.rk || (b.rk == a.rk && b.key < a.key)) a = b;
+}
+
+__device__ __forceinline__ BRat warp_brat(BRat a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        BRat b;
+        b.rk = __shfl_xor_sync(0xffffffffu, a.rk, o);
+        b.key = __shfl_xor_sync(0xffffffffu, a.key, o);
+        b.i = __shfl_xor_sync(0xffffffffu, a.i, o);
+        b.a = __shfl_xor_sync(0xffffffffu, a.a, o);
+        brat_merge(a, b);
+    }
+    return a;
 }
 
 struct BatchScratch {
     BArg arg[kMaxWarps];
-    RatPart rat[kMaxWarps];
+    BRat rat[kMaxWarps];
     BArg arg_out;
-    RatPart rat_out;
+    BRat rat_out;
     int lp;
 };
 
@@ -88,7 +139,7 @@ __device__ __forceinline__ BArg warp_barg(BArg a) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         BArg b;
-        b.v = __shfl_xor_sync(0xffffffffu, a.v, o);
+        b.vk = __shfl_xor_sync(0xffffffffu, a.vk, o);
         b.var = __shfl_xor_sync(0xffffffffu, a.var, o);
         b.slot = __shfl_xor_sync(0xffffffffu, a.slot, o);
         b.fvar = __shfl_xor_sync(0xffffffffu, a.fvar, o);
@@ -99,13 +150,15 @@ __device__ __forceinline__ BArg warp_barg(BArg a) {
 }
 
 __device__ __forceinline__ BArg barg_none() {
-    return BArg{__longlong_as_double(0x7ff0000000000000LL), INT_MAX, -1, INT_MAX, -1};
+    return BArg{kKeyInf, INT_MAX, -1, INT_MAX, -1};
 }
 
-// Step 1 candidate of objective-row slot j (value v, variable var).
+// Step 1 candidate of objective-row slot j (value v, variable var); a NaN
+// entry fails the test v < -eps_d and is no candidate.
 __device__ __forceinline__ void barg_consider(BArg& a, double v, int vj, int j, double eps_d) {
     if (v < -eps_d) {
-        if (v < a.v || (v == a.v && vj < a.var)) { a.v = v; a.var = vj; a.slot = j; }
+        const long long vk = dkey(v);
+        if (vk < a.vk || (vk == a.vk && vj < a.var)) { a.vk = vk; a.var = vj; a.slot = j; }
         if (vj < a.fvar) { a.fvar = vj; a.fslot = j; }
     }
 }
@@ -114,15 +167,15 @@ __device__ __forceinline__ void barg_consider(BArg& a, double v, int vj, int j, 
 // posts the warp's partial, every thread merges the posted partials.  The
 // partials' slots are next written after at least one more barrier.
 template <int NT>
-__device__ RatPart batch_block_rat(RatPart a, BatchScratch& s) {
+__device__ BRat batch_block_rat(BRat a, BatchScratch& s) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    a = warp_rat(a);
+    a = warp_brat(a);
     if (NT == 32) return a;
     if (lane == 0) s.rat[w] = a;
     __syncthreads();
-    RatPart r = s.rat[0];
+    BRat r = s.rat[0];
 #pragma unroll
-    for (int k = 1; k < NT / 32; ++k) rat_merge(r, s.rat[k]);
+    for (int k = 1; k < NT / 32; ++k) brat_merge(r, s.rat[k]);
     return r;
 }
 
@@ -152,7 +205,7 @@ __device__ void batch_solve_one(const BatchParams& P, int k, unsigned char* smem
             v = i == 0 ? -c[j] : A[(size_t)(i - 1) * n + j];
         else if (j == n && i > 0)
             v = b[i - 1];
-        if (j <= n) bad |= !isfinite(v) || (j == n && i > 0 && !(v >= 0.0));
+        if (j <= n) bad |= !dbits_finite(v) || (j == n && i > 0 && !(v >= 0.0));
         T[t] = v;
     }
     for (int j = tid; j < n; j += NT) var[j] = j;
@@ -180,26 +233,29 @@ __device__ void batch_solve_one(const BatchParams& P, int k, unsigned char* smem
         if (it >= cap) { status = kIterLimit; break; }
         // Step 2: minimum ratio on slot qs (ties: row, or basic variable in
         // Bland mode); column qs is copied to F on the way
-        RatPart best = rat_none();
+        BRat best = brat_none();
         if (tid == 0) F[0] = T[qs];
         for (int i = 1 + tid; i <= m; i += NT) {
             const double av = T[(size_t)i * ldc + qs];
             F[i] = av;
             if (av > P.eps_p) {
-                RatPart cnd;
-                cnd.r = __ddiv_rn(T[(size_t)i * ldc + n], av);
-                cnd.i = i;
-                cnd.key = bland ? basis[i - 1] : i;
-                cnd.a = av;
-                cnd.pad = 0.0;
-                rat_merge(best, cnd);
+                const double r = __ddiv_rn(T[(size_t)i * ldc + n], av);
+                if (!dbits_nan(r)) {   // a NaN ratio never wins the comparison
+                    BRat cnd;
+                    cnd.rk = dkey(r);
+                    cnd.i = i;
+                    cnd.key = bland ? basis[i - 1] : i;
+                    cnd.a = av;
+                    brat_merge(best, cnd);
+                }
             }
         }
         best = batch_block_rat<NT>(best, sc);
         if (best.i == INT_MAX) { status = kUnbounded; break; }
         const int p = best.i;
         const double piv = best.a;
-        if (!isfinite(piv) || !isfinite(best.r)) { status = kNumeric; break; }
+        const double ratio = dkey_value(best.rk);
+        if (!dbits_finite(piv) || !dbits_finite(ratio)) { status = kNumeric; break; }
         // Step 3: scaled pivot row; the leaving variable takes slot qs
         for (int j = tid; j <= n; j += NT) R[j] = j == qs ? __ddiv_rn(1.0, piv) : __ddiv_rn(T[(size_t)p * ldc + j], piv);
         if (tid == 0) {
@@ -209,7 +265,7 @@ __device__ void batch_solve_one(const BatchParams& P, int k, unsigned char* smem
         }
         ++it;
         if (P.rule == 0) {
-            if (best.r <= 0.0) {
+            if (best.rk <= 0) {   // ratio <= 0
                 ++degen;
                 if (P.k_cyc > 0 && degen >= P.k_cyc) bland = 1;
             } else {
