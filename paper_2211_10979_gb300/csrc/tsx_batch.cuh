@@ -62,31 +62,8 @@ __host__ __device__ inline size_t batch_smem_bytes(int m, int n, int ldc) {
 
 constexpr int kRc = 4;        // scaled-pivot-row entries per lane kept in registers
 
-// The reductions of Steps 1-2 compare 64-bit integer keys with the order of
-// the doubles they stand for: on GB300 every FP64 comparison occupies the
-// SM's FP64 pipe (16 cycles a warp instruction), the pipe that also runs the
-// update's DFMAs, while integer compares run on the ALU pipes.  For doubles
-// that are not NaN, x < y iff dkey(x) < dkey(y), and x == y iff
-// dkey(x) == dkey(y) (-0 and +0 share the key of +0), so every decision and
-// tie is the one the floating-point comparisons take.  NaN values never win
-// a floating-point `<` or `==` comparison; the kernel keeps them out of the
-// candidates instead.  The map is its own inverse up to the sign of zero.
-__device__ __forceinline__ long long dkey(double x) {
-    long long b = __double_as_longlong(x);
-    if (b == (long long)0x8000000000000000ULL) b = 0;
-    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
-}
-__device__ __forceinline__ double dkey_value(long long k) {
-    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
-}
-__device__ __forceinline__ bool dbits_nan(double x) {
-    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
-}
-__device__ __forceinline__ bool dbits_finite(double x) {
-    return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
-}
-constexpr long long kKeyInf = 0x7ff0000000000000LL;   // dkey(+inf)
-
+// The reductions of Steps 1-2 compare the integer keys of tsx_device.cuh
+// (dkey), not the doubles: no FP64-pipe instruction in the argmin trees.
 struct BArg {                 // entering candidate
     long long vk;             // dkey of its objective-row entry
     int var;                  // its variable (tie-break), INT_MAX if none

@@ -232,6 +232,31 @@ __device__ __forceinline__ bool sector_nonzero(const Sector<V>& s) {
     return nz;
 }
 
+// The reductions of Steps 1-2 compare 64-bit integer keys with the order of
+// the doubles they stand for: on GB300 every FP64 comparison occupies the
+// SM's FP64 pipe (16 cycles a warp instruction), the pipe that also runs the
+// update's DFMAs, while integer compares run on the ALU pipes.  For doubles
+// that are not NaN, x < y iff dkey(x) < dkey(y), and x == y iff
+// dkey(x) == dkey(y) (-0 and +0 share the key of +0), so every decision and
+// tie is the one the floating-point comparisons take.  NaN values never win
+// a floating-point `<` or `==` comparison; the kernel keeps them out of the
+// candidates instead.  The map is its own inverse up to the sign of zero.
+__device__ __forceinline__ long long dkey(double x) {
+    long long b = __double_as_longlong(x);
+    if (b == (long long)0x8000000000000000ULL) b = 0;
+    return b ^ ((b >> 63) & 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double dkey_value(long long k) {
+    return __longlong_as_double(k ^ ((k >> 63) & 0x7fffffffffffffffLL));
+}
+__device__ __forceinline__ bool dbits_nan(double x) {
+    return (__double_as_longlong(x) & 0x7fffffffffffffffLL) > 0x7ff0000000000000LL;
+}
+__device__ __forceinline__ bool dbits_finite(double x) {
+    return (__double_as_longlong(x) & 0x7ff0000000000000LL) != 0x7ff0000000000000LL;
+}
+constexpr long long kKeyInf = 0x7ff0000000000000LL;   // dkey(+inf)
+
 __device__ __forceinline__ ArgPart arg_none() {
     return ArgPart{__longlong_as_double(0x7ff0000000000000LL), INT_MAX, INT_MAX, INT_MAX, INT_MAX, {0, 0}};
 }
@@ -241,16 +266,39 @@ __device__ __forceinline__ RatPart rat_none() { return RatPart{__longlong_as_dou
 // ties; and the lowest candidate variable (Bland).  The key of a column is its
 // variable: the column index itself in the full tableau, var[] in the
 // condensed one.
+// Merges of Step 1-2 partials (shuffle trees, block and grid reductions)
+// compare keys: measured 5888 vs 5817 pivots/s at 8192^2 (the ratio and
+// staging phases 2 us shorter per pivot).  Keys in the per-entry candidate
+// scans as well cost more ALU work in the objective-row pass than the FP64
+// comparisons they replace (5709).
+#ifndef TSX_KEYS
+#define TSX_KEYS 1   // 0: FP64 comparisons; 1: merges of partials on keys; 2: the candidate scans too
+#endif
+// Values of partials are +inf (none) or candidates (never NaN).
 __device__ __forceinline__ void arg_merge(ArgPart& a, const ArgPart& b) {
+#if TSX_KEYS >= 1
+    const long long bk = dkey(b.v), ak = dkey(a.v);
+    if (bk < ak || (bk == ak && b.key < a.key)) { a.v = b.v; a.key = b.key; a.slot = b.slot; }
+#else
     if (b.v < a.v || (b.v == a.v && b.key < a.key)) { a.v = b.v; a.key = b.key; a.slot = b.slot; }
+#endif
     if (b.fkey < a.fkey) { a.fkey = b.fkey; a.fslot = b.fslot; }
 }
 
 __device__ __forceinline__ void arg_consider(ArgPart& a, double v, int j, int key, int jend, double eps_d) {
+#if TSX_KEYS >= 2
+    const long long vk = dkey(v);
+    if (j < jend && !dbits_nan(v) && vk < dkey(-eps_d)) {
+        const long long ak = dkey(a.v);
+        if (vk < ak || (vk == ak && key < a.key)) { a.v = v; a.key = key; a.slot = j; }
+        if (key < a.fkey) { a.fkey = key; a.fslot = j; }
+    }
+#else
     if (j < jend && v < -eps_d) {
         if (v < a.v || (v == a.v && key < a.key)) { a.v = v; a.key = key; a.slot = j; }
         if (key < a.fkey) { a.fkey = key; a.fslot = j; }
     }
+#endif
 }
 
 // Columns j .. j+E-1 of the objective row; var == null: full tableau (key = j).
@@ -266,8 +314,15 @@ __device__ __forceinline__ void arg_consider_sector(ArgPart& a, const Sector<V>&
 }
 
 // (r, key) lexicographic minimum: smallest ratio, lowest key on ties.
+// Ratios are +inf (none) or candidates; a NaN ratio is never made a
+// candidate (it would lose every comparison).
 __device__ __forceinline__ void rat_merge(RatPart& a, const RatPart& b) {
+#if TSX_KEYS >= 1
+    const long long bk = dkey(b.r), ak = dkey(a.r);
+    if (bk < ak || (bk == ak && b.key < a.key)) a = b;
+#else
     if (b.r < a.r || (b.r == a.r && b.key < a.key)) a = b;
+#endif
 }
 
 __device__ __forceinline__ ArgPart warp_arg(ArgPart a) {
@@ -448,7 +503,7 @@ __device__ void phase_ratio(const Params<V>& P, int q, int bland, BlockScratch& 
             c.i = (int)i;
             c.key = bland ? __ldcg(P.basis + (i - 1)) : (int)i;
             c.a = (double)a;
-            rat_merge(best, c);
+            if (!dbits_nan(c.r)) rat_merge(best, c);
         }
     }
     best = block_rat(best, s);

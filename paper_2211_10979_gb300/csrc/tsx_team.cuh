@@ -249,7 +249,7 @@ __device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, Team
                 c.key = bland ? __ldcg(J.basis + (i - 1)) : i;
                 c.a = (double)a;
                 c.pad = 0.0;
-                rat_merge(best, c);
+                if (!dbits_nan(c.r)) rat_merge(best, c);
             }
         }
         best = block_rat(best, s);

@@ -136,3 +136,36 @@ def test_invalid_sizes_refused(tsx):
     with pytest.raises(ValueError, match="m > 0"):
         tsx.Batch(m=np.array([0], np.int32), n=np.array([3], np.int32), A=np.zeros(0), b=np.zeros(0),
                   c=np.zeros(3))
+
+
+def _tie_lps():
+    """LPs whose Step 1 and Step 2 comparisons meet exact ties, signed zeros
+    and zero ratios: duplicated rows and columns of a small integer matrix,
+    equal costs, and two unit rows with right-hand sides -0.0 and +0.0."""
+    rng = np.random.default_rng(77)
+    out = []
+    for h, n in ((3, 6), (6, 9), (20, 33), (35, 64)):
+        A0 = rng.integers(1, 4, size=(h, n - 2)).astype(np.float64)
+        A = np.vstack([A0, A0])                                  # every ratio appears twice
+        A = np.hstack([A, A[:, 2:4]])                            # duplicated columns
+        units = np.zeros((2, n))
+        units[0, 0] = 1.0
+        units[1, 1] = 2.0
+        A = np.vstack([A, units])
+        b = np.concatenate([np.tile(rng.integers(1, 5, size=h).astype(np.float64) * 4.0, 2), [-0.0, 0.0]])
+        c = rng.integers(1, 3, size=n).astype(np.float64)       # equal reduced costs
+        out.append((A, b, c))
+    return out
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_ties_and_signed_zeros_inside_a_batch(tsx, rule):
+    problems = _tie_lps()
+    kw = {"rule": rule} if rule else {"k_cyc": 5}
+    refs = [oracle.solve(*p, oracle.Options(**kw)) for p in problems]
+    with tsx.Batch(problems) as bt:
+        bt.solve(tsx.batch_options(keep_tableaux=1, **kw))
+        sol = bt.results()
+        _check(sol, problems, refs)
+        for k in range(len(problems)):
+            np.testing.assert_array_equal(bt.tableau(k), refs[k].T)
