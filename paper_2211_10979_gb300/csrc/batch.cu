@@ -136,17 +136,18 @@ void lp_batch_destroy(lp_batch_t h) {
     bdev_free(h, h->work);
     bdev_free(h, h->inputs);
     if (h->stream) cudaStreamSynchronize(h->stream);
+    // the side streams' work was joined into h->stream: all of it is done
     for (int k = 0; k < kClasses; ++k) {
-        if (h->side[k]) cudaStreamDestroy(h->side[k]);
-        if (h->join[k]) cudaEventDestroy(h->join[k]);
+        stream_put(h->side[k]);
+        event_put(h->join[k], false);
     }
-    if (h->fork) cudaEventDestroy(h->fork);
-    if (h->e_in) cudaEventDestroy(h->e_in);
-    if (h->e_out) cudaEventDestroy(h->e_out);
-    if (h->cap) cudaStreamDestroy(h->cap);
-    if (h->ev0) cudaEventDestroy(h->ev0);
-    if (h->ev1) cudaEventDestroy(h->ev1);
-    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    event_put(h->fork, false);
+    event_put(h->e_in, false);
+    event_put(h->e_out, false);
+    stream_put(h->cap);
+    event_put(h->ev0, true);
+    event_put(h->ev1, true);
+    if (h->own_stream) stream_put(h->stream);
     delete h;
 }
 
@@ -244,7 +245,7 @@ static lp_batch* batch_common(int count, const int* m, const int* n, cudaStream_
         h->sum_t += (long long)(m[k] + 1) * L.ldc;
     }
     if (own_stream) {
-        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        if (!(h->stream = stream_get())) {
             set_error("lp_batch_create: cudaStreamCreate failed");
             delete h;
             return nullptr;
@@ -253,7 +254,7 @@ static lp_batch* batch_common(int count, const int* m, const int* n, cudaStream_
     } else {
         h->stream = stream;
     }
-    if (cudaEventCreate(&h->ev0) != cudaSuccess || cudaEventCreate(&h->ev1) != cudaSuccess) {
+    if (!(h->ev0 = event_get(true)) || !(h->ev1 = event_get(true))) {
         set_error("lp_batch_create: event creation failed");
         lp_batch_destroy(h);
         return nullptr;
@@ -421,13 +422,9 @@ static cudaError_t launch_class_nt(lp_batch* h, const BatchParams& P, int q, int
 // Streams and events of the graph path, created on its first use.
 static bool ensure_graph_streams(lp_batch* h) {
     if (h->cap) return true;
-    bool ok = cudaEventCreateWithFlags(&h->fork, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&h->e_in, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&h->e_out, cudaEventDisableTiming) == cudaSuccess;
-    for (int q = 0; q < kClasses; ++q)
-        ok = ok && cudaStreamCreateWithFlags(&h->side[q], cudaStreamNonBlocking) == cudaSuccess &&
-             cudaEventCreateWithFlags(&h->join[q], cudaEventDisableTiming) == cudaSuccess;
-    ok = ok && cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) == cudaSuccess;
+    bool ok = (h->fork = event_get(false)) && (h->e_in = event_get(false)) && (h->e_out = event_get(false));
+    for (int q = 0; q < kClasses; ++q) ok = ok && (h->side[q] = stream_get()) && (h->join[q] = event_get(false));
+    ok = ok && (h->cap = stream_get());
     return ok;
 }
 

@@ -147,6 +147,80 @@ struct lp_handle {
     lp_stats stats{};
 };
 
+namespace {
+struct Recycled {
+    std::mutex mu;
+    std::vector<cudaEvent_t> ev[2];   // [0] timing disabled, [1] timing
+    std::vector<cudaStream_t> st;
+};
+constexpr int kMaxRecycleDevices = 64;
+Recycled& recycled(int dev) {
+    static Recycled r[kMaxRecycleDevices];
+    return r[dev];
+}
+int current_device_index() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxRecycleDevices) return -1;
+    return dev;
+}
+}  // namespace
+
+cudaEvent_t tsx::event_get(bool timing) {
+    const int dev = current_device_index();
+    if (dev >= 0) {
+        Recycled& r = recycled(dev);
+        std::lock_guard<std::mutex> lk(r.mu);
+        if (!r.ev[timing].empty()) {
+            cudaEvent_t e = r.ev[timing].back();
+            r.ev[timing].pop_back();
+            return e;
+        }
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, timing ? cudaEventDefault : cudaEventDisableTiming) != cudaSuccess) return nullptr;
+    return e;
+}
+
+void tsx::event_put(cudaEvent_t e, bool timing) {
+    if (!e) return;
+    const int dev = current_device_index();
+    if (dev < 0) {
+        cudaEventDestroy(e);
+        return;
+    }
+    Recycled& r = recycled(dev);
+    std::lock_guard<std::mutex> lk(r.mu);
+    r.ev[timing].push_back(e);
+}
+
+cudaStream_t tsx::stream_get() {
+    const int dev = current_device_index();
+    if (dev >= 0) {
+        Recycled& r = recycled(dev);
+        std::lock_guard<std::mutex> lk(r.mu);
+        if (!r.st.empty()) {
+            cudaStream_t s = r.st.back();
+            r.st.pop_back();
+            return s;
+        }
+    }
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    return s;
+}
+
+void tsx::stream_put(cudaStream_t s) {
+    if (!s) return;
+    const int dev = current_device_index();
+    if (dev < 0) {
+        cudaStreamDestroy(s);
+        return;
+    }
+    Recycled& r = recycled(dev);
+    std::lock_guard<std::mutex> lk(r.mu);
+    r.st.push_back(s);
+}
+
 cudaError_t tsx::pool_alloc(void** ptr, size_t bytes, cudaStream_t stream) {
     constexpr int kMaxPoolDevices = 64;
     static std::mutex mu;
@@ -259,10 +333,9 @@ static void destroy_impl(lp_handle* h) {
     dev_free(h, h->common);
     dev_free(h, h->inputs);
     if (h->stream) cudaStreamSynchronize(h->stream);
-    for (auto& e : h->ev)
-        if (e) cudaEventDestroy(e);
-    if (h->ready) cudaEventDestroy(h->ready);
-    if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    for (auto& e : h->ev) event_put(e, true);
+    event_put(h->ready, false);
+    if (h->own_stream && h->stream) stream_put(h->stream);
     delete h;
 }
 
@@ -272,7 +345,7 @@ void lp_destroy(lp_t h) { destroy_impl(h); }
 // destroys many handles; most never time anything).
 static bool ensure_events(lp_handle* h) {
     for (auto& e : h->ev)
-        if (!e && cudaEventCreate(&e) != cudaSuccess) {
+        if (!e && !(e = event_get(true))) {
             set_error("cudaEventCreate failed: %s", cudaGetErrorString(cudaGetLastError()));
             return false;
         }
@@ -296,7 +369,7 @@ static lp_handle* create_common(int m, int n, cudaStream_t stream, bool own_stre
     cudaGetDevice(&h->device);
     current_allocator(&h->alloc, &h->dealloc, &h->alloc_ctx);
     if (own_stream) {
-        if (cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking) != cudaSuccess) {
+        if (!(h->stream = stream_get())) {
             set_error("lp_create: cudaStreamCreate failed: %s", cudaGetErrorString(cudaGetLastError()));
             delete h;
             return nullptr;
@@ -305,7 +378,7 @@ static lp_handle* create_common(int m, int n, cudaStream_t stream, bool own_stre
     } else {
         h->stream = stream;
     }
-    const bool ok = cudaEventCreateWithFlags(&h->ready, cudaEventDisableTiming) == cudaSuccess;
+    const bool ok = (h->ready = event_get(false)) != nullptr;
     if (!ok) {
         set_error("lp_create: cudaEventCreate failed");
         destroy_impl(h);
@@ -1301,14 +1374,14 @@ static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, 
         for (int k = 0; k < nthreads; ++k)
             th.emplace_back([&, k] {
                 cudaSetDevice(device);
-                cudaStream_t ss = nullptr;
-                if (cudaStreamCreateWithFlags(&ss, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaStream_t ss = stream_get();
+                if (!ss) {
                     fail[k] = LP_ERR_CUDA;
                     return;
                 }
                 fail[k] = finish(k, ss);
                 cudaStreamSynchronize(ss);
-                cudaStreamDestroy(ss);
+                stream_put(ss);
             });
         for (auto& t : th) t.join();
     }

@@ -27,6 +27,16 @@ void use_default_allocator(bool on);
 // mapping it again made each new handle of a busy server cost ~0.5 ms).
 cudaError_t pool_alloc(void** ptr, size_t bytes, cudaStream_t stream);
 
+// Events and non-blocking streams of the current device, recycled through
+// per-device free lists instead of created and destroyed per handle: with
+// eight server threads calling the runtime, cudaEventCreate took ~30 us and
+// cudaEventDestroy ~58 us a call (0.2 us on one thread).  A stream must be
+// idle when it is put back; a recycled event is recorded before it is used.
+cudaEvent_t event_get(bool timing);
+void event_put(cudaEvent_t e, bool timing);
+cudaStream_t stream_get();
+void stream_put(cudaStream_t s);
+
 // Shared-memory bytes the batched solver has for one LP on the current device,
 // and whether an m x n LP fits in them.
 size_t batch_smem_limit();
