@@ -27,7 +27,12 @@
  * Device memory comes from the allocator installed with lp_set_allocator()
  * (default: stream-ordered allocation on the handle's stream from a memory
  * pool per device that the library creates and that keeps freed memory for
- * reuse until the process exits).
+ * reuse until the process exits).  CUDA events and non-blocking streams that
+ * handles no longer need are kept for reuse as well (their creation and
+ * destruction serialise concurrent callers in the CUDA runtime).  The pool,
+ * the events and the streams belong to the device's primary context:
+ * resetting the device (cudaDeviceReset) while the library holds them makes
+ * later calls fail with LP_ERR_CUDA.
  */
 #ifndef TABSIMPLEX_H
 #define TABSIMPLEX_H
