@@ -172,6 +172,10 @@ __device__ __forceinline__ void st_release(unsigned* p, unsigned v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+__device__ __forceinline__ void red_add_release(unsigned* p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned* p, unsigned v) {
     unsigned old;
     asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;"
@@ -382,6 +386,7 @@ struct BlockScratch {
     ArgPart arg_out;
     RatPart rat_out;
     int ok;
+    unsigned passed;   // counted grid barriers this block has passed (thread 0)
 };
 
 // Block-wide reductions; every thread returns the block result.
@@ -456,6 +461,51 @@ __device__ inline bool grid_barrier(DevState* st, long long timeout_ns, BlockScr
     }
     __syncthreads();
     return s.ok != 0;
+}
+
+#ifndef TSX_BARRIER_COUNT
+#define TSX_BARRIER_COUNT 1   // counted barriers in the pivot and team kernels
+#endif
+
+// Counted grid barrier (the pivot kernel): the arrival counter only grows
+// within a launch (it starts at 0: the state block is reset before every
+// launch); thread 0 of each block adds 1 with release semantics and no
+// returned value, then waits until the counter reaches (barriers passed + 1)
+// x G.  One L2 round trip less than the generation barrier above (no read
+// of the generation, no returning atomic before the release).  The 32-bit
+// counter may wrap: blocks are at most one barrier apart, so the signed
+// difference decides.  Bounded and failing exactly like grid_barrier.
+__device__ inline bool grid_barrier_counted(DevState* st, long long timeout_ns, BlockScratch& s) {
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        const unsigned target = (s.passed + 1u) * gridDim.x;
+        red_add_release(&st->bar_count, 1u);
+        const long long t0 = global_ns();
+        const unsigned long long max_spins = (unsigned long long)(timeout_ns > 0 ? timeout_ns : 0) + 4096ull;
+        unsigned long long spins = 0;
+        while ((int)(ld_acquire(&st->bar_count) - target) < 0) {
+            ++spins;
+            if ((spins & 31ull) == 1) {
+                if (ld_relaxed(&st->status) < 0) { ok = 0; break; }
+                if (global_ns() - t0 >= timeout_ns || spins > max_spins) {
+                    atomicCAS(&st->status, kRunning, kTimeout);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        s.passed += 1u;
+        __threadfence();
+        s.ok = ok;
+    }
+    __syncthreads();
+    return s.ok != 0;
+}
+
+__device__ __forceinline__ bool pivot_barrier(DevState* st, long long timeout_ns, BlockScratch& s) {
+    return TSX_BARRIER_COUNT ? grid_barrier_counted(st, timeout_ns, s) : grid_barrier(st, timeout_ns, s);
 }
 
 // ------------------------------------------------------------------ phases

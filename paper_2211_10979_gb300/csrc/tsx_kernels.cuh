@@ -172,9 +172,10 @@ __global__ void __launch_bounds__(NT, persistent_sm_threads(NT) / NT) k_pivot_pe
     TmaRing<(tma_stages(NT) >= 2 ? tma_stages(NT) : 2)> ring;
     auto* ringp = tma_stages(NT) >= 2 ? &ring : nullptr;
     if constexpr (tma_stages(NT) >= 2) ring = tma_ring_init<NT>(tsx_dyn);
+    if (threadIdx.x == 0) s.passed = 0;
     clk.start();
     phase_init_argmin(P);
-    if (!grid_barrier(P.st, P.timeout_ns, s)) return;
+    if (!pivot_barrier(P.st, P.timeout_ns, s)) return;
     long long it = 0;
     int bland = P.rule == 1 ? 1 : 0;
     int degen = 0;
@@ -187,7 +188,7 @@ __global__ void __launch_bounds__(NT, persistent_sm_threads(NT) / NT) k_pivot_pe
         if (it >= P.max_iters) { finish(P, kIterLimit, it, bland, degen, clk.acc); return; }
         phase_ratio(P, q, bland, s);                      // Step 2 (block partials)
         clk.lap(0);
-        if (!grid_barrier(P.st, P.timeout_ns, s)) return;
+        if (!pivot_barrier(P.st, P.timeout_ns, s)) return;
         clk.lap(3);
         const RatPart l = phase_leaving(P, s);            // Step 2 (global)
         if (l.i == INT_MAX) { finish(P, kUnbounded, it, bland, degen, clk.acc); return; }
@@ -196,13 +197,13 @@ __global__ void __launch_bounds__(NT, persistent_sm_threads(NT) / NT) k_pivot_pe
         phase_stage_row(P, l.i, q, piv);                  // Step 3 (pivot row)
         if (blockIdx.x == 0 && threadIdx.x == 0) record_pivot(P, it, q, qv, l.i);
         clk.lap(1);
-        if (!grid_barrier(P.st, P.timeout_ns, s)) return;
+        if (!pivot_barrier(P.st, P.timeout_ns, s)) return;
         clk.lap(4);
         phase_update<V, persistent_rows(NT)>(P, l.i, q, it, ringp);   // Step 3 (rank-1 update)
         ++it;
         degeneracy_step(P, l.r, bland, degen);
         clk.lap(2);
-        if (!grid_barrier(P.st, P.timeout_ns, s)) return;
+        if (!pivot_barrier(P.st, P.timeout_ns, s)) return;
         clk.lap(5);
     }
 }

@@ -72,21 +72,36 @@ struct TeamParams {
 // Barrier of the C blocks of one team; bounded like grid_barrier.  Returns
 // false (in every thread) if the wait ran out or another block of the team
 // gave up.
-__device__ inline bool team_barrier(TeamState* ts, unsigned C, long long timeout_ns, int& sok) {
+// With TSX_BARRIER_COUNT the arrival counter only grows within a launch (the
+// team states are zeroed before it): a block adds 1 (release, no returned
+// value) and waits for (barriers passed + 1) x C, `passed` counting its own
+// barriers; otherwise the last arrival resets the counter and bumps a
+// generation word.
+__device__ inline bool team_barrier(TeamState* ts, unsigned C, long long timeout_ns, int& sok, unsigned& passed) {
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = 1;
-        const unsigned gen = ld_acquire(&ts->bar_gen);
-        const unsigned arrived = atom_add_acq_rel(&ts->bar_count, 1u);
-        if (arrived == C - 1) {
-            ts->bar_count = 0;
-            st_release(&ts->bar_gen, gen + 1);
+        bool done = false;
+        unsigned gen = 0, target = 0;
+        if (TSX_BARRIER_COUNT) {
+            target = (passed + 1u) * C;
+            red_add_release(&ts->bar_count, 1u);
         } else {
+            gen = ld_acquire(&ts->bar_gen);
+            const unsigned arrived = atom_add_acq_rel(&ts->bar_count, 1u);
+            if (arrived == C - 1) {
+                ts->bar_count = 0;
+                st_release(&ts->bar_gen, gen + 1);
+                done = true;
+            }
+        }
+        if (!done) {
             const long long t0 = global_ns();
             const unsigned long long max_spins = (unsigned long long)(timeout_ns > 0 ? timeout_ns : 0) + 4096ull;
             unsigned long long spins = 0;
-            while (ld_acquire(&ts->bar_gen) == gen) {
+            while (TSX_BARRIER_COUNT ? (int)(ld_acquire(&ts->bar_count) - target) < 0
+                                     : ld_acquire(&ts->bar_gen) == gen) {
                 ++spins;
                 if ((spins & 31ull) == 1) {
                     if (ld_relaxed(&ts->fail) != 0) { ok = 0; break; }
@@ -98,6 +113,7 @@ __device__ inline bool team_barrier(TeamState* ts, unsigned C, long long timeout
                 }
             }
         }
+        passed += 1u;
         __threadfence();
         sok = ok;
     }
@@ -216,14 +232,14 @@ __device__ void team_update(const TeamJob<V>& J, const V* R, const V* Floc, int 
 // Solves one LP with the team of C blocks; false if a team barrier failed.
 template <int RF, typename V>
 __device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, TeamState* ts, int bt, unsigned C,
-                               V* R, V* Floc, BlockScratch& s, int& sok) {
+                               V* R, V* Floc, BlockScratch& s, int& sok, unsigned& tpass) {
     const int m = J.m, n = J.n, ld = J.ld;
     int r0, r1;
     team_rows(m, (int)C, bt, r0, r1);
     team_build(J, r0, r1, bt, ts);
     __syncthreads();
     if (bt == 0) team_row0(J, (const V*)nullptr, V(0), -1, P, ts, s);   // Step 1 of the first pivot
-    if (!team_barrier(ts, C, P.timeout_ns, sok)) return false;
+    if (!team_barrier(ts, C, P.timeout_ns, sok, tpass)) return false;
     const long long cap = P.max_iters < 0 ? 50LL * ((long long)m + n) : P.max_iters;
     long long it = 0;
     int bland = P.rule == 1, degen = 0;
@@ -254,7 +270,7 @@ __device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, Team
         }
         best = block_rat(best, s);
         if (threadIdx.x == 0) store_rat(&ts->rat[bt], best);
-        if (!team_barrier(ts, C, P.timeout_ns, sok)) return false;
+        if (!team_barrier(ts, C, P.timeout_ns, sok, tpass)) return false;
         RatPart l = rat_none();
         if (threadIdx.x < (int)C) l = load_rat(&ts->rat[threadIdx.x]);
         l = block_rat(l, s);
@@ -283,7 +299,7 @@ __device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, Team
         if (bt == 0) team_row0(J, R, Floc[0], q, P, ts, s);   // the next Step 1 on the new row 0
         team_update<V, RF>(J, R, Floc, r0, lo, r1, p, q);
         ++it;
-        if (!team_barrier(ts, C, P.timeout_ns, sok)) return false;
+        if (!team_barrier(ts, C, P.timeout_ns, sok, tpass)) return false;
         if (p >= r0 && p < r1) {   // every block has read row p: its owner stores R there
             for (int j = threadIdx.x; j < ld; j += blockDim.x) J.T[(size_t)p * (size_t)ld + j] = R[j];
             __syncthreads();
@@ -292,7 +308,7 @@ __device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, Team
     // commit: the status is written only once every block of the team has
     // finished its part (a block that gave up at a barrier never gets here,
     // and the LP stays unfinished)
-    if (!team_barrier(ts, C, P.timeout_ns, sok)) return false;
+    if (!team_barrier(ts, C, P.timeout_ns, sok, tpass)) return false;
     if (bt == 0 && threadIdx.x == 0) {
         J.st->status = status;
         J.st->iters = it;
@@ -311,6 +327,8 @@ __global__ void __launch_bounds__(NT, team_sm_threads(NT) / NT) k_team_solve(Tea
     extern __shared__ __align__(32) unsigned char team_smem[];
     __shared__ BlockScratch s;
     __shared__ int sok;
+    __shared__ unsigned tpass;   // counted team barriers passed (thread 0)
+    if (threadIdx.x == 0) tpass = 0;
     const int t = P.team_of[blockIdx.x];
     const int bt = blockIdx.x - P.first[t];
     const unsigned C = (unsigned)P.size[t];
@@ -329,11 +347,11 @@ __global__ void __launch_bounds__(NT, team_sm_threads(NT) / NT) k_team_solve(Tea
             }
             ts->job = k;
         }
-        if (!team_barrier(ts, C, P.timeout_ns, sok)) return;
+        if (!team_barrier(ts, C, P.timeout_ns, sok, tpass)) return;
         const int k = *(volatile const int*)&ts->job;
         if (k < 0) return;
         const TeamJob<V> J = P.jobs[k];
-        if (!team_solve_one<team_rows_in_flight(NT)>(P, J, ts, bt, C, R, Floc, s, sok)) return;
+        if (!team_solve_one<team_rows_in_flight(NT)>(P, J, ts, bt, C, R, Floc, s, sok, tpass)) return;
     }
 }
 
