@@ -81,7 +81,13 @@ def parse_args(argv=None):
                     help="fp32: float tableau for every pivot + FP64 recovery on the GPU")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    return ap.parse_args(argv)
+    args = ap.parse_args(argv)
+    if args.precision == "fp32" and args.max_iters >= 0:
+        # the FP32 path treats a pivot cap as the end of its float phase and
+        # lets the FP64 cleanup finish the solve: a truncated FP32 solve is not
+        # a fixed amount of work
+        ap.error("--max-iters applies to FP64 solves only")
+    return args
 
 
 # ------------------------------------------------------------------ ranks

@@ -66,3 +66,12 @@ def test_reference_arm_other_ranks_exit_without_work(capsys):
     args = bench.parse_args(["--impl", "reference", "--steps", "1", "--warmup", "0"])
     assert bench.run_reference(args, rank=1, world=2) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_truncated_fp32_solves_are_refused():
+    # the FP32 path finishes a capped float phase with FP64 cleanup pivots, so
+    # a pivot cap does not bound its work
+    import bench
+    with pytest.raises(SystemExit):
+        bench.parse_args(["--precision", "fp32", "--max-iters", "5"])
+    assert bench.parse_args(["--max-iters", "5"]).max_iters == 5
