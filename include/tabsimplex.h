@@ -456,6 +456,19 @@ void lps_close(lps_t sv);
 lp_status lp_generate_dense(int m, int n, unsigned long long seed, double *dA, double *db,
                             double *dc, void *stream);
 
+/* Measurement helper, not part of the method: the device's FP64 fused
+ * multiply-add rate, the ceiling of kernels bound by the FP64 pipe (the
+ * batched solver).  One launch of `blocks` x `threads` threads (threads a
+ * multiple of 32, at most 1024), each running 8 independent chains of
+ * `iters` dependent fma(a, x, y) on the current device, on `stream`
+ * (cudaStream_t, NULL = legacy default stream).  Blocks until done; *ms_out
+ * receives the launch's CUDA-event time and *fma_per_s_out the rate
+ * (blocks x threads x 8 x iters / time), both HOST pointers, may be NULL.
+ * Allocates blocks x threads doubles of device memory for the chains' results
+ * for the duration of the call. */
+lp_status lp_measure_fp64_fma_rate(int blocks, int threads, long long iters, void *stream,
+                                   double *ms_out, double *fma_per_s_out);
+
 /* Solve without allocating any device memory.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory
  * themselves or let the library do it -- for example a plugin running inside
@@ -463,8 +476,8 @@ lp_status lp_generate_dense(int m, int n, unsigned long long seed, double *dA, d
  * latency-sensitive loop that must not call cudaMalloc/cudaFree, which can
  * block on or synchronise with other work on the device.
  *
- * Same computation as lp_create_device + lp_solve (tableau build from the
- * slack basis, then Steps 1-3 until termination), with every buffer supplied by
+ * It takes the same pivots and gives the same results as lp_create_device
+ * followed by lp_solve with the same options, with every buffer supplied by
  * the caller and the work buffers (pivot column, scaled pivot row, reduction
  * partials, status and barrier words) taken from one fixed array that the
  * library holds in device global memory: LP_NOALLOC_SCRATCH_BYTES (2 MiB) on
@@ -472,14 +485,15 @@ lp_status lp_generate_dense(int m, int n, unsigned long long seed, double *dA, d
  *   dA, db, dc  device inputs (m x n row-major, m, n float64), read only;
  *               every entry finite and b >= 0, else LP_ERR_INVALID
  *   dT          device output, (m + 1) x ld float64, 32-byte aligned; receives
- *               the final tableau (rows: objective, constraints 1..m; columns:
- *               x_1..x_n, slacks, right-hand side at n + m, zeros after)
+ *               the final tableau with every column, basic ones included (rows:
+ *               objective, then constraints 1..m; columns: x_1..x_n, the m
+ *               slacks, the right-hand side at n + m, zeros after)
  *   ld          leading dimension of dT in elements: >= n + m + 1, multiple of 4
  *   dbasis      device output, m ints: variable basic in constraint row i + 1
  *   opt         options as for lp_solve (NULL = defaults); opt->stream is the
  *               stream used; log_capacity must be 0 and blocks <= 1024
  *   iters       host output (may be NULL): pivots performed
- * The tableau is the full Table I layout (opt->layout is ignored).
+ * opt->layout is ignored: dT always holds every column, as described above.
  * The work buffers need 8 (m + 1) + 9 ld + 32 ceil(ld / 128) + 32 * 1024 bytes
  * plus about 1.5 KiB of alignment and state, at most LP_NOALLOC_SCRATCH_BYTES
  * (about m + ld <= 2.2e5, e.g. m = n = 70000); larger sizes return LP_ERR_INVALID

@@ -73,6 +73,13 @@ def _load():
         lib.orc_solve.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, ctypes.POINTER(_Opts),
                                   ctypes.POINTER(ctypes.c_long), ip, ip, ctypes.c_long]
         lib.orc_solve.restype = ctypes.c_int
+        lib.orc_solve_traced.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, ctypes.POINTER(_Opts),
+                                         ctypes.POINTER(ctypes.c_long), ip, ip, ctypes.c_long,
+                                         dp, dp, dp, dp]
+        lib.orc_solve_traced.restype = ctypes.c_int
+        lib.orc_pivot_gaps.argtypes = [ctypes.c_int, ctypes.c_int, dp, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_double, ctypes.c_double, dp, dp]
+        lib.orc_pivot_gaps.restype = None
         lib.orc_extract.argtypes = [ctypes.c_int, ctypes.c_int, dp, ip, dp, dp, dp]
         lib.orc_extract.restype = None
         fp = ctypes.POINTER(ctypes.c_float)
@@ -176,6 +183,52 @@ def solve_tableau(T, basis, m, n, opts: Options | None = None, log_cap: int = 1 
                            _ip(qlog), _ip(plog), cap)
     k = min(it.value, cap)
     return int(st), int(it.value), qlog[:k].copy(), plog[:k].copy()
+
+
+def pivot_gaps(T, m, n, q, p, eps_d=1e-9, eps_p=1e-9):
+    """Separation of the Step 1 and Step 2 decisions (q, p) on tableau T:
+    (second most negative candidate - T[0][q], second smallest eligible ratio -
+    ratio of row p), +inf where there is no second candidate."""
+    T = np.ascontiguousarray(T, dtype=np.float64)
+    dg, rg = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    _load().orc_pivot_gaps(m, n, _dp(T), q, p, eps_d, eps_p, ctypes.byref(dg), ctypes.byref(rg))
+    return dg.value, rg.value
+
+
+@dataclass
+class Trace:
+    """Per-pivot record of a traced solve: minimum ratio of Step 2, the
+    entering column's objective-row entry T[0][q], and the gaps of pivot_gaps
+    (NaN for pivots taken under Bland's rule)."""
+    theta: np.ndarray
+    dval: np.ndarray
+    dgap: np.ndarray
+    rgap: np.ndarray
+
+
+def solve_traced(A, b, c, opts: Options | None = None, log_cap: int = 1 << 20):
+    """solve() that also records, for every pivot, its minimum ratio and the
+    separation of its Step 1 and Step 2 decisions.  Returns (Result, Trace)."""
+    opts = opts or Options()
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    m, n = A.shape
+    T, basis = build_tableau(A, b, c)
+    cap = int(log_cap)
+    qlog = np.full(cap, -1, dtype=np.int32)
+    plog = np.full(cap, -1, dtype=np.int32)
+    theta = np.full(cap, np.nan)
+    dgap = np.full(cap, np.nan)
+    rgap = np.full(cap, np.nan)
+    dval = np.full(cap, np.nan)
+    it = ctypes.c_long(0)
+    o = opts.c()
+    st = _load().orc_solve_traced(m, n, _dp(T), _ip(basis), ctypes.byref(o), ctypes.byref(it),
+                                  _ip(qlog), _ip(plog), cap, _dp(dgap), _dp(rgap), _dp(theta),
+                                  _dp(dval))
+    k = min(it.value, cap)
+    x, y, obj = extract(T, basis, m, n)
+    res = Result(int(st), int(it.value), x, y, obj, basis, qlog[:k].copy(), plog[:k].copy(), T)
+    return res, Trace(theta[:k].copy(), dval[:k].copy(), dgap[:k].copy(), rgap[:k].copy())
 
 
 def extract(T, basis, m, n):

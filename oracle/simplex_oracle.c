@@ -169,12 +169,47 @@ void orc_pivot(int m, int n, double *T, int p, int q, double *r, double *f)
         TAB(T, W, p, j) = r[j];
 }
 
+/* Separation of the decisions of one Dantzig pivot (a check of the instance,
+ * not part of the method): with q and p chosen by Steps 1 and 2,
+ *   *dgap = (second most negative candidate T[0][j], j != q) - T[0][q],
+ *   *rgap = (second smallest eligible ratio, i != p) - ratio of row p,
+ * each +INFINITY when there is no second candidate.  A pivot whose gaps are
+ * positive would pick the same (q, p) under any order of the comparisons. */
+void orc_pivot_gaps(int m, int n, const double *T, int q, int p, double eps_d,
+                    double eps_p, double *dgap, double *rgap)
+{
+    const int W = n + m + 1;
+    const double vq = TAB(T, W, 0, q);
+    double second = INFINITY;
+    for (int j = 0; j < W - 1; ++j) {
+        double v = TAB(T, W, 0, j);
+        if (j != q && v < -eps_d && v < second)
+            second = v;
+    }
+    *dgap = second - vq;
+    const double rp = TAB(T, W, p, W - 1) / TAB(T, W, p, q);
+    second = INFINITY;
+    for (int i = 1; i <= m; ++i) {
+        double a = TAB(T, W, i, q);
+        if (i != p && a > eps_p) {
+            double r = TAB(T, W, i, W - 1) / a;
+            if (r < second)
+                second = r;
+        }
+    }
+    *rgap = second - rp;
+}
+
 /* Iterate/Finalization Step (Sec. III): Steps 1-3 until optimal or unbounded.
  * Runs on a tableau built by orc_build (or one already pivoted by an earlier
  * call; the degenerate-run state then starts from zero).  The i-th pivot's
- * (q, p) pair is written to qlog[i], plog[i] while i < log_cap. */
-int orc_solve(int m, int n, double *T, int *basis, const orc_options *opt,
-              long *iters_out, int *qlog, int *plog, long log_cap)
+ * (q, p) pair is written to qlog[i], plog[i] while i < log_cap; when
+ * dgap/rgap/thetalog/dval are not NULL, the pivot's minimum ratio, its
+ * objective-row entry T[0][q] and the gaps of orc_pivot_gaps (NAN for a pivot
+ * taken under Bland's rule) go there too. */
+int orc_solve_traced(int m, int n, double *T, int *basis, const orc_options *opt,
+                     long *iters_out, int *qlog, int *plog, long log_cap,
+                     double *dgap, double *rgap, double *thetalog, double *dval)
 {
     if (m <= 0 || n <= 0 || !T || !basis || !opt)
         return ORC_INVALID;
@@ -216,6 +251,18 @@ int orc_solve(int m, int n, double *T, int *basis, const orc_options *opt,
                 qlog[it] = q;
             if (plog)
                 plog[it] = p;
+            if (thetalog)
+                thetalog[it] = theta;
+            if (dval)
+                dval[it] = TAB(T, W, 0, q);
+            if (dgap && rgap) {
+                if (bland) {
+                    dgap[it] = NAN;
+                    rgap[it] = NAN;
+                } else {
+                    orc_pivot_gaps(m, n, T, q, p, opt->eps_d, opt->eps_p, &dgap[it], &rgap[it]);
+                }
+            }
         }
         orc_pivot(m, n, T, p, q, r, f);
         basis[p - 1] = q;
@@ -239,6 +286,13 @@ int orc_solve(int m, int n, double *T, int *basis, const orc_options *opt,
     if (iters_out)
         *iters_out = it;
     return status;
+}
+
+int orc_solve(int m, int n, double *T, int *basis, const orc_options *opt,
+              long *iters_out, int *qlog, int *plog, long log_cap)
+{
+    return orc_solve_traced(m, n, T, basis, opt, iters_out, qlog, plog, log_cap,
+                            NULL, NULL, NULL, NULL);
 }
 
 /* Read the solution out of a tableau (Sec. III, Table I layout): x_j is the

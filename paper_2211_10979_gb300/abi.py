@@ -30,7 +30,8 @@ EXPORTS = ("lp_options_init", "lp_create", "lp_create_device", "lp_solve", "lp_g
            "lp_batch_create", "lp_batch_create_device", "lp_batch_solve", "lp_batch_get",
            "lp_batch_get_tableau", "lp_batch_get_stats", "lp_batch_destroy", "lps_options_init",
            "lps_open", "lps_submit", "lps_submit_device", "lps_wait", "lps_result", "lps_release",
-           "lps_get_stats", "lps_last_error", "lps_close", "lp_generate_dense")
+           "lps_get_stats", "lps_last_error", "lps_close", "lp_generate_dense",
+           "lp_measure_fp64_fma_rate")
 LP_PENDING = 100
 
 # capacity of the library's fixed work-buffer array used by lp_solve_noalloc
@@ -222,6 +223,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "lps_last_error": (ctypes.c_char_p, [vp]),
             "lps_close": (None, [vp]),
             "lp_generate_dense": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_ulonglong, vp, vp, vp, vp]),
+            "lp_measure_fp64_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, vp,
+                                                        ctypes.POINTER(ctypes.c_double),
+                                                        ctypes.POINTER(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -325,7 +329,26 @@ def lp_solve_noalloc(m: int, n: int, dA, db, dc, dT, ld: int, dbasis,
     """Solve into caller-owned device buffers without any device allocation.
 
     dA, db, dc: device inputs; dT: device (m+1) x ld float64 output; dbasis:
-    device int32 output (m).  Returns (status, iters)."""
+    device int32 output (m).  Returns (status, iters).  The C function cannot
+    see buffer sizes, so torch tensors are checked here first (CUDA, dtype,
+    contiguous, large enough) and a mismatch raises ValueError before any
+    device work; plain integer addresses are passed through unchecked."""
+    need = (("dA", dA, "float64", int(m) * int(n)), ("db", db, "float64", int(m)),
+            ("dc", dc, "float64", int(n)), ("dT", dT, "float64", (int(m) + 1) * int(ld)),
+            ("dbasis", dbasis, "int32", int(m)))
+    for name, t, dtype, count in need:
+        if t is None or isinstance(t, int) or not hasattr(t, "is_cuda"):
+            if t is not None and not isinstance(t, int):
+                raise ValueError(f"lp_solve_noalloc: {name} must be a CUDA tensor or a device address")
+            continue
+        if not t.is_cuda:
+            raise ValueError(f"lp_solve_noalloc: {name} is not on a CUDA device")
+        if str(t.dtype) != f"torch.{dtype}":
+            raise ValueError(f"lp_solve_noalloc: {name} must be {dtype}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"lp_solve_noalloc: {name} must be contiguous")
+        if t.numel() < count:
+            raise ValueError(f"lp_solve_noalloc: {name} holds {t.numel()} elements, needs {count}")
     it = ctypes.c_longlong(0)
     st = load().lp_solve_noalloc(int(m), int(n), _ptr(dA), _ptr(db), _ptr(dc), _ptr(dT), int(ld),
                                  _ptr(dbasis), ctypes.byref(opts) if opts is not None else None,
@@ -440,6 +463,17 @@ def lps_last_error(sv: int) -> str:
 def lps_close(sv: int) -> None:
     if sv:
         load().lps_close(sv)
+
+
+def lp_measure_fp64_fma_rate(blocks: int, threads: int, iters: int, stream=None):
+    """Measurement helper: (launch ms, FP64 fma per second) of a DFMA-chain
+    kernel on the current device."""
+    ms, rate = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = load().lp_measure_fp64_fma_rate(int(blocks), int(threads), int(iters), stream,
+                                         ctypes.byref(ms), ctypes.byref(rate))
+    if st != 0:
+        raise RuntimeError(lp_last_error())
+    return ms.value, rate.value
 
 
 def lp_generate_dense(m: int, n: int, seed: int, dA, db, dc, stream=None) -> int:

@@ -18,7 +18,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB = os.path.join(PKG, "libtabsimplex.so")
-SOURCES = ["tabsimplex.cu", "batch.cu", "server.cu"]
+SOURCES = ["tabsimplex.cu", "batch.cu", "server.cu", "measure.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-fvisibility=default", "-shared"]

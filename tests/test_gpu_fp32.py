@@ -137,23 +137,37 @@ def test_golden_traces_and_special_cases(tsx, golden_dir):
 
 def test_fp32_full_size_16384(tsx):
     # the precision workload: m = n = 16384, float tableau (2.1 GB) for every
-    # pivot, FP64 recovery; checked by certificates and against the FP64 path
+    # pivot, FP64 recovery; checked against the FP64 oracle's whole solve
+    # (tests/golden/full_size, written by the oracle alone) and by certificates.
+    # The FP64 path on the same LP must equal that oracle run exactly.
     import torch
+    from test_gpu_full_size import load_golden
     m = n = 16384
+    g = load_golden(m, n, 1)
     A, b, c = lpgen.dense_lp(m, n, 1)
+    assert lpgen.lp_digest(A, b, c) == g["lp_sha256"]
     dA, db, dc = (torch.from_numpy(v).cuda() for v in (A, b, c))
     s = torch.cuda.current_stream().cuda_stream
     with tsx.Problem(dA, db, dc, device=True, stream=s) as pr:
         assert pr.solve(tsx.options(stream=s, precision=tsx.LP_PREC_FP32)) == tsx.LP_OPTIMAL
         sol32 = pr.solution()
         st32 = pr.stats()
-        assert pr.solve(tsx.options(stream=s)) == tsx.LP_OPTIMAL
+        assert pr.solve(tsx.options(stream=s, log_capacity=1 << 16)) == tsx.LP_OPTIMAL
         sol64 = pr.solution()
-    assert abs(sol32.obj - sol64.obj) <= 1e-9 * abs(sol64.obj)
+        q, p = (v.tolist() for v in pr.pivot_log(1 << 16))
+    ref_obj = g["obj_value"]
+    assert abs(sol32.obj - ref_obj) <= 1e-9 * abs(ref_obj)
+    assert np.abs(sol32.x - g["x"]).max() <= 1e-9 * max(1.0, float(np.abs(g["x"]).max()))
+    assert np.abs(sol32.y - g["y"]).max() <= 1e-9 * max(1.0, float(np.abs(g["y"]).max()))
     pv, dv = _violations(A, b, c, sol32.x, sol32.y)
     assert pv <= 1e-9 and dv <= 1e-9
-    assert abs(c @ sol32.x - b @ sol32.y) <= 1e-9 * abs(sol64.obj)
+    assert abs(c @ sol32.x - b @ sol32.y) <= 1e-9 * abs(ref_obj)
     assert st32["primal_violation"] <= 1e-9 and st32["dual_violation"] <= 1e-9
+    # the FP64 path: the oracle's run, pivot for pivot
+    assert sol64.iters == g["iters"] and q == g["qlog"] and p == g["plog"]
+    assert sol64.obj == ref_obj
+    np.testing.assert_array_equal(sol64.x, g["x"])
+    np.testing.assert_array_equal(sol64.y, g["y"])
 
 
 @pytest.mark.parametrize("path", [1, 2])

@@ -2,14 +2,21 @@
 times (persistent kernel, default grid and block, zero-column skipping on).
 
 The oracle cannot finish a whole 8192 x 8192 solve in test time (~2800 pivots
-at ~15 pivots/s), so the checks are:
+at ~15 pivots/s), so the whole solves are compared with goldens that
+tests/golden/make_full_size.py wrote by running the oracle to completion
+(tests/golden/full_size/*.json; its seeds are checked there to be
+non-degenerate, so the exact pivot sequence is expected):
+  - whole solves: status, pivot count, every (q, p) pair, the final basis, and
+    x, y and the objective, all at tolerance 0 (both device layouts at 8192^2);
   - the first K pivots: the GPU tableau after K pivots equals the oracle's
-    after K pivots, entry by entry (tolerance 0), and so do the (q, p) pairs;
-  - the full solve: properties that hold at any size -- the basic columns are
-    exact unit vectors, x and y satisfy primal and dual feasibility and strong
-    duality in FP64 within 1e-9 (relative), and the pivot log starts with the
-    oracle's K pivots.
+    after K pivots, entry by entry (tolerance 0);
+  - properties that hold at any size: the basic columns are exact unit
+    vectors, and x and y satisfy primal and dual feasibility and strong
+    duality in FP64 within 1e-9 (relative).
 """
+import json
+import os
+
 import numpy as np
 import pytest
 
@@ -19,6 +26,26 @@ import oracle
 pytestmark = pytest.mark.gpu
 
 K = 3
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full_size")
+
+
+def load_golden(m, n, seed):
+    """Oracle record of the whole solve of lpgen.dense_lp(m, n, seed)."""
+    with open(os.path.join(GOLDEN, f"{m}x{n}_seed{seed}.json")) as fh:
+        g = json.load(fh)
+    g["obj_value"] = float.fromhex(g["obj"])
+    basis = n + np.arange(m, dtype=np.int64)
+    for i, v in g["basis_moved"]:
+        basis[i] = v
+    g["basis"] = basis
+    x = np.zeros(n)
+    for j, v in g["x_nonzero"]:
+        x[j] = float.fromhex(v)
+    y = np.zeros(m)
+    for i, v in g["y_nonzero"]:
+        y[i] = float.fromhex(v)
+    g["x"], g["y"] = x, y
+    return g
 
 
 @pytest.fixture(scope="module")
@@ -79,3 +106,34 @@ def test_full_size_first_pivots_and_certificates(tsx, m, n, layout):
     sub[rows, np.arange(m)] = 0.0
     assert not np.any(sub)
     _certificate(A, b, c, sol.x, sol.y, sol.obj)
+
+
+@pytest.mark.parametrize("m,n,seed,layout", [
+    (8192, 8192, 1, 0), (8192, 8192, 2, 0), (8192, 8192, 3, 0), (4096, 16384, 1, 0),
+    (8192, 8192, 1, 1), (8192, 8192, 2, 1),
+])
+def test_full_size_whole_solve_equals_oracle(tsx, m, n, seed, layout):
+    # the bench's workload (layout 0, seeds 1-3 and the aspect-ratio case) and
+    # the Table I layout, solved to the end and compared with the oracle's
+    # whole run at tolerance 0
+    import torch
+    g = load_golden(m, n, seed)
+    assert g["separation"]["non_degenerate"]
+    A, b, c = lpgen.dense_lp(m, n, seed)
+    assert lpgen.lp_digest(A, b, c) == g["lp_sha256"]
+    dA, db, dc = (torch.from_numpy(v).cuda() for v in (A, b, c))
+    s = torch.cuda.current_stream().cuda_stream
+    with tsx.Problem(dA, db, dc, device=True, stream=s) as pr:
+        st = pr.solve(tsx.options(stream=s, log_capacity=1 << 16, layout=layout))
+        assert tsx.STATUS_NAMES[st] == g["status"] == "OPTIMAL"
+        sol = pr.solution()
+        assert sol.iters == g["iters"]
+        q, p = (v.tolist() for v in pr.pivot_log(1 << 16))
+        assert len(q) == g["iters"]
+        first_bad = next((k for k in range(len(q)) if (q[k], p[k]) != (g["qlog"][k], g["plog"][k])), None)
+        assert first_bad is None, f"pivot {first_bad} differs"
+        assert pr.stats()["path"] == tsx.LP_PATH_PERSISTENT
+    np.testing.assert_array_equal(sol.basis, g["basis"])
+    assert sol.obj == g["obj_value"]
+    np.testing.assert_array_equal(sol.x, g["x"])
+    np.testing.assert_array_equal(sol.y, g["y"])

@@ -76,6 +76,47 @@ def test_step2_rules_on_hand_made_column():
     assert oracle.leaving(T, basis, 3, 1, 0)[0] == -1
 
 
+def test_pivot_gaps_on_hand_made_tableau():
+    # objective row [-1, -3, -2.5, 2 | 0] (m = 3, n = 1 plus slacks is not needed:
+    # the gaps only read row 0 and column q): Step 1 picks column 1 (-3); the
+    # next candidate is -2.5 -> gap 0.5.  Column 1 entries 2, 4, 1 with rhs
+    # 4, 10, 3 -> ratios 2, 2.5, 3: row 1 leaves, next ratio 2.5 -> gap 0.5.
+    T = np.zeros((4, 5))
+    T[0, :4] = [-1.0, -3.0, -2.5, 2.0]
+    T[1:, 1] = [2.0, 4.0, 1.0]
+    T[1:, 4] = [4.0, 10.0, 3.0]
+    assert oracle.entering(T, 3, 1) == 1
+    assert oracle.leaving(T, np.array([1, 2, 3], dtype=np.int32), 3, 1, 1) == (1, 2.0)
+    assert oracle.pivot_gaps(T, 3, 1, 1, 1) == (0.5, 0.5)
+    # a tie shows as a zero gap; a lone candidate as an infinite one
+    T[0, 2] = -3.0
+    T[2, 4] = 8.0
+    assert oracle.pivot_gaps(T, 3, 1, 1, 1) == (0.0, 0.0)
+    T[0, :4] = [0.0, -3.0, 0.0, 2.0]
+    T[2:, 1] = [0.0, -1.0]
+    assert oracle.pivot_gaps(T, 3, 1, 1, 1) == (np.inf, np.inf)
+
+
+def test_traced_solve_is_the_plain_solve_with_its_gaps():
+    A, b, c = lpgen.dense_lp(48, 40, 5)
+    r = oracle.solve(A, b, c)
+    rt, tr = oracle.solve_traced(A, b, c)
+    assert (rt.status, rt.iters, rt.obj) == (r.status, r.iters, r.obj)
+    assert rt.qlog.tolist() == r.qlog.tolist() and rt.plog.tolist() == r.plog.tolist()
+    np.testing.assert_array_equal(rt.T, r.T)
+    # replay pivot by pivot: each recorded gap, ratio and entry is the one of
+    # that pivot's tableau
+    m, n = A.shape
+    T, basis = oracle.build_tableau(A, b, c)
+    for k, (q, p) in enumerate(zip(r.qlog.tolist(), r.plog.tolist())):
+        assert tr.dval[k] == T[0, q]
+        assert tr.theta[k] == oracle.leaving(T, basis, m, n, q)[1]
+        assert (tr.dgap[k], tr.rgap[k]) == oracle.pivot_gaps(T, m, n, q, p)
+        assert tr.dgap[k] > 0 and tr.rgap[k] > 0
+        oracle.pivot(T, m, n, p, q)
+        basis[p - 1] = q
+
+
 # ------------------------------------------------------------- brute force
 def _vertex_max(A, b, c):
     """max c.x over {Ax <= b, x >= 0} by enumerating every choice of n tight

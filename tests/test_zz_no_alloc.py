@@ -58,6 +58,71 @@ def test_noalloc_matches_allocating_path_twice_in_a_row(env):
         np.testing.assert_array_equal(dbasis.cpu().numpy(), rbasis)
 
 
+def test_noalloc_call_allocates_nothing(env):
+    # the property the entry point exists for: after a first call (which looks
+    # up the fixed array's address once), a call leaves the device's free
+    # memory unchanged and never reaches the library's allocator
+    import ctypes
+    torch, tsx = env
+    stream = torch.cuda.current_stream().cuda_stream
+    m, n = 300, 200
+    A, b, c = lpgen.dense_lp(m, n, 7)
+    dA, db, dc = (torch.from_numpy(v).cuda() for v in (A, b, c))
+    ld = (n + m + 1 + 3) // 4 * 4
+    dT = torch.zeros((m + 1) * ld, dtype=torch.float64, device="cuda")
+    dbasis = torch.zeros(m, dtype=torch.int32, device="cuda")
+    opts = tsx.options(stream=stream)
+    assert tsx.lp_solve_noalloc(m, n, dA, db, dc, dT, ld, dbasis, opts)[0] == tsx.LP_OPTIMAL
+    calls = [0]
+
+    def count_alloc(nbytes, strm, ctx):
+        calls[0] += 1
+        return None
+
+    def count_free(ptr, nbytes, strm, ctx):
+        calls[0] += 1
+
+    alloc_cb, free_cb = tsx.abi.ALLOC_FN(count_alloc), tsx.abi.FREE_FN(count_free)
+    assert tsx.abi.lp_set_allocator(alloc_cb, free_cb) == 0
+    try:
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        st, _ = tsx.lp_solve_noalloc(m, n, dA, db, dc, dT, ld, dbasis, opts)
+        torch.cuda.synchronize()
+        free_after = torch.cuda.mem_get_info()[0]
+    finally:
+        # put back whatever was installed before (torch's hooks if an earlier
+        # test routed the library through torch, else the library default)
+        prev = tsx._torch_hooks
+        if prev is not None:
+            tsx.abi.lp_set_allocator(prev[0], prev[1])
+        else:
+            tsx.abi.lp_set_allocator(ctypes.cast(None, tsx.abi.ALLOC_FN),
+                                     ctypes.cast(None, tsx.abi.FREE_FN))
+    assert st == tsx.LP_OPTIMAL
+    assert calls[0] == 0
+    assert free_after == free_before
+
+
+def test_noalloc_binding_checks_tensors(env):
+    torch, tsx = env
+    m, n, ld = 4, 3, 8
+    ok = dict(dA=torch.zeros(m * n, dtype=torch.float64, device="cuda"),
+              db=torch.zeros(m, dtype=torch.float64, device="cuda"),
+              dc=torch.zeros(n, dtype=torch.float64, device="cuda"),
+              dT=torch.zeros((m + 1) * ld, dtype=torch.float64, device="cuda"),
+              dbasis=torch.zeros(m, dtype=torch.int32, device="cuda"))
+    bad = [("dT", torch.zeros((m + 1) * ld - 1, dtype=torch.float64, device="cuda")),
+           ("dbasis", torch.zeros(m, dtype=torch.int64, device="cuda")),
+           ("dA", torch.zeros(m * n, dtype=torch.float64)),
+           ("dc", torch.zeros(2 * n, dtype=torch.float64, device="cuda")[::2])]
+    for name, t in bad:
+        args = dict(ok, **{name: t})
+        with pytest.raises(ValueError, match=name):
+            tsx.lp_solve_noalloc(m, n, args["dA"], args["db"], args["dc"], args["dT"], ld,
+                                 args["dbasis"])
+
+
 def test_noalloc_per_phase_path_and_bland(env):
     torch, tsx = env
     A = np.array([[0.5, -5.5, -2.5, 9.0], [0.5, -1.5, -0.5, 1.0], [1.0, 0.0, 0.0, 0.0]])
