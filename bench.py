@@ -66,6 +66,8 @@ def parse_args(argv=None):
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="serve: length of the stream")
     ap.add_argument("--serve-workers", type=int, default=8)
+    ap.add_argument("--plain-seconds", type=float, default=5.0,
+                    help="serve: the plain path replays only this much of the stream")
     ap.add_argument("--serve-blocks", type=int, default=0, help="serve: grid cap per single-lane solve")
     ap.add_argument("--serve-team", type=int, default=0,
                     help="serve: blocks per team of the lp_solve_many waves (0 = library default, "
@@ -79,6 +81,9 @@ def parse_args(argv=None):
                     help="batch: threads per LP (32/64/128/256); 0 = autotuned per size class")
     ap.add_argument("--plain-sample", type=int, default=256,
                     help="LPs of the batch solved one at a time for the plain-path figure")
+    ap.add_argument("--generator", choices=["dense", "diag"], default="dense",
+                    help="single: lpgen.dense_lp (default) or lpgen.diag_dominant_lp (every "
+                         "structural ends basic: a k = m FP64 recovery)")
     ap.add_argument("--precision", choices=["fp64", "fp32"], default="fp64",
                     help="fp32: float tableau for every pivot + FP64 recovery on the GPU")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the oracle sample")
@@ -288,7 +293,8 @@ def run_gpu(args, rank, world, local):
         args.e2e_steps = 0
         args.no_cpu_baseline = True
     else:
-        host = {s: lpgen.dense_lp(m, n, s) for s in seeds}
+        gen = lpgen.diag_dominant_lp if args.generator == "diag" else lpgen.dense_lp
+        host = {s: gen(m, n, s) for s in seeds}
         resident = {s: tuple(torch.from_numpy(v).to(dev) for v in host[s]) for s in seeds}
     prec = tsx.LP_PREC_FP32 if args.precision == "fp32" else tsx.LP_PREC_FP64
     layout = tsx.LP_LAYOUT_FULL if args.layout == "full" else tsx.LP_LAYOUT_CONDENSED
@@ -431,12 +437,15 @@ def run_gpu(args, rank, world, local):
             "config": {
                 "workload": f"dense LP m={m} n={n} {args.precision.upper()}, "
                             + ("full solve" if args.max_iters < 0 else f"first {args.max_iters} pivots")
-                            + " per step (seeded A~U[1,10), b~U[100,1000), c~U[1,10); slack basis; Dantzig)",
+                            + (" per step (seeded A~U[1,10), b~U[100,1000), c~U[1,10); slack basis; Dantzig)"
+                               if args.generator == "dense" else
+                               " per step (seeded diagonally dominant A: A_ij~U[0,1), A_ii+=4max(m,n); "
+                               "b~U[100,1000), c~U[1,10); every structural ends basic)"),
                 "m": m, "n": n, "seeds_per_rank": len(seeds),
                 "pivots_per_step": pivots / args.steps,
                 "l2": f"inputs larger than L2 (tableau {(m + 1) * stats[0]['ld'] * elem / 1e9:.2f} GB)",
                 "layout": args.layout,
-                "path": {1: "persistent", 2: "multilaunch"}.get(stats[0]["path"]),
+                "path": {1: "persistent", 2: "multilaunch", 4: "cluster"}.get(stats[0]["path"]),
                 "grid": stats[0]["grid"], "block": stats[0]["block"],
                 "skip_zero_columns": args.skip_zero,
             },
@@ -463,6 +472,28 @@ def run_gpu(args, rank, world, local):
         if prec_info:
             line["precision"] = prec_info
             line["roofline"]["traffic"] = None
+        if stats[0]["path"] == 4:
+            # the cluster path keeps the tableau on chip: its ceiling is the
+            # FP64 pipes of the cluster's SMs, not HBM
+            nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+            csize = stats[0]["grid"]
+            peak_all, probe = fp64_fma_rate(tsx, sptr)
+            peak_c = peak_all * csize / nsm
+            flops = 2.0 * (m + 1) * (n + 1) * pivots / args.steps   # one fma per condensed entry
+            ach = flops / (kernel_ms / 1000.0) / 1e12
+            line["roofline"] = {
+                "bound": "alu", "achieved": ach, "peak": peak_c, "unit": "TFLOP/s", "frac": ach / peak_c,
+                "peak_source": f"measured FP64 fma rate of the whole GPU in this run ({peak_all:.3f} TFLOP/s, "
+                               f"lp_measure_fp64_fma_rate) x {csize}/{nsm} SMs of one cluster",
+                "frac_of_whole_gpu": ach / peak_all, "probe": probe, "traffic": None,
+                "kernel": "k_cluster_solve", "cluster_blocks": csize,
+                "flops_per_launch": flops, "kernel_ms_per_launch": kernel_ms,
+                "us_per_pivot": 1000.0 * kernel_ms * args.steps / max(1, pivots),
+                "phase_us_per_pivot": dict(zip(
+                    ["step2", "wait_barrier1", "minimum_and_R", "wait_barrier2", "step3", "step1"],
+                    [round(1000.0 * sum(st["phase_ms"][k] for st in stats) / max(1, pivots), 3)
+                     for k in range(6)])),
+            }
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()
@@ -780,15 +811,28 @@ def run_many(args, rank, world, local):
 
 def play_stream(tsx, torch, dev, shapes, arrivals, seeds, server_kw):
     """Submits each request at its arrival time (inputs generated on the device
-    just before), waits for all, returns per-request (status, latency s, obj)
-    and the server's statistics.  Latency runs from the scheduled arrival."""
+    just before), collects every result, returns per-request (status, latency
+    s, obj, done time) in submission order and the server's statistics.
+    Latency runs from the scheduled arrival.  The inputs of finished requests
+    are released during the stream (a long stream does not keep them all)."""
     stream = torch.cuda.Stream(dev)
     sptr = stream.cuda_stream
-    out = []
+    out = [None] * len(shapes)
     with tsx.Server(**server_kw) as sv:
-        held = []
+        pending = {}
+        last_sweep = time.monotonic()
+
+        def sweep(block):
+            for ticket in list(pending):
+                if not block and sv.wait(ticket, 0.0) == tsx.LP_PENDING:
+                    continue
+                sv.wait(ticket)
+                idx, t_sched, _ = pending.pop(ticket)
+                r = sv.result(ticket)
+                out[idx] = (r.status, r.t_done - t_sched, r.obj, r.t_done)
+
         t0 = time.monotonic()
-        for (m, n), t_arr, sd in zip(shapes, arrivals, seeds):
+        for idx, ((m, n), t_arr, sd) in enumerate(zip(shapes, arrivals, seeds)):
             delay = t0 + t_arr - time.monotonic()
             if delay > 0:
                 time.sleep(delay)
@@ -797,11 +841,11 @@ def play_stream(tsx, torch, dev, shapes, arrivals, seeds, server_kw):
             dc = torch.empty(n, dtype=torch.float64, device=dev)
             tsx.lp_generate_dense(m, n, sd, dA, db, dc, sptr)
             stream.synchronize()
-            held.append((sv.submit_device(m, n, dA, db, dc), t0 + t_arr, (dA, db, dc)))
-        for ticket, t_sched, _ in held:
-            sv.wait(ticket)
-            r = sv.result(ticket)
-            out.append((r.status, r.t_done - t_sched, r.obj, r.t_done))
+            pending[sv.submit_device(m, n, dA, db, dc)] = (idx, t0 + t_arr, (dA, db, dc))
+            if time.monotonic() - last_sweep > 0.02:
+                sweep(False)
+                last_sweep = time.monotonic()
+        sweep(True)
         st = sv.stats()
         st["last_error"] = sv.last_error()
     return out, st, t0
@@ -828,7 +872,10 @@ def run_serve(args, rank, world, local):
                                  {"workers": args.serve_workers, "blocks_per_lp": args.serve_blocks,
                                   "path": args.serve_path, "team_blocks": args.serve_team})
     clk = clocks.stop()
-    plain, st_plain, t0p = play_stream(tsx, torch, dev, shapes, arrivals, seeds,
+    # the plain path on the stream's first plain_seconds (it cannot keep up
+    # with the arrival rate: its queue grows along the whole stream)
+    kp = max(1, min(count, int(np.searchsorted(arrivals, args.plain_seconds))))
+    plain, st_plain, t0p = play_stream(tsx, torch, dev, shapes[:kp], arrivals[:kp], seeds[:kp],
                                        {"workers": 1, "batch_small": 0, "path": 0, "team_blocks": -1})
 
     def summary(res, t_start):
@@ -844,7 +891,7 @@ def run_serve(args, rank, world, local):
     hist = {}
     for r in served:
         hist[tsx.STATUS_NAMES.get(r[0], str(r[0]))] = hist.get(tsx.STATUS_NAMES.get(r[0], str(r[0])), 0) + 1
-    rel = [abs(a[2] - b[2]) / max(1e-300, abs(b[2])) for a, b in zip(served, plain)]
+    rel = [abs(a[2] - b[2]) / max(1e-300, abs(b[2])) for a, b in zip(served[:kp], plain)]
     line = {
         "metric": "LPs/s", "value": s_srv["solves_per_s"], "unit": "LPs/s", "n_gpus": world,
         "steps": 1, "warmup": 1, "ms_per_step": 1e3 * count / s_srv["solves_per_s"],
@@ -864,8 +911,18 @@ def run_serve(args, rank, world, local):
                    "wave_launch_ms": round(st["wave_launch_ms"], 1),
                    "peak_admitted_bytes": st["peak_bytes"]},
         "latency": {"p50_ms": s_srv["p50_ms"], "p99_ms": s_srv["p99_ms"], "mean_ms": s_srv["mean_ms"],
-                    "max_ms": s_srv["max_ms"], "from": "scheduled arrival to result on the host"},
-        "plain": dict(s_pl, path="one LP at a time in arrival order (1 worker, no micro-batches)"),
+                    "max_ms": s_srv["max_ms"], "from": "scheduled arrival to result on the host",
+                    "breakdown_ms": {
+                        "queue": [round(st["queue_p50_ms"], 2), round(st["queue_p99_ms"], 2)],
+                        "wait_for_launch": [round(st["wait_p50_ms"], 2), round(st["wait_p99_ms"], 2)],
+                        "kernel": [round(st["run_p50_ms"], 2), round(st["run_p99_ms"], 2)],
+                        "recovery_readout": [round(st["post_p50_ms"], 2), round(st["post_p99_ms"], 2)],
+                        "server_total": [round(st["lat_p50_ms"], 2), round(st["lat_p99_ms"], 2)],
+                        "what": "[p50, p99] per stage, measured in the server: submit -> admitted by a "
+                                "worker -> its launch starts (a wave waits for the previous wave's launch) "
+                                "-> its kernel completes (a wave: the whole team launch) -> result stored"}},
+        "plain": dict(s_pl, path="one LP at a time in arrival order (1 worker, no micro-batches)",
+                      sample=f"the stream's first {kp} requests ({args.plain_seconds:g} s of arrivals)"),
         "speedup_vs_plain": s_srv["solves_per_s"] / s_pl["solves_per_s"],
         "objective_rel_diff_vs_plain_max": max(rel),
         "optimal": s_srv["optimal"], "status_counts": hist, "last_error": st["last_error"] or None,

@@ -64,7 +64,8 @@ typedef enum {
 
 enum { LP_RULE_DANTZIG = 0, LP_RULE_BLAND = 1 };
 enum { LP_PATH_AUTO = 0, LP_PATH_PERSISTENT = 1, LP_PATH_MULTILAUNCH = 2,
-       LP_PATH_TEAM = 3 /* lp_stats.path of an lp_solve_many solve */ };
+       LP_PATH_TEAM = 3 /* lp_stats.path of an lp_solve_many solve */,
+       LP_PATH_CLUSTER = 4 };
 enum { LP_PREC_FP64 = 0, LP_PREC_FP32 = 1 };
 
 /* Solve options.  Initialise with lp_options_init() and change fields. */
@@ -83,11 +84,18 @@ typedef struct {
     long long barrier_timeout_ns; /* limit of one device-wide barrier wait
                                      (default 2e9 ns); on expiry the solve ends
                                      with LP_ERR_TIMEOUT                        */
-    int path;                     /* LP_PATH_AUTO (default): the persistent
+    int path;                     /* LP_PATH_AUTO (default): LP_PATH_CLUSTER
+                                     for an FP64 condensed tableau that fits
+                                     one thread-block cluster's shared memory
+                                     (up to 16 blocks, about 227 KB each: the
+                                     whole solve on chip, two cluster barriers
+                                     per pivot), else the persistent
                                      cooperative kernel when it can be
                                      launched, else one launch per phase;
-                                     LP_PATH_PERSISTENT or LP_PATH_MULTILAUNCH
-                                     force one of them                          */
+                                     LP_PATH_PERSISTENT, LP_PATH_MULTILAUNCH or
+                                     LP_PATH_CLUSTER force one of them (the
+                                     cluster path refuses, LP_ERR_INVALID, an
+                                     LP it cannot hold)                         */
     int skip_zero_columns;        /* full layout only: 1 (default): Step 3
                                      leaves untouched every 32-byte group of
                                      columns whose scaled pivot row entries are
@@ -144,10 +152,14 @@ typedef struct {
                                      narrow team size)                          */
     int block;                    /* threads per block                          */
     int ld;                       /* leading dimension of the tableau (elems)   */
-    double phase_ms[6];           /* persistent path, as seen by block 0: work
-                                     time of {ratio test (Steps 1-2), pivot-row
-                                     staging, rank-1 update (Step 3)}, then the
-                                     barrier wait after each of them            */
+    double phase_ms[6];           /* as seen by block 0.  Persistent path:
+                                     work time of {ratio test (Steps 1-2),
+                                     pivot-row staging, rank-1 update (Step
+                                     3)}, then the barrier wait after each of
+                                     them.  Cluster path: {Step 2, wait at
+                                     the first cluster barrier, cluster
+                                     minimum and pivot-row slices, wait at the
+                                     second cluster barrier, Step 3, Step 1}   */
     int precision;                /* precision of the solve                     */
     int pivot_status;             /* status at the end of the pivot phase       */
     int k;                        /* FP32 path: structural basic variables      */
@@ -407,6 +419,13 @@ typedef struct {
     double wave_create_ms;        /* of wave_ms: handle creation               */
     double wave_wait_ms;          /* of wave_ms: waiting for the launch token  */
     double wave_launch_ms;        /* of wave_ms: set-up and team launch (host) */
+    /* where a request's latency goes (every completed request):              */
+    double wait_p50_ms, wait_p99_ms;  /* admitted -> its solve's launch starts
+                                         (a wave waits for the previous one)   */
+    double run_p50_ms, run_p99_ms;    /* launch -> its kernel completes (a
+                                         wave's whole team launch)             */
+    double post_p50_ms, post_p99_ms;  /* kernel done -> result stored (FP64
+                                         recovery, read-out)                   */
 } lps_stats;
 
 void lps_options_init(lps_options *opt);

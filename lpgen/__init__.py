@@ -72,6 +72,23 @@ def dense_lp(m: int, n: int, seed: int):
     return A, b, c
 
 
+def diag_dominant_lp(m: int, n: int, seed: int):
+    """A dense LP whose optimal basis holds min(m, n) structural variables:
+    A_ij = u (i != j), A_ii = 4 max(m, n) + u, b_i = 100 + 900u, c_j = 1 + 9u
+    (draws in the order A row-major, b, c).  The strong diagonal makes
+    x = A^-1 b and y = A^-T c positive at m = n, so every structural variable
+    ends basic (k = m): the workload of an FP64 recovery of a large basis.
+    """
+    if m <= 0 or n <= 0:
+        raise ValueError("m and n must be positive")
+    A = uniform01(seed, 0, m * n).reshape(m, n)
+    d = np.arange(min(m, n))
+    A[d, d] += 4.0 * max(m, n)
+    b = 100.0 + 900.0 * uniform01(seed, m * n, m)
+    c = 1.0 + 9.0 * uniform01(seed, m * n + m, n)
+    return A, b, c
+
+
 def lp_digest(A, b, c) -> str:
     """SHA-256 of the little-endian float64 bytes of A, then b, then c."""
     h = hashlib.sha256()

@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "OPTIMAL", 1: "UNBOUNDED", 2: "ITER_LIMIT", 3: "NUMERIC", -1:
                 -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE", 100: "PENDING"}
 LP_RULE_DANTZIG, LP_RULE_BLAND = 0, 1
 LP_LAYOUT_CONDENSED, LP_LAYOUT_FULL = 0, 1
-LP_PATH_AUTO, LP_PATH_PERSISTENT, LP_PATH_MULTILAUNCH, LP_PATH_TEAM = 0, 1, 2, 3
+LP_PATH_AUTO, LP_PATH_PERSISTENT, LP_PATH_MULTILAUNCH, LP_PATH_TEAM, LP_PATH_CLUSTER = 0, 1, 2, 3, 4
 LP_PREC_FP64, LP_PREC_FP32 = 0, 1
 
 # every symbol include/tabsimplex.h declares
@@ -160,6 +160,12 @@ class lps_stats(ctypes.Structure):
         ("wave_create_ms", ctypes.c_double),
         ("wave_wait_ms", ctypes.c_double),
         ("wave_launch_ms", ctypes.c_double),
+        ("wait_p50_ms", ctypes.c_double),
+        ("wait_p99_ms", ctypes.c_double),
+        ("run_p50_ms", ctypes.c_double),
+        ("run_p99_ms", ctypes.c_double),
+        ("post_p50_ms", ctypes.c_double),
+        ("post_p99_ms", ctypes.c_double),
     ]
 
     def as_dict(self):

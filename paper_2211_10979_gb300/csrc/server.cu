@@ -93,6 +93,7 @@ struct Request {
     double obj = 0.0;
     std::vector<double> x, y;
     Clock::time_point t_submit, t_admit, t_done;
+    Clock::time_point t_launch, t_kernel;  // its solve's launch began / its kernel completed
     bool done = false;
 };
 
@@ -123,7 +124,7 @@ struct lp_server {
     std::deque<std::shared_ptr<Request>> queue;
     std::unordered_map<long long, std::shared_ptr<Request>> all;
     std::vector<std::thread> workers;
-    std::vector<double> lat_ms, queue_ms;
+    std::vector<double> lat_ms, queue_ms, wait_ms, run_ms, post_ms;
     long long next_id = 0;
     long long used = 0, peak = 0;
     long long submitted = 0, completed = 0, batches = 0, batched_lps = 0, waves = 0, wave_lps = 0;
@@ -173,7 +174,9 @@ static void solve_single(lp_server* sv, Request& r, cudaStream_t s) {
     o.blocks = sv->blocks;
     o.path = sv->opt.path;
     o.stream = r.on_device ? (void*)s : nullptr;
+    r.t_launch = Clock::now();
     r.status = lp_solve(h, &o);
+    r.t_kernel = Clock::now();
     if (r.status < 0) note_error(sv, "solve");
     r.x.assign(r.n, 0.0);
     r.y.assign(r.m, 0.0);
@@ -235,7 +238,14 @@ static void solve_batch(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs
     std::vector<int> st(count);
     std::vector<long long> it(count);
     std::vector<double> obj(count), x(sn), y(sm);
-    if (lp_batch_solve(h, &bo) == LP_OPTIMAL &&
+    const auto tl = Clock::now();
+    const lp_status bs = lp_batch_solve(h, &bo);
+    const auto tk = Clock::now();
+    for (auto& r : rs) {
+        r->t_launch = tl;
+        r->t_kernel = tk;
+    }
+    if (bs == LP_OPTIMAL &&
         lp_batch_get(h, st.data(), it.data(), obj.data(), x.data(), y.data()) == LP_OPTIMAL) {
         size_t xo = 0, yo = 0;
         for (int k = 0; k < count; ++k) {
@@ -316,6 +326,10 @@ static void solve_wave(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs,
                                     : solve_many_hooked(hs.data(), (int)hs.size(), &o, st.data(), kWaveReserve, release);
     if (!released) release();
     if (rc != LP_OPTIMAL) note_error(sv, "wave");
+    for (Request* r : who) {
+        r->t_launch = t2;
+        r->t_kernel = t3;
+    }
     auto ms_of = [](Clock::time_point a, Clock::time_point b) {
         return 1e3 * std::chrono::duration<double>(b - a).count();
     };
@@ -432,6 +446,11 @@ static void worker_main(lp_server* sv) {
                 ++sv->completed;
                 sv->lat_ms.push_back(1e3 * std::chrono::duration<double>(r->t_done - r->t_submit).count());
                 sv->queue_ms.push_back(1e3 * std::chrono::duration<double>(r->t_admit - r->t_submit).count());
+                if (r->t_launch.time_since_epoch().count() && r->t_kernel.time_since_epoch().count()) {
+                    sv->wait_ms.push_back(1e3 * std::chrono::duration<double>(r->t_launch - r->t_admit).count());
+                    sv->run_ms.push_back(1e3 * std::chrono::duration<double>(r->t_kernel - r->t_launch).count());
+                    sv->post_ms.push_back(1e3 * std::chrono::duration<double>(r->t_done - r->t_kernel).count());
+                }
                 r->hA.clear();
                 r->hA.shrink_to_fit();
                 r->hb.clear();
@@ -610,6 +629,12 @@ lp_status lps_get_stats(lps_t sv, lps_stats* st) {
     st->lat_mean_ms = sv->lat_ms.empty() ? 0.0 : sum / (double)sv->lat_ms.size();
     st->queue_p50_ms = percentile(sv->queue_ms, 0.50);
     st->queue_p99_ms = percentile(sv->queue_ms, 0.99);
+    st->wait_p50_ms = percentile(sv->wait_ms, 0.50);
+    st->wait_p99_ms = percentile(sv->wait_ms, 0.99);
+    st->run_p50_ms = percentile(sv->run_ms, 0.50);
+    st->run_p99_ms = percentile(sv->run_ms, 0.99);
+    st->post_p50_ms = percentile(sv->post_ms, 0.50);
+    st->post_p99_ms = percentile(sv->post_ms, 0.99);
     st->batches = sv->batches;
     st->batched_lps = sv->batched_lps;
     st->waves = sv->waves;

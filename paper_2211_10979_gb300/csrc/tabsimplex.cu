@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "tabsimplex.h"
+#include "tsx_cluster.cuh"
 #include "tsx_host.h"
 #include "tsx_kernels.cuh"
 #include "tsx_recover.cuh"
@@ -647,6 +648,89 @@ static int multilaunch_grid(int device, int m, int ld, int max_grid, int user_bl
     return update_grid<NT, V>(m, ld, kRowsInFlight, std::max(1, nsm * per), max_grid, user_blocks);
 }
 
+// ------------------------------------------------------- cluster path
+// An FP64 condensed LP whose tableau fits the shared memory of one cluster of
+// up to 16 blocks is solved by k_cluster_solve (tsx_cluster.cuh).  The
+// cluster size: the smallest power of two giving each block at most 16
+// constraint rows (more blocks add FP64 pipes; fewer cut the barrier's
+// reach), raised until the block's rows fit its shared memory, and lowered
+// when the device cannot co-schedule that many blocks with that much shared
+// memory.  0: the LP does not fit a cluster.
+template <int NT>
+static size_t cluster_static_smem() {
+    cudaFuncAttributes fa{};
+    cudaFuncGetAttributes(&fa, k_cluster_solve<NT>);
+    return fa.sharedSizeBytes;
+}
+
+template <int NT>
+static cudaError_t cluster_allow(size_t smem) {
+    static std::mutex mu;
+    static size_t allowed = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (smem <= allowed) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute((const void*)k_cluster_solve<NT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute((const void*)k_cluster_solve<NT>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    if (e == cudaSuccess) allowed = smem;
+    return e;
+}
+
+template <int NT>
+static cudaLaunchConfig_t cluster_config(int C, size_t smem, cudaStream_t s, cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)C, 1, 1);
+    cfg.blockDim = dim3(NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+template <int NT>
+static int cluster_size_for(int device, int m, int n) {
+    int optin = 0;
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+    const size_t limit = (size_t)std::max(0, optin) > cluster_static_smem<NT>() + 256
+                             ? (size_t)optin - cluster_static_smem<NT>() - 256
+                             : 0;
+    int C = 1;
+    while (C < kClusterMax && cluster_rows_per(m, C) > 16) C *= 2;
+    while (C <= kClusterMax && cluster_smem_bytes(m, n, C) > limit) C *= 2;
+    for (; C >= 1; C /= 2) {
+        const size_t smem = cluster_smem_bytes(m, n, C);
+        if (smem > limit) return 0;
+        if (cluster_allow<NT>(smem) != cudaSuccess) {
+            cudaGetLastError();
+            return 0;
+        }
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = cluster_config<NT>(C, smem, nullptr, attr);
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, (const void*)k_cluster_solve<NT>, &cfg) == cudaSuccess &&
+            nclusters > 0)
+            return C;
+        cudaGetLastError();
+    }
+    return 0;
+}
+
+template <int NT>
+static cudaError_t launch_cluster(const ClusterParams& P, int C, cudaStream_t s) {
+    const size_t smem = cluster_smem_bytes(P.m, P.n, C);
+    cudaError_t e = cluster_allow<NT>(smem);
+    if (e != cudaSuccess) return e;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = cluster_config<NT>(C, smem, s, attr);
+    return cudaLaunchKernelEx(&cfg, k_cluster_solve<NT>, P);
+}
+
 // Runs the pivot phase (build + Steps 1-3) on the handle's tableau of V.
 template <int NT, typename V>
 static lp_status pivot_phase(lp_handle* h, const lp_options& o, cudaStream_t s, double eps_d, double eps_p,
@@ -665,6 +749,15 @@ static lp_status pivot_phase(lp_handle* h, const lp_options& o, cudaStream_t s, 
     int coop = 0;
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
     int path = o.path;
+    // the cluster path: FP64, condensed tableau, small enough for one cluster
+    int csize = 0;
+    const bool cluster_ok = sizeof(V) == 8 && h->work.cond && (path == LP_PATH_AUTO || path == LP_PATH_CLUSTER);
+    if (cluster_ok) csize = cluster_size_for<NT>(h->device, m, n);
+    if (path == LP_PATH_CLUSTER && !csize) {
+        set_error("lp_solve: the cluster path needs an FP64 condensed tableau that fits one cluster's shared memory");
+        return LP_ERR_INVALID;
+    }
+    if (path == LP_PATH_AUTO && csize) path = LP_PATH_CLUSTER;
     if (path == LP_PATH_AUTO) path = (coop && coresident > 0) ? LP_PATH_PERSISTENT : LP_PATH_MULTILAUNCH;
     if (path == LP_PATH_PERSISTENT && (!coop || coresident <= 0)) {
         set_error("lp_solve: persistent path requested but cooperative launch is unavailable");
@@ -685,6 +778,32 @@ static lp_status pivot_phase(lp_handle* h, const lp_options& o, cudaStream_t s, 
     cudaEventRecord(h->ev[1], s);
     launches += 2;
 
+    int grid_run = grid;
+    if (path == LP_PATH_CLUSTER) {
+        ClusterParams CP{};
+        CP.T = (double*)h->work.T;
+        CP.ldg = ld;
+        CP.m = m;
+        CP.n = n;
+        CP.basis = h->basis;
+        CP.var = h->work.var;
+        CP.st = h->st;
+        CP.qlog = P.qlog;
+        CP.plog = P.plog;
+        CP.log_cap = P.log_cap;
+        CP.eps_d = eps_d;
+        CP.eps_p = eps_p;
+        CP.max_iters = o.max_iters;
+        CP.k_cyc = o.k_cyc;
+        CP.rule = o.rule;
+        cudaError_t e = launch_cluster<NT>(CP, csize, s);
+        if (e != cudaSuccess) {
+            set_error("lp_solve: cluster launch failed: %s", cudaGetErrorString(e));
+            return LP_ERR_CUDA;
+        }
+        ++launches;
+        grid_run = csize;
+    }
     if (path == LP_PATH_PERSISTENT) {
         cudaError_t e = launch_persistent<NT, V>(P, grid, s);
         if (e != cudaSuccess) {
@@ -699,7 +818,6 @@ static lp_status pivot_phase(lp_handle* h, const lp_options& o, cudaStream_t s, 
             ++launches;
         }
     }
-    int grid_run = grid;
     if (path == LP_PATH_MULTILAUNCH) {
         grid_run = multilaunch_grid<NT, V>(h->device, m, ld, h->max_grid, o.blocks);
         if (run_multilaunch<NT, V>(P, grid_run, s, launches) == LP_ERR_CUDA) return LP_ERR_CUDA;
@@ -1051,7 +1169,8 @@ static lp_status solve_nt(lp_handle* h, const lp_options& o, cudaStream_t s) {
 }
 
 static bool options_valid(const lp_options& o) {
-    return o.eps_d >= 0.0 && o.eps_p >= 0.0 && o.rule >= 0 && o.rule <= 1 && o.path >= 0 && o.path <= 2 &&
+    return o.eps_d >= 0.0 && o.eps_p >= 0.0 && o.rule >= 0 && o.rule <= 1 && o.path >= 0 && o.path <= 4 &&
+           o.path != LP_PATH_TEAM &&
            o.log_capacity >= 0 && o.precision >= 0 && o.precision <= 1 && o.eps_d_fp32 >= 0.0 &&
            o.eps_p_fp32 >= 0.0 && o.recover_tol >= 0.0 && o.cleanup_max >= 0 &&
            (o.layout == LP_LAYOUT_CONDENSED || o.layout == LP_LAYOUT_FULL);

@@ -17,7 +17,7 @@
 // workspace slice instead (k_batch_solve_global; L2-resident for medium LPs).
 #pragma once
 
-#include "tsx_device.cuh"
+#include "tsx_select.cuh"
 
 namespace tsx {
 
@@ -51,57 +51,23 @@ struct BatchParams {
     int k_cyc, rule;
 };
 
+#ifndef TSX_BATCH_FLAT
+#define TSX_BATCH_FLAT 1      // 1: flattened update + screened ratio test (batch_solve_one_flat)
+#endif
+
 // Shared-memory bytes of one LP's block.
 __host__ __device__ inline size_t batch_smem_bytes(int m, int n, int ldc) {
     size_t bytes = (size_t)(m + 1) * ldc * 8      // tableau
                  + (size_t)(m + 1) * 8             // F (pivot column)
                  + (size_t)ldc * 8                 // R (scaled pivot row)
                  + (size_t)n * 4 + (size_t)m * 4;  // var, basis
+#if TSX_BATCH_FLAT
+    bytes += (size_t)m * 4;                        // ratio-test candidate rows
+#endif
     return (bytes + 15) / 16 * 16;
 }
 
 constexpr int kRc = 4;        // scaled-pivot-row entries per lane kept in registers
-
-// The reductions of Steps 1-2 compare the integer keys of tsx_device.cuh
-// (dkey), not the doubles: no FP64-pipe instruction in the argmin trees.
-struct BArg {                 // entering candidate
-    long long vk;             // dkey of its objective-row entry
-    int var;                  // its variable (tie-break), INT_MAX if none
-    int slot;
-    int fvar;                 // Bland: lowest candidate variable
-    int fslot;
-};
-
-__device__ __forceinline__ void barg_merge(BArg& a, const BArg& b) {
-    if (b.vk < a.vk || (b.vk == a.vk && b.var < a.var)) { a.vk = b.vk; a.var = b.var; a.slot = b.slot; }
-    if (b.fvar < a.fvar) { a.fvar = b.fvar; a.fslot = b.fslot; }
-}
-
-struct BRat {                 // leaving candidate
-    long long rk;             // dkey of the ratio rhs_i / T[i][q]; dkey(+inf) if none
-    int key;                  // tie-break key: row (Dantzig) or basic variable (Bland)
-    int i;                    // its row, INT_MAX if none
-    double a;                 // its pivot element
-};
-
-__device__ __forceinline__ BRat brat_none() { return BRat{kKeyInf, INT_MAX, INT_MAX, 0.0}; }
-
-__device__ __forceinline__ void brat_merge(BRat& a, const BRat& b) {
-    if (b.rk < a.rk || (b.rk == a.rk && b.key < a.key)) a = b;
-}
-
-__device__ __forceinline__ BRat warp_brat(BRat a) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        BRat b;
-        b.rk = __shfl_xor_sync(0xffffffffu, a.rk, o);
-        b.key = __shfl_xor_sync(0xffffffffu, a.key, o);
-        b.i = __shfl_xor_sync(0xffffffffu, a.i, o);
-        b.a = __shfl_xor_sync(0xffffffffu, a.a, o);
-        brat_merge(a, b);
-    }
-    return a;
-}
 
 struct BatchScratch {
     BArg arg[kMaxWarps];
@@ -109,36 +75,8 @@ struct BatchScratch {
     BArg arg_out;
     BRat rat_out;
     int lp;
+    int ncand;                // flat solver: rows on the candidate list
 };
-
-// Warp-wide entering candidate (every lane returns the warp's result).
-__device__ __forceinline__ BArg warp_barg(BArg a) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        BArg b;
-        b.vk = __shfl_xor_sync(0xffffffffu, a.vk, o);
-        b.var = __shfl_xor_sync(0xffffffffu, a.var, o);
-        b.slot = __shfl_xor_sync(0xffffffffu, a.slot, o);
-        b.fvar = __shfl_xor_sync(0xffffffffu, a.fvar, o);
-        b.fslot = __shfl_xor_sync(0xffffffffu, a.fslot, o);
-        barg_merge(a, b);
-    }
-    return a;
-}
-
-__device__ __forceinline__ BArg barg_none() {
-    return BArg{kKeyInf, INT_MAX, -1, INT_MAX, -1};
-}
-
-// Step 1 candidate of objective-row slot j (value v, variable var); a NaN
-// entry fails the test v < -eps_d and is no candidate.
-__device__ __forceinline__ void barg_consider(BArg& a, double v, int vj, int j, double eps_d) {
-    if (v < -eps_d) {
-        const long long vk = dkey(v);
-        if (vk < a.vk || (vk == a.vk && vj < a.var)) { a.vk = vk; a.var = vj; a.slot = j; }
-        if (vj < a.fvar) { a.fvar = vj; a.fslot = j; }
-    }
-}
 
 // Block-wide ratio-test minimum with one barrier: each warp reduces, lane 0
 // posts the warp's partial, every thread merges the posted partials.  The
@@ -312,9 +250,219 @@ __device__ void batch_solve_one(const BatchParams& P, int k, unsigned char* smem
     __syncthreads();
 }
 
+// ---------------------------------------------------------------------------
+// The same solve with every FP64 instruction of a pivot as full as it can be.
+// GB300 issues an FP64 warp instruction to its one FP64 pipe per SM for the
+// same 16 cycles whether 1 or 32 lanes are active, and an IEEE division costs
+// about nine of them, so the pipe time of a pivot is counted in warp
+// instructions:
+//   - Step 3 runs over the (m+1) x (n+1) entries as one flat index space (each
+//     warp instruction updates 32 consecutive entries, across row ends), not
+//     row by row (a row of n+1 entries fills ceil((n+1)/32) instructions);
+//   - Step 2 screens the rows in single precision first: a row whose FP32
+//     ratio estimate is more than a factor 1 + 2^-18 above its warp's
+//     smallest estimate cannot hold the minimum ratio (the estimate's relative
+//     error is below 2^-21), so only the remaining rows -- usually one per
+//     warp, plus any row the estimate cannot represent -- get the exact IEEE
+//     division, all of them in one warp;
+//   - the candidate tests of Steps 1-2 compare integer keys, not doubles.
+// Every decision is taken on the same correctly rounded values as before, so
+// pivots and results are unchanged.  Four block barriers per pivot: after the
+// screen, after the exact minimum, after the pivot-row staging, after Step 3.
+// ---------------------------------------------------------------------------
+
+template <int NT>
+__device__ void batch_solve_one_flat(const BatchParams& P, int k, unsigned char* smem, BatchScratch& sc) {
+    const BatchLP L = P.lps[k];
+    const int m = L.m, n = L.n, ldc = L.ldc;
+    double* T = reinterpret_cast<double*>(smem);
+    double* F = T + (size_t)(m + 1) * ldc;
+    double* R = F + (m + 1);
+    int* var = reinterpret_cast<int*>(R + ldc);
+    int* basis = var + n;
+    int* cand = basis + m;
+    const double* A = P.A + L.a_off;
+    const double* b = P.b + L.b_off;
+    const double* c = P.c + L.c_off;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = NT / 32;
+    const long long epsk = dkey(-P.eps_d);
+    // bit pattern of eps_p >= 0, with -0 taken as +0
+    const long long eps_bits = max(0LL, (long long)__double_as_longlong(P.eps_p));
+
+    // Initialization Step: condensed Table I (slack basis), plus input checks
+    int bad = 0;
+    for (long long t = tid; t < (long long)(m + 1) * ldc; t += NT) {
+        const int i = (int)(t / ldc), j = (int)(t - (long long)i * ldc);
+        double v = 0.0;
+        if (j < n)
+            v = i == 0 ? -c[j] : A[(size_t)(i - 1) * n + j];
+        else if (j == n && i > 0)
+            v = b[i - 1];
+        if (j <= n) bad |= !dbits_finite(v) || (j == n && i > 0 && !(v >= 0.0));
+        T[t] = v;
+    }
+    for (int j = tid; j < n; j += NT) var[j] = j;
+    for (int i = tid; i < m; i += NT) basis[i] = n + i;
+    // Step 1 of the first pivot: warp 0 scans the objective row
+    {
+        BArg a0 = barg_none();
+        if (warp == 0) {
+            for (int j = lane; j < n; j += 32) barg_consider_key(a0, -c[j], j, j, epsk);
+            a0 = warp_barg(a0);
+        }
+        if (lane == 0) sc.arg[warp] = a0;
+        if (tid == 0) sc.ncand = 0;
+    }
+    bad = __syncthreads_or(bad);
+    const long long cap = P.max_iters < 0 ? 50LL * (m + n) : P.max_iters;
+    int status = kRunning;
+    if (bad) status = -1;   // LP_ERR_INVALID
+    long long it = 0;
+    int bland = P.rule == 1, degen = 0;
+    // this thread's first entry of the flat (m+1) x (n+1) index space, and
+    // the step between its entries
+    const int W1 = n + 1;
+    const int i_first = tid / W1, j_first = tid - (tid / W1) * W1;
+    const int di = NT / W1, dj = NT - (NT / W1) * W1;
+    const bool row0_warp = warp * 32 < W1;   // warps whose entries include row 0
+    while (status == kRunning) {
+        // Step 1: merge the objective-row partials of the previous update
+        BArg a = sc.arg[0];
+#pragma unroll 1
+        for (int w = 1; w < NW; ++w) barg_merge(a, sc.arg[w]);
+        const int qs = bland ? a.fslot : a.slot;
+        if (qs < 0) { status = kOptimal; break; }
+        if (it >= cap) { status = kIterLimit; break; }
+        // Step 2, screen: F = column qs; each warp keeps the rows whose FP32
+        // ratio estimate is within 1 + 2^-18 of its smallest estimate, and
+        // every eligible row without a usable estimate, on the candidate list
+        if (tid == 0) F[0] = T[qs];
+        float emin = __int_as_float(0x7f800000);   // +inf
+        for (int i = 1 + tid; i <= m; i += NT) {
+            const double av = T[(size_t)i * ldc + qs];
+            F[i] = av;
+            float est;
+            if (eligible_bits(av, eps_bits) && ratio_estimate(T[(size_t)i * ldc + n], av, est))
+                emin = fminf(emin, est);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) emin = fminf(emin, __shfl_xor_sync(0xffffffffu, emin, o));
+        const float band = __fmul_ru(emin, 1.0f + 0x1p-18f);
+        for (int base = 1 + warp * 32; base <= m; base += NT) {
+            const int i = base + lane;
+            bool keep = false;
+            if (i <= m) {
+                const double av = F[i];
+                if (eligible_bits(av, eps_bits)) {
+                    float est;
+                    keep = !ratio_estimate(T[(size_t)i * ldc + n], av, est) || est <= band;
+                }
+            }
+            const unsigned ball = __ballot_sync(0xffffffffu, keep);
+            if (ball) {
+                int at = 0;
+                if (lane == 0) at = atomicAdd(&sc.ncand, __popc(ball));
+                at = __shfl_sync(0xffffffffu, at, 0);
+                if (keep) cand[at + __popc(ball & ((1u << lane) - 1u))] = i;
+            }
+        }
+        __syncthreads();
+        // Step 2, exact: warp 0 divides the candidates (IEEE division) and
+        // takes the minimum (ties: row, or basic variable in Bland mode)
+        if (warp == 0) {
+            BRat best = brat_none();
+            const int nc = sc.ncand;
+            for (int t = lane; t < nc; t += 32) {
+                const int i = cand[t];
+                const double av = F[i];
+                const double r = __ddiv_rn(T[(size_t)i * ldc + n], av);
+                if (!dbits_nan(r)) {   // a NaN ratio never wins the comparison
+                    BRat cnd;
+                    cnd.rk = dkey(r);
+                    cnd.i = i;
+                    cnd.key = bland ? basis[i - 1] : i;
+                    cnd.a = av;
+                    brat_merge(best, cnd);
+                }
+            }
+            best = warp_brat(best);
+            if (lane == 0) {
+                sc.rat_out = best;
+                sc.ncand = 0;
+            }
+        }
+        __syncthreads();
+        const BRat best = sc.rat_out;
+        if (best.i == INT_MAX) { status = kUnbounded; break; }
+        const int p = best.i;
+        const double piv = best.a;
+        const double ratio = dkey_value(best.rk);
+        if (!dbits_finite(piv) || !dbits_finite(ratio)) { status = kNumeric; break; }
+        // Step 3: scaled pivot row; the leaving variable takes slot qs
+        for (int j = tid; j <= n; j += NT) R[j] = j == qs ? __ddiv_rn(1.0, piv) : __ddiv_rn(T[(size_t)p * ldc + j], piv);
+        if (tid == 0) {
+            const int leaving = basis[p - 1];
+            basis[p - 1] = var[qs];
+            var[qs] = leaving;
+        }
+        ++it;
+        if (P.rule == 0) {
+            if (best.rk <= 0) {   // ratio <= 0
+                ++degen;
+                if (P.k_cyc > 0 && degen >= P.k_cyc) bland = 1;
+            } else {
+                degen = 0;
+                bland = 0;
+            }
+        }
+        __syncthreads();
+        // rank-1 update over the flat index space; row p becomes R; the
+        // objective row's new entries feed the next Step 1
+        BArg an = flat_update(T, ldc, m, W1, n, F, R, qs, p, var, epsk, i_first, j_first, di, dj);
+        if (row0_warp) an = warp_barg(an);
+        if (lane == 0) sc.arg[warp] = an;
+        __syncthreads();
+    }
+    // read-out (Table I layout): x from the basis, y from the objective row
+    double* x = P.x + L.c_off;
+    double* y = P.y + L.b_off;
+    for (int j = tid; j < n; j += NT) x[j] = 0.0;
+    for (int i = tid; i < m; i += NT) y[i] = 0.0;
+    __syncthreads();
+    if (status != -1) {
+        for (int i = tid; i < m; i += NT)
+            if (basis[i] < n) x[basis[i]] = T[(size_t)(i + 1) * ldc + n];
+        for (int j = tid; j < n; j += NT)
+            if (var[j] >= n) y[var[j] - n] = T[j];
+    }
+    if (tid == 0) {
+        P.status[k] = status;
+        P.iters[k] = it;
+        P.obj[k] = status == -1 ? 0.0 : T[n];
+        if (it) atomicAdd(P.total_pivots, (unsigned long long)it);
+    }
+    if (P.keepT) {
+        double* kt = P.keepT + L.t_off;
+        for (long long t = tid; t < (long long)(m + 1) * ldc; t += NT) kt[t] = T[t];
+        for (int j = tid; j < n; j += NT) P.keepvar[L.c_off + j] = var[j];
+        for (int i = tid; i < m; i += NT) P.keepbasis[L.b_off + i] = basis[i];
+    }
+    __syncthreads();
+}
+
+template <int NT>
+__device__ __forceinline__ void batch_solve_lp(const BatchParams& P, int k, unsigned char* smem, BatchScratch& sc) {
+#if TSX_BATCH_FLAT
+    batch_solve_one_flat<NT>(P, k, smem, sc);
+#else
+    batch_solve_one<NT>(P, k, smem, sc);
+#endif
+}
+
 // One bucket: persistent blocks take LPs of `list` from a counter until none is left.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_batch_solve(BatchParams P, const int* __restrict__ list, int count,
+__global__ void __launch_bounds__(NT, TSX_BATCH_MINB ? (1024 / NT > 0 ? 1024 / NT : 1) : 1) k_batch_solve(BatchParams P, const int* __restrict__ list, int count,
                                                    unsigned* __restrict__ queue) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ BatchScratch sc;
@@ -324,13 +472,13 @@ __global__ void __launch_bounds__(NT) k_batch_solve(BatchParams P, const int* __
         const int t = sc.lp;
         __syncthreads();
         if (t >= count) return;
-        batch_solve_one<NT>(P, list[t], smem, sc);
+        batch_solve_lp<NT>(P, list[t], smem, sc);
     }
 }
 
 // LPs too large for shared memory: the same solve on a global workspace slice.
 template <int NT>
-__global__ void __launch_bounds__(NT) k_batch_solve_global(BatchParams P, const int* __restrict__ list, int count,
+__global__ void __launch_bounds__(NT, TSX_BATCH_MINB ? (1024 / NT > 0 ? 1024 / NT : 1) : 1) k_batch_solve_global(BatchParams P, const int* __restrict__ list, int count,
                                                           unsigned* __restrict__ queue, unsigned char* work) {
     __shared__ BatchScratch sc;
     for (;;) {
@@ -340,7 +488,7 @@ __global__ void __launch_bounds__(NT) k_batch_solve_global(BatchParams P, const 
         __syncthreads();
         if (t >= count) return;
         const int k = list[t];
-        batch_solve_one<NT>(P, k, work + P.lps[k].w_off, sc);
+        batch_solve_lp<NT>(P, k, work + P.lps[k].w_off, sc);
     }
 }
 

@@ -41,18 +41,21 @@ if ROOT not in sys.path:
 OUT = os.path.join(HERE, "full_size")
 GAP_REL = 1e-9
 
-# (m, n, seed, what the case serves)
+# (m, n, seed, what the case serves, generator: lpgen.dense_lp or lpgen.diag_dominant_lp)
 CASES = {
-    "8192x8192s1": (8192, 8192, 1, "bench size, FP64 parity"),
-    "8192x8192s2": (8192, 8192, 2, "bench size, FP64 parity"),
-    "8192x8192s3": (8192, 8192, 3, "bench size, FP64 parity"),
-    "4096x16384s1": (4096, 16384, 1, "aspect-ratio bench size, FP64 parity"),
-    "16384x16384s1": (16384, 16384, 1, "precision config: FP64 reference objective"),
+    "8192x8192s1": (8192, 8192, 1, "bench size, FP64 parity", "dense_lp"),
+    "8192x8192s2": (8192, 8192, 2, "bench size, FP64 parity", "dense_lp"),
+    "8192x8192s3": (8192, 8192, 3, "bench size, FP64 parity", "dense_lp"),
+    "4096x16384s1": (4096, 16384, 1, "aspect-ratio bench size, FP64 parity", "dense_lp"),
+    "16384x16384s1": (16384, 16384, 1, "precision config: FP64 reference objective", "dense_lp"),
+    "diag2048s1": (2048, 2048, 1, "FP64 recovery of a basis with k = 2048 structurals", "diag_dominant_lp"),
+    "diag4096s1": (4096, 4096, 1, "FP64 recovery of a basis with k = 4096 structurals", "diag_dominant_lp"),
 }
 
 
-def path_of(m: int, n: int, seed: int) -> str:
-    return os.path.join(OUT, f"{m}x{n}_seed{seed}.json")
+def path_of(m: int, n: int, seed: int, gen: str = "dense_lp") -> str:
+    prefix = "" if gen == "dense_lp" else "diag_"
+    return os.path.join(OUT, f"{prefix}{m}x{n}_seed{seed}.json")
 
 
 def _rel_gap_summary(gap: np.ndarray, base: np.ndarray):
@@ -70,8 +73,8 @@ def run_case(name: str) -> str:
     import lpgen
     import oracle
 
-    m, n, seed, what = CASES[name]
-    A, b, c = lpgen.dense_lp(m, n, seed)
+    m, n, seed, what, gen = CASES[name]
+    A, b, c = getattr(lpgen, gen)(m, n, seed)
     t0 = time.time()
     res, tr = oracle.solve_traced(A, b, c)
     secs = time.time() - t0
@@ -90,7 +93,7 @@ def run_case(name: str) -> str:
     ynz = np.nonzero(res.y)[0]
     rec = {
         "what": what,
-        "generator": "lpgen.dense_lp(m, n, seed)",
+        "generator": f"lpgen.{gen}(m, n, seed)",
         "m": m, "n": n, "seed": seed,
         "lp_sha256": lpgen.lp_digest(A, b, c),
         "oracle": "oracle.solve_traced, default options (Dantzig, eps 1e-9, k_cyc 50)",
@@ -116,7 +119,7 @@ def run_case(name: str) -> str:
         "oracle_seconds": round(secs, 1),
     }
     os.makedirs(OUT, exist_ok=True)
-    p = path_of(m, n, seed)
+    p = path_of(m, n, seed, gen)
     tmp = p + ".tmp"
     with open(tmp, "w") as f:
         json.dump(rec, f, separators=(",", ":"))

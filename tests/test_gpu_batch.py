@@ -169,3 +169,51 @@ def test_ties_and_signed_zeros_inside_a_batch(tsx, rule):
         _check(sol, problems, refs)
         for k in range(len(problems)):
             np.testing.assert_array_equal(bt.tableau(k), refs[k].T)
+
+
+def _screen_lps():
+    """LPs aimed at the single-precision screen of the ratio test: exact ties
+    among more rows than a warp holds, ratios one ulp apart (inside the screen's
+    band, so the exact division decides), and rows whose entries lie outside
+    float's exponent range (they bypass the screen)."""
+    out = []
+    # 100 identical constraint rows in column 0: 100 tied candidates per pivot
+    A = np.ones((100, 5))
+    A[:, 1:] = np.linspace(0.5, 2.0, 4)
+    out.append((A, np.full(100, 100.0), np.array([9.0, 1.0, 2.0, 3.0, 4.0])))
+    # ratios b_i / A_i0 = 7 (1 + d_i 2^-50), d_i in 0..5: all within the band
+    rng = np.random.default_rng(11)
+    m, n = 60, 8
+    A = rng.integers(1, 9, size=(m, n)).astype(np.float64) / 4.0
+    d = rng.integers(0, 6, size=m)
+    b = A[:, 0] * 7.0 * (1.0 + d * 2.0 ** -50)
+    c = np.concatenate([[10.0], np.ones(n - 1)])
+    out.append((A, b, c))
+    # rows scaled by 2^300 and 2^-300 (ratios unchanged; no float estimate)
+    A, b, c = lpgen.dense_lp(40, 30, 21)
+    A, b = A.copy(), b.copy()
+    A[:10] *= 2.0 ** 300
+    b[:10] *= 2.0 ** 300
+    A[10:20] *= 2.0 ** -300
+    b[10:20] *= 2.0 ** -300
+    out.append((A, b, c))
+    # a zero right-hand side (ratio 0, degenerate) next to ordinary rows
+    A, b, c = lpgen.dense_lp(50, 50, 22)
+    b = b.copy()
+    b[[3, 17, 40]] = 0.0
+    out.append((A, b, c))
+    return out
+
+
+@pytest.mark.parametrize("threads", [32, 128, 512])
+@pytest.mark.parametrize("rule", [0, 1])
+def test_ratio_screen_edge_cases(tsx, threads, rule):
+    problems = _screen_lps()
+    kw = {"rule": rule} if rule else {"k_cyc": 5}
+    refs = [oracle.solve(*p, oracle.Options(**kw)) for p in problems]
+    with tsx.Batch(problems) as bt:
+        bt.solve(tsx.batch_options(threads=threads, keep_tableaux=1, **kw))
+        sol = bt.results()
+        _check(sol, problems, refs)
+        for k in range(len(problems)):
+            np.testing.assert_array_equal(bt.tableau(k), refs[k].T)

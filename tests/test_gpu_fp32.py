@@ -170,6 +170,33 @@ def test_fp32_full_size_16384(tsx):
     np.testing.assert_array_equal(sol64.y, g["y"])
 
 
+@pytest.mark.parametrize("m", [2048, 4096])
+def test_fp32_recovery_of_a_large_basis(tsx, m):
+    # every structural variable ends basic (k = m): the FP64 recovery factors
+    # an m x m block; its result is checked against the FP64 oracle's whole
+    # solve (tests/golden/full_size, written by the oracle alone)
+    import torch
+    from test_gpu_full_size import load_golden
+    g = load_golden(m, m, 1, gen="diag_dominant_lp")
+    A, b, c = lpgen.diag_dominant_lp(m, m, 1)
+    assert lpgen.lp_digest(A, b, c) == g["lp_sha256"]
+    assert len(g["x_nonzero"]) == m   # the oracle's basis: k = m
+    dA, db, dc = (torch.from_numpy(v).cuda() for v in (A, b, c))
+    s = torch.cuda.current_stream().cuda_stream
+    with tsx.Problem(dA, db, dc, device=True, stream=s) as pr:
+        assert pr.solve(tsx.options(stream=s, precision=tsx.LP_PREC_FP32)) == tsx.LP_OPTIMAL
+        sol = pr.solution()
+        st = pr.stats()
+    assert st["k"] == m and st["recover_ms"] > 0
+    ref_obj = g["obj_value"]
+    assert abs(sol.obj - ref_obj) <= 1e-9 * abs(ref_obj)
+    assert np.abs(sol.x - g["x"]).max() <= 1e-9 * max(1.0, float(np.abs(g["x"]).max()))
+    assert np.abs(sol.y - g["y"]).max() <= 1e-9 * max(1.0, float(np.abs(g["y"]).max()))
+    pv, dv = _violations(A, b, c, sol.x, sol.y)
+    assert pv <= 1e-9 and dv <= 1e-9
+    assert st["primal_violation"] <= 1e-9 and st["dual_violation"] <= 1e-9
+
+
 @pytest.mark.parametrize("path", [1, 2])
 def test_concurrent_solves_equal_their_solo_runs(tsx, path):
     # eight host threads solve medium LPs at once on full grids, so the

@@ -29,9 +29,10 @@ K = 3
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "full_size")
 
 
-def load_golden(m, n, seed):
-    """Oracle record of the whole solve of lpgen.dense_lp(m, n, seed)."""
-    with open(os.path.join(GOLDEN, f"{m}x{n}_seed{seed}.json")) as fh:
+def load_golden(m, n, seed, gen="dense_lp"):
+    """Oracle record of the whole solve of lpgen.<gen>(m, n, seed)."""
+    prefix = "" if gen == "dense_lp" else "diag_"
+    with open(os.path.join(GOLDEN, f"{prefix}{m}x{n}_seed{seed}.json")) as fh:
         g = json.load(fh)
     g["obj_value"] = float.fromhex(g["obj"])
     basis = n + np.arange(m, dtype=np.int64)

@@ -104,7 +104,7 @@ def test_golden_hand_traces(tsx, golden_dir):
         A = np.array(g["A"], dtype=np.float64)
         b = np.array(g["b"], dtype=np.float64)
         c = np.array(g["c"], dtype=np.float64)
-        for path, layout in ((1, 0), (2, 0), (1, 1), (2, 1)):
+        for path, layout in ((1, 0), (2, 0), (4, 0), (1, 1), (2, 1)):
             st, sol, T, q, p, _ = _gpu_run(tsx, A, b, c, path=path, layout=layout)
             assert tsx.STATUS_NAMES[st] == g["status"]
             assert q.tolist() == [s["q"] for s in g["steps"]]
@@ -119,9 +119,8 @@ def test_cycling_lp_bland_fallback(tsx):
     c = np.array([10.0, -57.0, -9.0, -24.0])
     for kw in ({"k_cyc": 3}, {"k_cyc": 50}, {"rule": 1}, {"k_cyc": 0, "max_iters": 200}):
         ref = _oracle_run(A, b, c, **kw)
-        for path in (1, 2):
-            for layout in (0, 1):
-                _assert_same(_gpu_run(tsx, A, b, c, path=path, layout=layout, **kw), ref)
+        for path, layout in ((1, 0), (1, 1), (2, 0), (2, 1), (4, 0)):
+            _assert_same(_gpu_run(tsx, A, b, c, path=path, layout=layout, **kw), ref)
 
 
 def test_unbounded_and_zero_objective(tsx):
@@ -210,3 +209,53 @@ def test_stats_account_for_the_update(tsx, layout):
         assert ld == -(-W // 16) * 16
         assert 0 < stats["update_bytes"] <= 2.0 * (m + 1) * ld * 8 * it + side
     assert stats["pivot_ms"] > 0 and stats["kernel_launches"] >= 3
+
+
+# the cluster path (LP_PATH_CLUSTER, chosen by default for FP64 condensed LPs
+# that fit one cluster's shared memory): shapes around the row split (16 rows
+# per block, clusters of 1-16 blocks) and the largest that fit
+CLUSTER_SHAPES = [(1, 1), (1, 7), (7, 1), (3, 4), (16, 16), (17, 33), (33, 17), (37, 53), (64, 64),
+                  (100, 300), (300, 100), (129, 257), (256, 256), (255, 511), (511, 255), (600, 600)]
+
+
+@pytest.mark.parametrize("m,n", CLUSTER_SHAPES)
+def test_cluster_path_bit_exact(tsx, m, n):
+    A, b, c = lpgen.dense_lp(m, n, 7 + m + 3 * n)
+    ref = _oracle_run(A, b, c)
+    run = _gpu_run(tsx, A, b, c, path=tsx.LP_PATH_CLUSTER)
+    _assert_same(run, ref)
+    stats = run[5]
+    assert stats["path"] == tsx.LP_PATH_CLUSTER and 1 <= stats["grid"] <= 16
+    # the default path picks the cluster for these sizes
+    assert _gpu_run(tsx, A, b, c)[5]["path"] == tsx.LP_PATH_CLUSTER
+
+
+@pytest.mark.parametrize("kw", [{"k_cyc": 3}, {"rule": 1}, {"max_iters": 7}, {"eps_p": 0.0, "eps_d": 0.0}])
+def test_cluster_path_options(tsx, kw):
+    A, b, c = lpgen.dense_lp(200, 150, 31)
+    ref = _oracle_run(A, b, c, **kw)
+    _assert_same(_gpu_run(tsx, A, b, c, path=tsx.LP_PATH_CLUSTER, **kw), ref)
+    A0, b0, c0 = lpgen.dense_lp(40, 30, 11)
+    A = np.vstack([A0, A0[:10], np.ones((3, 30))])
+    b = np.concatenate([b0, b0[:10], np.full(3, 50.0)])
+    _assert_same(_gpu_run(tsx, A, b, c0, path=tsx.LP_PATH_CLUSTER, **kw), _oracle_run(A, b, c0, **kw))
+
+
+def test_cluster_path_unbounded_zero_and_refusals(tsx):
+    A = np.array([[1.0, -2.0], [1.0, 0.0]])
+    b = np.array([4.0, 3.0])
+    c = np.array([0.0, 1.0])
+    _assert_same(_gpu_run(tsx, A, b, c, path=tsx.LP_PATH_CLUSTER), _oracle_run(A, b, c))
+    A, b, _ = lpgen.dense_lp(5, 4, 3)
+    _assert_same(_gpu_run(tsx, A, b, -np.ones(4), path=tsx.LP_PATH_CLUSTER), _oracle_run(A, b, -np.ones(4)))
+    # refused: the Table I layout, a float tableau, an LP too large for a cluster
+    A, b, c = lpgen.dense_lp(64, 64, 3)
+    with tsx.Problem(A, b, c) as pr:
+        for kw in ({"layout": tsx.LP_LAYOUT_FULL}, {"precision": tsx.LP_PREC_FP32}):
+            assert tsx.lp_solve(pr.h, tsx.options(path=tsx.LP_PATH_CLUSTER, **kw)) == tsx.LP_ERR_INVALID
+            assert "cluster" in tsx.lp_last_error()
+    A, b, c = lpgen.dense_lp(1024, 1024, 3)
+    with tsx.Problem(A, b, c) as pr:
+        assert tsx.lp_solve(pr.h, tsx.options(path=tsx.LP_PATH_CLUSTER)) == tsx.LP_ERR_INVALID
+        assert pr.solve() == tsx.LP_OPTIMAL
+        assert pr.stats()["path"] == tsx.LP_PATH_PERSISTENT
