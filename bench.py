@@ -60,9 +60,13 @@ def parse_args(argv=None):
     ap.add_argument("--path", type=int, default=0)
     ap.add_argument("--threads", type=int, default=0)
     ap.add_argument("--blocks", type=int, default=0)
-    ap.add_argument("--workload", choices=["single", "batch", "serve", "many", "fp64-peak"], default="single",
+    ap.add_argument("--workload", choices=["single", "batch", "serve", "many", "fp64-peak", "hybrid"],
+                    default="single",
                     help="batch: 4096 small LPs (m, n uniform in [16, 128]) per step; serve: a "
                          "Poisson stream of LPs (m, n log-uniform in [32, 4096]) through the server")
+    ap.add_argument("--thetas", default="1.0,0.995,0.99,0.98,0.95,0.9,0.8",
+                    help="hybrid: GPU shares of the column slots to sweep")
+    ap.add_argument("--cpu-threads", type=int, default=0, help="hybrid: host threads (0 = all but one)")
     ap.add_argument("--rate", type=float, default=2000.0, help="serve: arrivals per second")
     ap.add_argument("--serve-seconds", type=float, default=1.0, help="serve: length of the stream")
     ap.add_argument("--serve-workers", type=int, default=8)
@@ -72,6 +76,8 @@ def parse_args(argv=None):
     ap.add_argument("--serve-team", type=int, default=0,
                     help="serve: blocks per team of the lp_solve_many waves (0 = library default, "
                          "< 0 = no waves: one LP per worker)")
+    ap.add_argument("--serve-continuous", type=int, default=1,
+                    help="serve: 1 = one continuous team launch for the large requests, 0 = waves")
     ap.add_argument("--serve-path", type=int, default=2,
                     help="serve: single-lane solve path (1 persistent cooperative, 2 one launch per phase)")
     ap.add_argument("--batch-count", type=int, default=4096)
@@ -870,7 +876,8 @@ def run_serve(args, rank, world, local):
     clocks.start()
     served, st, t0 = play_stream(tsx, torch, dev, shapes, arrivals, seeds,
                                  {"workers": args.serve_workers, "blocks_per_lp": args.serve_blocks,
-                                  "path": args.serve_path, "team_blocks": args.serve_team})
+                                  "path": args.serve_path, "team_blocks": args.serve_team,
+                                  "continuous": args.serve_continuous})
     clk = clocks.stop()
     # the plain path on the stream's first plain_seconds (it cannot keep up
     # with the arrival rate: its queue grows along the whole stream)
@@ -905,6 +912,8 @@ def run_serve(args, rank, world, local):
                    "workers": args.serve_workers, "blocks_per_lp": args.serve_blocks or "default",
                    "single_lane_path": args.serve_path,
                    "batches": st["batches"], "batched_lps": st["batched_lps"],
+                   "large_lane": "continuous team launch" if args.serve_continuous else "lp_solve_many waves",
+                   "lane_lps": st["lane_lps"], "lane_launches": st["lane_launches"],
                    "waves": st["waves"], "wave_lps": st["wave_lps"], "team_blocks": args.serve_team or "default",
                    "wave_ms": round(st["wave_ms"], 1), "wave_kernel_ms": round(st["wave_kernel_ms"], 1),
                    "wave_create_ms": round(st["wave_create_ms"], 1), "wave_wait_ms": round(st["wave_wait_ms"], 1),
@@ -936,6 +945,64 @@ def run_serve(args, rank, world, local):
     return 0
 
 
+def run_hybrid(args, rank, world, local):
+    """The paper's CPU+GPU column split (Section IV; Tables VI-VIII): one whole
+    solve of the seed-1 LP per share theta of the column slots on the GPU, the
+    rest on host threads, beside the GPU-only persistent path.  Context, not a
+    target: wall-clock time of lp_solve (host threads and GPU kernel alike)."""
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    import paper_2211_10979_gb300 as tsx
+    from paper_2211_10979_gb300 import build as tsx_build
+    tsx_build.build()
+    tsx.use_torch_allocator()
+    m, n = args.m, args.n
+    A, b, c = lpgen.dense_lp(m, n, 1)
+    dA, db, dc = (torch.from_numpy(v).to(dev) for v in (A, b, c))
+    sptr = torch.cuda.current_stream(dev).cuda_stream
+    rows = []
+    with tsx.Problem(dA, db, dc, device=True, stream=sptr) as pr:
+        def timed(**kw):
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            st = pr.solve(tsx.options(stream=sptr, **kw))
+            secs = time.perf_counter() - t0
+            if st != tsx.LP_OPTIMAL:
+                raise RuntimeError(f"solve ended {tsx.STATUS_NAMES.get(st, st)}: {tsx.lp_last_error()}")
+            sol = pr.solution()
+            return secs, sol.iters, sol.obj
+        for _ in range(max(1, args.warmup)):
+            timed(path=tsx.LP_PATH_PERSISTENT)
+        clocks = ClockSampler(local)
+        clocks.start()
+        base_s, base_it, base_obj = min((timed(path=tsx.LP_PATH_PERSISTENT) for _ in range(args.steps)),
+                                        key=lambda r: r[0])
+        rows.append({"theta": "GPU only (persistent path)", "seconds": base_s, "pivots": base_it,
+                     "pivots_per_s": base_it / base_s, "vs_gpu_only": 1.0})
+        for th in [float(x) for x in args.thetas.split(",") if x]:
+            timed(path=tsx.LP_PATH_HYBRID, gpu_share=th, cpu_threads=args.cpu_threads)   # warm-up
+            secs, it, obj = min((timed(path=tsx.LP_PATH_HYBRID, gpu_share=th, cpu_threads=args.cpu_threads)
+                                 for _ in range(args.steps)), key=lambda r: r[0])
+            assert it == base_it and obj == base_obj, "the split changes no pivot"
+            rows.append({"theta": th, "seconds": secs, "pivots": it, "pivots_per_s": it / secs,
+                         "vs_gpu_only": base_s / secs})
+        clk = clocks.stop()
+    hw = os.cpu_count()
+    line = {
+        "metric": "pivots/s", "value": rows[0]["pivots_per_s"], "unit": "pivots/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"dense LP m={m} n={n} FP64 seed 1, whole solve per theta (best of {args.steps})",
+                   "what": "theta = share of the nonbasic column slots on the GPU; the rest on host threads "
+                           "(the paper's Section IV split); wall-clock time of lp_solve",
+                   "cpu_threads": args.cpu_threads or max(1, hw - 1), "host_cores": hw},
+        "sweep": rows, "clocks": clk, "roofline": None,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     rank, world, local = dist_env()
@@ -947,6 +1014,8 @@ def main(argv=None):
         return run_batch(args, rank, world, local)
     if args.workload == "fp64-peak":
         return run_fp64_peak(args, rank, world, local) if rank == 0 else 0
+    if args.workload == "hybrid":
+        return run_hybrid(args, rank, world, local) if rank == 0 else 0
     if args.workload == "many":
         if rank != 0:
             return 0

@@ -65,7 +65,7 @@ typedef enum {
 enum { LP_RULE_DANTZIG = 0, LP_RULE_BLAND = 1 };
 enum { LP_PATH_AUTO = 0, LP_PATH_PERSISTENT = 1, LP_PATH_MULTILAUNCH = 2,
        LP_PATH_TEAM = 3 /* lp_stats.path of an lp_solve_many solve */,
-       LP_PATH_CLUSTER = 4 };
+       LP_PATH_CLUSTER = 4, LP_PATH_HYBRID = 5 };
 enum { LP_PREC_FP64 = 0, LP_PREC_FP32 = 1 };
 
 /* Solve options.  Initialise with lp_options_init() and change fields. */
@@ -95,7 +95,13 @@ typedef struct {
                                      LP_PATH_PERSISTENT, LP_PATH_MULTILAUNCH or
                                      LP_PATH_CLUSTER force one of them (the
                                      cluster path refuses, LP_ERR_INVALID, an
-                                     LP it cannot hold)                         */
+                                     LP it cannot hold).  LP_PATH_HYBRID: the
+                                     paper's CPU+GPU column split (Section
+                                     IV): the persistent kernel on a share
+                                     gpu_share of the columns, host threads on
+                                     the rest, exchanging the Step 1 and Step
+                                     2 results every pivot (FP64, condensed
+                                     layout; the same pivots and values)      */
     int skip_zero_columns;        /* full layout only: 1 (default): Step 3
                                      leaves untouched every 32-byte group of
                                      columns whose scaled pivot row entries are
@@ -130,6 +136,14 @@ typedef struct {
                                      the full tableau's, with half the bytes
                                      at m = n.  LP_LAYOUT_FULL: the Table I
                                      tableau itself ((m+1) x (n+m+1))           */
+    double gpu_share;             /* LP_PATH_HYBRID (FP64, condensed): the
+                                     fraction theta of the nonbasic column
+                                     slots kept on the GPU; host threads hold
+                                     the rest (Section IV's CPU/GPU split of
+                                     the tableau; default 0.95)                */
+    int cpu_threads;              /* LP_PATH_HYBRID: host threads of the CPU
+                                     share; 0 = the hardware threads less one,
+                                     at least 1 (default 0)                    */
 } lp_options;
 
 enum { LP_LAYOUT_CONDENSED = 0, LP_LAYOUT_FULL = 1 };
@@ -366,7 +380,11 @@ void lp_batch_destroy(lp_batch_t h);
  * next wave is formed while the current one's team launch runs, and the
  * finished wave's recovery and read-out overlap the next launch (or, with
  * team_blocks < 0, one per worker by lp_create / lp_solve on a share of the
- * GPU's blocks).  Requests arriving while others are on the GPU are
+ * GPU's blocks).  By default (continuous = 1) there are no waves: one team
+ * launch stays resident while requests keep coming, each admitted large
+ * request is appended to its job list at once and taken by the next free
+ * team, and each result is finished (FP64 recovery, read-out) as soon as its
+ * own team is done.  Requests arriving while others are on the GPU are
  * admitted as workers and memory free up, and their work overlaps on the
  * device.  The paper has no serving layer; every solve inside is the method of
  * lp_solve.
@@ -403,6 +421,14 @@ typedef struct {
                                      many blocks -- every such request waiting
                                      when a wave starts joins it, one wave at a
                                      time; < 0: one per worker by lp_solve     */
+    int continuous;               /* 1 (default, with team_blocks >= 0): the
+                                     large requests go to one continuous team
+                                     launch instead of waves: each is taken by
+                                     the next team that finishes an LP as soon
+                                     as it is admitted, and its result is
+                                     returned as soon as its own team is done
+                                     (the launch ends when idle and restarts
+                                     with the next request); 0: waves         */
 } lps_options;
 
 typedef struct {
@@ -426,6 +452,8 @@ typedef struct {
                                          wave's whole team launch)             */
     double post_p50_ms, post_p99_ms;  /* kernel done -> result stored (FP64
                                          recovery, read-out)                   */
+    long long lane_lps;           /* requests solved by the continuous launch  */
+    long long lane_launches;      /* continuous team launches started          */
 } lps_stats;
 
 void lps_options_init(lps_options *opt);

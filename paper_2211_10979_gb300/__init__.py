@@ -15,7 +15,7 @@ import numpy as np
 from . import abi
 from .abi import (LP_ERR_CUDA, LP_ERR_INVALID, LP_ERR_NOMEM, LP_ERR_NUMERIC, LP_ERR_STATE,
                   LP_ERR_TIMEOUT, LP_ITER_LIMIT, LP_LAYOUT_CONDENSED, LP_LAYOUT_FULL, LP_OPTIMAL,
-                  LP_PATH_AUTO, LP_PATH_CLUSTER, LP_PATH_MULTILAUNCH, LP_PATH_TEAM,
+                  LP_PATH_AUTO, LP_PATH_CLUSTER, LP_PATH_HYBRID, LP_PATH_MULTILAUNCH, LP_PATH_TEAM,
                   LP_PATH_PERSISTENT, LP_PREC_FP32, LP_PREC_FP64, LP_RULE_BLAND, LP_RULE_DANTZIG, LP_UNBOUNDED, STATUS_NAMES,
                   lp_create, lp_create_device, lp_destroy, lp_get_pivot_log, lp_get_solution,
                   lp_get_stats, lp_get_tableau, lp_last_error, lp_options, lp_options_init,

@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "OPTIMAL", 1: "UNBOUNDED", 2: "ITER_LIMIT", 3: "NUMERIC", -1:
                 -2: "NOMEM", -3: "CUDA", -4: "TIMEOUT", -5: "STATE", 100: "PENDING"}
 LP_RULE_DANTZIG, LP_RULE_BLAND = 0, 1
 LP_LAYOUT_CONDENSED, LP_LAYOUT_FULL = 0, 1
-LP_PATH_AUTO, LP_PATH_PERSISTENT, LP_PATH_MULTILAUNCH, LP_PATH_TEAM, LP_PATH_CLUSTER = 0, 1, 2, 3, 4
+LP_PATH_AUTO, LP_PATH_PERSISTENT, LP_PATH_MULTILAUNCH, LP_PATH_TEAM, LP_PATH_CLUSTER, LP_PATH_HYBRID = 0, 1, 2, 3, 4, 5
 LP_PREC_FP64, LP_PREC_FP32 = 0, 1
 
 # every symbol include/tabsimplex.h declares
@@ -58,6 +58,8 @@ class lp_options(ctypes.Structure):
         ("recover_tol", ctypes.c_double),
         ("cleanup_max", ctypes.c_int),
         ("layout", ctypes.c_int),
+        ("gpu_share", ctypes.c_double),
+        ("cpu_threads", ctypes.c_int),
     ]
 
 
@@ -136,6 +138,7 @@ class lps_options(ctypes.Structure):
         ("batch_max_bytes", ctypes.c_longlong),
         ("path", ctypes.c_int),
         ("team_blocks", ctypes.c_int),
+        ("continuous", ctypes.c_int),
     ]
 
 
@@ -166,6 +169,8 @@ class lps_stats(ctypes.Structure):
         ("run_p99_ms", ctypes.c_double),
         ("post_p50_ms", ctypes.c_double),
         ("post_p99_ms", ctypes.c_double),
+        ("lane_lps", ctypes.c_longlong),
+        ("lane_launches", ctypes.c_longlong),
     ]
 
     def as_dict(self):

@@ -21,7 +21,7 @@ LIB = os.path.join(PKG, "libtabsimplex.so")
 SOURCES = ["tabsimplex.cu", "batch.cu", "server.cu", "measure.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
-         "-Xcompiler", "-fvisibility=default", "-shared"]
+         "-Xcompiler", "-fvisibility=default", "-Xcompiler", "-ffp-contract=off", "-shared"]
 
 
 def nvcc() -> str:

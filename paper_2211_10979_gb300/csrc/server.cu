@@ -94,6 +94,7 @@ struct Request {
     std::vector<double> x, y;
     Clock::time_point t_submit, t_admit, t_done;
     Clock::time_point t_launch, t_kernel;  // its solve's launch began / its kernel completed
+    lp_t h = nullptr;                     // its handle while in the continuous lane
     bool done = false;
 };
 
@@ -136,6 +137,18 @@ struct lp_server {
     bool stopping = false;
     bool started = false;
     Clock::time_point t_first, t_last;
+    // continuous lane (lps_options.continuous): the team launch, its poller,
+    // the requests in it, and those whose team is done (to be finished)
+    TeamLane* lane = nullptr;
+    std::thread poller;
+    std::unordered_map<lp_t, std::shared_ptr<Request>> in_lane;
+    std::deque<std::shared_ptr<Request>> finished;
+    std::condition_variable cv_fin;       // finishers wait for lane results
+    std::vector<std::thread> finishers;
+    bool lane_drained = false;            // the poller has ended: no more lane results
+    bool workers_done = false;            // every worker has left (no more admissions)
+    int lane_admitting = 0;               // workers between taking lane requests and submitting them
+    long long lane_lps = 0;
 };
 
 void lps_options_init(lps_options* o) {
@@ -151,6 +164,7 @@ void lps_options_init(lps_options* o) {
     o->batch_max_bytes = 0;
     o->path = LP_PATH_MULTILAUNCH;
     o->team_blocks = 0;
+    o->continuous = 1;
 }
 
 // Keeps the calling worker's last library error for lps_last_error.
@@ -273,6 +287,10 @@ static void solve_batch(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs
 // Blocks a wave's team launch leaves free (8 SMs' worth on GB300) for the
 // previous wave's recovery and the micro-batches.
 constexpr int kWaveReserve = 16;
+// Blocks the continuous team launch leaves free (16 SMs' worth on GB300): it
+// stays resident while requests keep coming, so the micro-batches and the
+// FP64 recoveries run beside it all the time.
+constexpr int kLaneReserve = 32;
 
 // Solves the requests too large for the micro-batches together: one
 // lp_solve_many call (a team of blocks per LP) on the calling worker thread.
@@ -362,6 +380,146 @@ static void solve_wave(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs,
     sv->wave_launch_ms += ms_of(t2, t3);
 }
 
+// Continuous lane: creates the handles of admitted large requests and hands
+// them to the running team launch; a request that does not fit a team is
+// solved here by lp_solve.  Returns the requests completed on this thread.
+static std::vector<std::shared_ptr<Request>> lane_admit(lp_server* sv, std::vector<std::shared_ptr<Request>>& rs,
+                                                        cudaStream_t s) {
+    std::vector<std::shared_ptr<Request>> now;
+    for (auto& rp : rs) {
+        Request& r = *rp;
+        lp_t h = r.on_device ? create_device_unchecked(r.m, r.n, r.dA, r.db, r.dc, s)
+                             : lp_create(r.m, r.n, r.hA.data(), r.hb.data(), r.hc.data());
+        if (!h) {
+            note_error(sv, "create");
+            r.status = LP_ERR_INVALID;
+            now.push_back(rp);
+            continue;
+        }
+        r.h = h;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->in_lane[h] = rp;
+        }
+        r.t_launch = Clock::now();
+        const long long tok = lane_submit(sv->lane, h);
+        if (tok >= 0) continue;
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            sv->in_lane.erase(h);
+        }
+        r.h = nullptr;
+        if (tok == -2) {   // larger than a team's shared memory: the single-LP path
+            lp_destroy(h);
+            solve_single(sv, r, s);
+        } else {
+            note_error(sv, "lane");
+            r.status = LP_ERR_CUDA;
+            lp_destroy(h);
+        }
+        now.push_back(rp);
+    }
+    return now;
+}
+
+// A request whose team is done: statistics, FP64 recovery, read-out.
+static void lane_complete(lp_server* sv, Request& r, cudaStream_t s) {
+    lp_status st = LP_ERR_STATE;
+    if (lane_finish(sv->lane, r.h, s, &st) != LP_OPTIMAL) {
+        note_error(sv, "lane finish");
+        st = LP_ERR_CUDA;
+    }
+    r.status = st;
+    if (r.status < 0) note_error(sv, "lane solve");
+    r.x.assign(r.n, 0.0);
+    r.y.assign(r.m, 0.0);
+    long long it = 0;
+    if (r.status >= 0) lp_get_solution(r.h, r.x.data(), r.y.data(), &r.obj, nullptr, &it);
+    r.iters = it;
+    lp_destroy(r.h);
+    r.h = nullptr;
+}
+
+// Polls the lane for requests whose team is done and hands them to the
+// workers; relaunches the team kernel when jobs wait (lane_poll).
+static void poller_main(lp_server* sv) {
+    cudaSetDevice(sv->device);
+    std::vector<lp_t> done;
+    for (;;) {
+        done.clear();
+        const int left = lane_poll(sv->lane, done);
+        if (!done.empty()) {
+            const auto now = Clock::now();
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                for (lp_t h : done) {
+                    auto it = sv->in_lane.find(h);
+                    if (it == sv->in_lane.end()) continue;
+                    it->second->t_kernel = now;
+                    sv->finished.push_back(it->second);
+                    sv->in_lane.erase(it);
+                }
+            }
+            sv->cv_fin.notify_all();
+            continue;
+        }
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            if (sv->stopping && sv->queue.empty() && sv->in_lane.empty() && sv->lane_admitting == 0 && left == 0 &&
+                sv->workers_done)
+                break;
+        }
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->lane_drained = true;
+    }
+    sv->cv_fin.notify_all();
+}
+
+// Finishes lane requests whose team is done (FP64 recovery, read-out), on
+// threads of their own so that admission and micro-batches never wait for them.
+static void finisher_main(lp_server* sv) {
+    cudaSetDevice(sv->device);
+    use_default_allocator(true);
+    cudaStream_t s = nullptr;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    for (;;) {
+        std::shared_ptr<Request> r;
+        {
+            std::unique_lock<std::mutex> lk(sv->mu);
+            sv->cv_fin.wait(lk, [&] { return !sv->finished.empty() || sv->lane_drained; });
+            if (sv->finished.empty()) break;
+            r = sv->finished.front();
+            sv->finished.pop_front();
+        }
+        lane_complete(sv, *r, s);
+        {
+            std::lock_guard<std::mutex> lk(sv->mu);
+            const auto now = Clock::now();
+            r->t_done = now;
+            r->done = true;
+            sv->used -= (long long)r->bytes;
+            ++sv->completed;
+            ++sv->lane_lps;
+            sv->lat_ms.push_back(1e3 * std::chrono::duration<double>(r->t_done - r->t_submit).count());
+            sv->queue_ms.push_back(1e3 * std::chrono::duration<double>(r->t_admit - r->t_submit).count());
+            sv->wait_ms.push_back(1e3 * std::chrono::duration<double>(r->t_launch - r->t_admit).count());
+            sv->run_ms.push_back(1e3 * std::chrono::duration<double>(r->t_kernel - r->t_launch).count());
+            sv->post_ms.push_back(1e3 * std::chrono::duration<double>(r->t_done - r->t_kernel).count());
+            r->hA.clear();
+            r->hA.shrink_to_fit();
+            r->hb.clear();
+            r->hc.clear();
+            sv->t_last = now;
+        }
+        sv->cv_done.notify_all();
+        sv->cv_work.notify_all();   // budget freed
+    }
+    cudaStreamDestroy(s);
+}
+
 static void worker_main(lp_server* sv) {
     cudaSetDevice(sv->device);
     use_default_allocator(true);
@@ -377,7 +535,8 @@ static void worker_main(lp_server* sv) {
             // is being prepared or waits for the previous one's launch, large
             // requests wait for the wave after it and the other workers serve
             // the small ones.
-            const bool waves = sv->team_blocks >= 0;
+            const bool lane = sv->lane != nullptr;
+            const bool waves = sv->team_blocks >= 0 && !lane;
             auto pick = [&]() -> std::deque<std::shared_ptr<Request>>::iterator {
                 for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
                     const bool large = !((*it)->small && sv->opt.batch_small);
@@ -402,8 +561,8 @@ static void worker_main(lp_server* sv) {
             sv->used += (long long)head->bytes;
             take.push_back(head);
             const bool head_large = !(head->small && sv->opt.batch_small);
-            if (waves && head_large) {
-                sv->wave_pending = true;
+            if ((waves || lane) && head_large) {
+                if (waves) sv->wave_pending = true;
                 for (auto it = sv->queue.begin(); it != sv->queue.end() && (int)take.size() < sv->opt.batch_max;) {
                     const bool large = !((*it)->small && sv->opt.batch_small);
                     if (large && sv->used + (long long)(*it)->bytes <= sv->opt.budget_bytes) {
@@ -428,9 +587,20 @@ static void worker_main(lp_server* sv) {
             sv->peak = std::max(sv->peak, sv->used);
             const auto now = Clock::now();
             for (auto& r : take) r->t_admit = now;
+            if (lane && head_large) ++sv->lane_admitting;
         }
         const bool large = !(take[0]->small && sv->opt.batch_small);
-        if (large && sv->team_blocks >= 0)
+        if (large && sv->lane) {
+            // handed to the running team launch: finished later by a worker,
+            // except requests that failed or were solved here
+            take = lane_admit(sv, take, s);
+            {
+                std::lock_guard<std::mutex> lk(sv->mu);
+                --sv->lane_admitting;
+            }
+            sv->cv_work.notify_all();
+            if (take.empty()) continue;
+        } else if (large && sv->team_blocks >= 0)
             solve_wave(sv, take, s);
         else if (large)
             solve_single(sv, *take[0], s);
@@ -485,6 +655,19 @@ lps_t lps_open(const lps_options* opt) {
     sv->team_blocks = sv->opt.team_blocks < 0 ? -1 : sv->opt.team_blocks;
     sv->blocks = sv->opt.blocks_per_lp > 0 ? sv->opt.blocks_per_lp
                                            : std::max(16, 4 * nsm / std::max(1, sv->opt.workers));
+    if (sv->opt.continuous && sv->team_blocks >= 0) {
+        lp_options lo;
+        lp_options_init(&lo);
+        lo.precision = sv->opt.precision;
+        lo.blocks = sv->team_blocks;
+        sv->lane = lane_open(&lo, kLaneReserve);
+        if (!sv->lane) {
+            delete sv;
+            return nullptr;
+        }
+        sv->poller = std::thread(poller_main, sv);
+        for (int w = 0; w < sv->opt.workers; ++w) sv->finishers.emplace_back(finisher_main, sv);
+    }
     for (int w = 0; w < sv->opt.workers; ++w) sv->workers.emplace_back(worker_main, sv);
     return sv;
 }
@@ -645,6 +828,8 @@ lp_status lps_get_stats(lps_t sv, lps_stats* st) {
     st->wave_wait_ms = sv->wave_wait_ms;
     st->wave_launch_ms = sv->wave_launch_ms;
     st->peak_bytes = sv->peak;
+    st->lane_lps = sv->lane_lps;
+    st->lane_launches = sv->lane ? lane_launches(sv->lane) : 0;
     return LP_OPTIMAL;
 }
 
@@ -664,5 +849,12 @@ void lps_close(lps_t sv) {
     }
     sv->cv_work.notify_all();
     for (auto& t : sv->workers) t.join();
+    {
+        std::lock_guard<std::mutex> lk(sv->mu);
+        sv->workers_done = true;
+    }
+    if (sv->poller.joinable()) sv->poller.join();
+    for (auto& t : sv->finishers) t.join();
+    if (sv->lane) lane_close(sv->lane);
     delete sv;
 }

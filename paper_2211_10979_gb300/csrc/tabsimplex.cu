@@ -19,6 +19,7 @@
 #include "tabsimplex.h"
 #include "tsx_cluster.cuh"
 #include "tsx_host.h"
+#include "tsx_hybrid_host.h"
 #include "tsx_kernels.cuh"
 #include "tsx_recover.cuh"
 #include "tsx_team.cuh"
@@ -116,6 +117,9 @@ struct RecBufs {                     // FP64 recovery buffers
     double *M = nullptr, *inv = nullptr, *xS = nullptr, *yR = nullptr, *bR = nullptr, *cS = nullptr;
     double *rp = nullptr, *rd = nullptr, *aS = nullptr, *rho = nullptr, *venter = nullptr;
     int *pivrow = nullptr, *S = nullptr, *Rr = nullptr;
+    int* pivstep = nullptr;          // in-place refactorisation: step of each pivot row
+    double* dpiv = nullptr;          // its pivot elements
+    void* parts = nullptr;           // its per-block pivot-search posts (2 x kRecMaxGrid)
 };
 
 struct lp_handle {
@@ -321,6 +325,8 @@ void lp_options_init(lp_options* o) {
     o->recover_tol = 1e-9;
     o->cleanup_max = 1000;
     o->layout = LP_LAYOUT_CONDENSED;
+    o->gpu_share = 0.95;
+    o->cpu_threads = 0;
 }
 
 static void destroy_impl(lp_handle* h) {
@@ -731,6 +737,171 @@ static cudaError_t launch_cluster(const ClusterParams& P, int C, cudaStream_t s)
     return cudaLaunchKernelEx(&cfg, k_cluster_solve<NT>, P);
 }
 
+// ------------------------------------------------------- hybrid path
+// The paper's CPU+GPU split (Section IV) on the handle's built condensed
+// tableau: the first nG = round(gpu_share n) column slots and a copy of the
+// right-hand side go to a GPU tableau for k_pivot_hybrid (tsx_hybrid.cuh), the
+// other slots and another copy of the right-hand side to host memory for the
+// host team (tsx_hybrid_host.h); both run to the end, then the parts are put
+// back into the handle's tableau, var[] and basis, and the GPU's state words
+// into the handle's (the caller reads the status from there).
+template <int NT>
+static lp_status run_hybrid(lp_handle* h, const lp_options& o, cudaStream_t s, const Params<double>& Pf,
+                            double eps_d, double eps_p, long long& launches, int& grid_used) {
+    const int m = h->m, n = h->n, ld = h->work.ld;
+    const int nG = (int)std::min<long long>(n, std::max<long long>(0, std::llround(o.gpu_share * n)));
+    const int nC = n - nG;
+    const int ldG = tableau_ld(nG + 1, 8), ldC = nC + 1;
+    const int nstrips = (ldG + 127) / 128;
+    double* T = (double*)h->work.T;
+    // the GPU part
+    Carve cv;
+    const size_t o_T = cv.take((size_t)(m + 1) * ldG * 8), o_F = cv.take((size_t)(m + 1) * 8);
+    const size_t o_R = cv.take((size_t)ldG * 8), o_cp = cv.take((size_t)nstrips * sizeof(ArgPart));
+    const size_t o_rp = cv.take((size_t)h->max_grid * sizeof(RatPart)), o_var = cv.take((size_t)std::max(1, nG) * 4);
+    const size_t o_bas = cv.take((size_t)m * 4), o_st = cv.take(sizeof(DevState));
+    Block gblk;
+    if (!dev_alloc_block(h, gblk, align_up(cv.off, 256))) {
+        set_error("lp_solve: device allocation of the hybrid path's GPU part failed");
+        return LP_ERR_NOMEM;
+    }
+    char* gb = (char*)gblk.ptr;
+    double* TG = (double*)(gb + o_T);
+    int* varG = (int*)(gb + o_var);
+    int* basG = (int*)(gb + o_bas);
+    DevState* stG = (DevState*)(gb + o_st);
+    // the host part (pageable) and the mailbox with the column buffers (mapped)
+    std::vector<double> TC((size_t)(m + 1) * ldC), FC((size_t)m + 1), RC((size_t)ldC);
+    std::vector<int> varC(std::max(1, nC)), basC(m);
+    const size_t mbytes = sizeof(HybMailbox) + 4 * ((size_t)m + 1) * sizeof(double);
+    char* mh = nullptr;
+    char* md = nullptr;
+    lp_status rc = LP_OPTIMAL;
+    auto fail = [&](lp_status st, const char* what) {
+        set_error("lp_solve (hybrid): %s", what);
+        rc = st;
+    };
+    if (cudaHostAlloc((void**)&mh, mbytes, cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void**)&md, mh, 0) != cudaSuccess) {
+        cudaGetLastError();
+        if (mh) cudaFreeHost(mh);
+        dev_free(h, gblk);
+        set_error("lp_solve (hybrid): mapped host memory for the mailbox failed");
+        return LP_ERR_NOMEM;
+    }
+    memset(mh, 0, mbytes);
+    HybMailbox* mb = (HybMailbox*)mh;
+    double* gF = (double*)(mh + sizeof(HybMailbox));
+    double* cF = gF + 2 * ((size_t)m + 1);
+    // split the built tableau
+    {
+        std::vector<int> iota(std::max(1, nG));
+        for (int j = 0; j < nG; ++j) iota[j] = j;
+        for (int j = 0; j < nC; ++j) varC[j] = nG + j;
+        bool ok = cudaMemsetAsync(TG, 0, (size_t)(m + 1) * ldG * 8, s) == cudaSuccess;
+        if (nG > 0)
+            ok = ok && cudaMemcpy2DAsync(TG, (size_t)ldG * 8, T, (size_t)ld * 8, (size_t)nG * 8, m + 1,
+                                         cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+        ok = ok && cudaMemcpy2DAsync(TG + nG, (size_t)ldG * 8, T + n, (size_t)ld * 8, 8, m + 1,
+                                     cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+        if (nC > 0)
+            ok = ok && cudaMemcpy2DAsync(TC.data(), (size_t)ldC * 8, T + nG, (size_t)ld * 8, (size_t)nC * 8, m + 1,
+                                         cudaMemcpyDeviceToHost, s) == cudaSuccess;
+        ok = ok && cudaMemcpy2DAsync(TC.data() + nC, (size_t)ldC * 8, T + n, (size_t)ld * 8, 8, m + 1,
+                                     cudaMemcpyDeviceToHost, s) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(basG, h->basis, (size_t)m * 4, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+        ok = ok && cudaMemcpyAsync(basC.data(), h->basis, (size_t)m * 4, cudaMemcpyDeviceToHost, s) == cudaSuccess;
+        if (nG > 0)
+            ok = ok && cudaMemcpyAsync(varG, iota.data(), (size_t)nG * 4, cudaMemcpyHostToDevice, s) == cudaSuccess;
+        k_reset_state<<<1, 32, 0, s>>>(stG);
+        ok = ok && cudaGetLastError() == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
+        if (!ok) fail(LP_ERR_CUDA, "splitting the tableau failed");
+    }
+    if (rc == LP_OPTIMAL) {
+        Params<double> P = make_params<double>(m, nG, ldG, TG, (double*)(gb + o_F), (double*)(gb + o_R), nullptr,
+                                               (ArgPart*)(gb + o_cp), (RatPart*)(gb + o_rp), stG, basG, o, eps_d,
+                                               eps_p, varG);
+        P.log_cap = Pf.log_cap;
+        P.qlog = Pf.qlog;
+        P.plog = Pf.plog;
+        int coresident = 0;
+        const int grid = pivot_grid<NT, double>(h->device, m, ldG, h->max_grid, o.blocks, coresident);
+        HybParams HP{};
+        HP.mb = (HybMailbox*)md;
+        HP.gF = (double*)(md + sizeof(HybMailbox));
+        HP.cF = HP.gF + 2 * ((size_t)m + 1);
+        HP.wait_ns = std::max(0LL, o.barrier_timeout_ns);
+        void* args[] = {(void*)&P, (void*)&HP};
+        if (cudaLaunchCooperativeKernel((const void*)k_pivot_hybrid<NT>, grid, NT, args, 0, s) != cudaSuccess) {
+            cudaGetLastError();
+            fail(LP_ERR_CUDA, "cooperative launch of the GPU part failed");
+        } else {
+            ++launches;
+            grid_used = grid;
+            HybHost H;
+            H.m = m;
+            H.nC = nC;
+            H.ldC = ldC;
+            H.T = TC.data();
+            H.var = varC.data();
+            H.basis = basC.data();
+            H.F = FC.data();
+            H.R = RC.data();
+            H.mb = mb;
+            H.gF = gF;
+            H.cF = cF;
+            H.eps_d = eps_d;
+            H.eps_p = eps_p;
+            H.max_iters = P.max_iters;
+            H.k_cyc = o.k_cyc;
+            H.rule = o.rule;
+            H.wait_ns = std::max(1LL, o.barrier_timeout_ns);
+            const int hw = (int)std::thread::hardware_concurrency();
+            H.nthreads = o.cpu_threads > 0 ? o.cpu_threads : std::max(1, hw - 1);
+            HybTeam team(H);
+            team.run();
+            DevState gs{};
+            if (cudaMemcpyAsync(&gs, stG, sizeof gs, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+                cudaStreamSynchronize(s) != cudaSuccess) {
+                cudaGetLastError();
+                fail(LP_ERR_CUDA, "the GPU part failed");
+            } else if (gs.status == kTimeout || H.status == kTimeout) {
+                gs.status = kTimeout;
+                set_error("lp_solve (hybrid): a wait for the other side exceeded %lld ns", (long long)HP.wait_ns);
+            } else if (gs.status != H.status || gs.iters != H.iters) {
+                fail(LP_ERR_CUDA, "the GPU and host parts ended differently");
+            }
+            if (rc == LP_OPTIMAL) {
+                // put the parts back: slots [0, nG) and the right-hand side from the
+                // GPU, [nG, n) from the host; var[], basis and the state words
+                bool ok = true;
+                if (nG > 0) {
+                    ok = ok && cudaMemcpy2DAsync(T, (size_t)ld * 8, TG, (size_t)ldG * 8, (size_t)nG * 8, m + 1,
+                                                 cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+                    ok = ok && cudaMemcpyAsync(h->work.var, varG, (size_t)nG * 4, cudaMemcpyDeviceToDevice, s) ==
+                                   cudaSuccess;
+                }
+                ok = ok && cudaMemcpy2DAsync(T + n, (size_t)ld * 8, TG + nG, (size_t)ldG * 8, 8, m + 1,
+                                             cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+                if (nC > 0) {
+                    ok = ok && cudaMemcpy2DAsync(T + nG, (size_t)ld * 8, TC.data(), (size_t)ldC * 8, (size_t)nC * 8,
+                                                 m + 1, cudaMemcpyHostToDevice, s) == cudaSuccess;
+                    ok = ok && cudaMemcpyAsync(h->work.var + nG, varC.data(), (size_t)nC * 4, cudaMemcpyHostToDevice,
+                                               s) == cudaSuccess;
+                }
+                ok = ok && cudaMemcpyAsync(h->basis, basG, (size_t)m * 4, cudaMemcpyDeviceToDevice, s) == cudaSuccess;
+                ok = ok && cudaMemcpyAsync(h->st, &gs, sizeof gs, cudaMemcpyHostToDevice, s) == cudaSuccess;
+                ok = ok && cudaStreamSynchronize(s) == cudaSuccess;
+                if (!ok) fail(LP_ERR_CUDA, "reassembling the tableau failed");
+            }
+        }
+    }
+    cudaStreamSynchronize(s);
+    cudaFreeHost(mh);
+    dev_free(h, gblk);
+    return rc;
+}
+
 // Runs the pivot phase (build + Steps 1-3) on the handle's tableau of V.
 template <int NT, typename V>
 static lp_status pivot_phase(lp_handle* h, const lp_options& o, cudaStream_t s, double eps_d, double eps_p,
@@ -757,6 +928,14 @@ static lp_status pivot_phase(lp_handle* h, const lp_options& o, cudaStream_t s, 
         set_error("lp_solve: the cluster path needs an FP64 condensed tableau that fits one cluster's shared memory");
         return LP_ERR_INVALID;
     }
+    if (path == LP_PATH_HYBRID && !(sizeof(V) == 8 && h->work.cond)) {
+        set_error("lp_solve: the hybrid path needs an FP64 condensed tableau");
+        return LP_ERR_INVALID;
+    }
+    if (path == LP_PATH_HYBRID && (!coop || coresident <= 0)) {
+        set_error("lp_solve: the hybrid path needs a cooperative launch");
+        return LP_ERR_CUDA;
+    }
     if (path == LP_PATH_AUTO && csize) path = LP_PATH_CLUSTER;
     if (path == LP_PATH_AUTO) path = (coop && coresident > 0) ? LP_PATH_PERSISTENT : LP_PATH_MULTILAUNCH;
     if (path == LP_PATH_PERSISTENT && (!coop || coresident <= 0)) {
@@ -779,6 +958,12 @@ static lp_status pivot_phase(lp_handle* h, const lp_options& o, cudaStream_t s, 
     launches += 2;
 
     int grid_run = grid;
+    if constexpr (sizeof(V) == 8) {
+        if (path == LP_PATH_HYBRID) {
+            const lp_status hr = run_hybrid<NT>(h, o, s, P, eps_d, eps_p, launches, grid_run);
+            if (hr != LP_OPTIMAL) return hr;
+        }
+    }
     if (path == LP_PATH_CLUSTER) {
         ClusterParams CP{};
         CP.T = (double*)h->work.T;
@@ -836,6 +1021,8 @@ static lp_status pivot_phase(lp_handle* h, const lp_options& o, cudaStream_t s, 
 }
 
 // ------------------------------------------------------------ FP64 recovery
+constexpr int kRecMaxGrid = 152 * 8;   // blocks of the in-place refactorisation, upper bound
+
 static lp_status ensure_recovery(lp_handle* h, int k) {
     RecBufs& r = h->rec;
     const int m = h->m, n = h->n;
@@ -872,6 +1059,8 @@ static lp_status ensure_recovery(lp_handle* h, int k) {
         for (auto& o : o_v) o = cv.take(K * 8);
         size_t o_i[3];
         for (auto& o : o_i) o = cv.take(K * 4);
+        const size_t o_ps = cv.take(K * 4), o_dp = cv.take(K * 8);
+        const size_t o_parts = cv.take(2 * (size_t)kRecMaxGrid * sizeof(PivVal));
         if (!dev_alloc_block(h, r.kb, align_up(cv.off, 256))) {
             set_error("lp_solve: allocation of the recovery matrices (k = %d) failed", k);
             r.kcap = -1;
@@ -884,6 +1073,9 @@ static lp_status ensure_recovery(lp_handle* h, int k) {
         for (int t = 0; t < 9; ++t) *vs[t] = (double*)(b + o_v[t]);
         int** is[3] = {&r.pivrow, &r.S, &r.Rr};
         for (int t = 0; t < 3; ++t) *is[t] = (int*)(b + o_i[t]);
+        r.pivstep = (int*)(b + o_ps);
+        r.dpiv = (double*)(b + o_dp);
+        r.parts = b + o_parts;
         r.kcap = kc;
     }
     return LP_OPTIMAL;
@@ -908,28 +1100,65 @@ static lp_status recover_factor(lp_handle* h, const lp_options& o, cudaStream_t 
     int singular = 0;
     if (k > 0) {
         const size_t kk = (size_t)k;
-        k_rec_gather<<<grid_for((long long)(2 * kk * kk), 256, 152 * 16), 256, 0, s>>>(n, h->A, r.S, r.Rr, k, r.M);
         CUDA_TRY(cudaMemsetAsync(r.singular, 0, 4, s), LP_ERR_CUDA);
         k_reset_state<<<1, 32, 0, s>>>(r.rst);
-        int nsm = 0, per = 0;
+        int nsm = 0, per = 0, optin = 0;
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
         const size_t bits = sizeof(unsigned) * ((kk + 31) / 32);
-        if (bits > 48 * 1024) {
-            set_error("lp_solve: k = %d structural basic variables exceed the refactorisation's limit", k);
-            return LP_ERR_INVALID;
-        }
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rec_gauss_jordan<256>, 256, bits);
-        int g = std::max(1, std::min(nsm * std::max(per, 1), grid_for((long long)(2 * kk * kk), 256, 1 << 20)));
-        if (o.blocks > 0) g = std::min(g, o.blocks);   // blocks per LP
         int* sg = r.singular;
         int* pv = r.pivrow;
         double* Mx = r.M;
         DevState* rs = r.rst;
         long long to = std::max(0LL, o.barrier_timeout_ns);
         int kv = k;
-        void* args[] = {&Mx, &kv, &pv, &sg, &rs, &to};
-        CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_rec_gauss_jordan<256>, g, 256, args, bits, s), LP_ERR_CUDA);
-        k_rec_finish<<<grid_for((long long)(kk * kk), 256, 152 * 16), 256, 0, s>>>(r.M, k, r.pivrow, r.inv);
+        const size_t smem_ip = kk * 8 + bits;   // pivot row + used-row bitmap
+        static std::once_flag once;
+        static size_t ip_limit = 0;             // dynamic shared memory the in-place kernel may use
+        std::call_once(once, [optin] {
+            cudaFuncAttributes fa{};
+            if (cudaFuncGetAttributes(&fa, k_rec_gj_inplace<256>) == cudaSuccess &&
+                (size_t)optin > fa.sharedSizeBytes) {
+                const size_t lim = (size_t)optin - fa.sharedSizeBytes;
+                if (cudaFuncSetAttribute((const void*)k_rec_gj_inplace<256>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lim) == cudaSuccess)
+                    ip_limit = lim;
+            }
+            cudaGetLastError();   // a refused attribute must not surface as a later launch's error
+        });
+        if (smem_ip <= ip_limit) {
+            // in place on the k x k block (k_rec_gj_inplace)
+            k_rec_gather_square<<<grid_for((long long)(kk * kk), 256, 152 * 16), 256, 0, s>>>(n, h->A, r.S, r.Rr, k,
+                                                                                            r.M);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rec_gj_inplace<256>, 256, smem_ip);
+            int g = std::max(1, std::min(std::min(nsm * std::max(per, 1), kRecMaxGrid),
+                                         grid_for(32LL * k, 256, 1 << 20)));
+            if (o.blocks > 0) g = std::min(g, o.blocks);   // blocks per LP
+            double* dp = r.dpiv;
+            PivVal* parts = (PivVal*)r.parts;
+            void* args[] = {&Mx, &kv, &pv, &dp, &parts, &sg, &rs, &to};
+            CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_rec_gj_inplace<256>, g, 256, args, smem_ip, s),
+                     LP_ERR_CUDA);
+            k_rec_pivstep<<<grid_for(k, 256, 1024), 256, 0, s>>>(r.pivrow, k, r.pivstep);
+            k_rec_finish_inplace<<<grid_for((long long)(kk * kk), 256, 152 * 16), 256, 0, s>>>(r.M, k, r.pivrow,
+                                                                                             r.pivstep, r.dpiv, r.inv);
+            launches += 2;
+        } else {
+            // [A_RS | I] (k x 2k), for k beyond the in-place kernel's shared memory
+            if (bits > 48 * 1024) {
+                set_error("lp_solve: k = %d structural basic variables exceed the refactorisation's limit", k);
+                return LP_ERR_INVALID;
+            }
+            k_rec_gather<<<grid_for((long long)(2 * kk * kk), 256, 152 * 16), 256, 0, s>>>(n, h->A, r.S, r.Rr, k,
+                                                                                          r.M);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_rec_gauss_jordan<256>, 256, bits);
+            int g = std::max(1, std::min(nsm * std::max(per, 1), grid_for((long long)(2 * kk * kk), 256, 1 << 20)));
+            if (o.blocks > 0) g = std::min(g, o.blocks);   // blocks per LP
+            void* args[] = {&Mx, &kv, &pv, &sg, &rs, &to};
+            CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_rec_gauss_jordan<256>, g, 256, args, bits, s),
+                     LP_ERR_CUDA);
+            k_rec_finish<<<grid_for((long long)(kk * kk), 256, 152 * 16), 256, 0, s>>>(r.M, k, r.pivrow, r.inv);
+        }
         k_rec_gather_rhs<<<grid_for(k, 256, 1024), 256, 0, s>>>(h->b, h->c, r.S, r.Rr, k, r.bR, r.cS);
         const int gw = grid_for(32LL * k, 256, 4096);
         k_rec_matvec<<<gw, 256, 0, s>>>(r.inv, k, r.bR, 0, nullptr, r.xS);
@@ -1169,8 +1398,8 @@ static lp_status solve_nt(lp_handle* h, const lp_options& o, cudaStream_t s) {
 }
 
 static bool options_valid(const lp_options& o) {
-    return o.eps_d >= 0.0 && o.eps_p >= 0.0 && o.rule >= 0 && o.rule <= 1 && o.path >= 0 && o.path <= 4 &&
-           o.path != LP_PATH_TEAM &&
+    return o.eps_d >= 0.0 && o.eps_p >= 0.0 && o.rule >= 0 && o.rule <= 1 && o.path >= 0 && o.path <= 5 &&
+           o.path != LP_PATH_TEAM && o.gpu_share >= 0.0 && o.gpu_share <= 1.0 && o.cpu_threads >= 0 &&
            o.log_capacity >= 0 && o.precision >= 0 && o.precision <= 1 && o.eps_d_fp32 >= 0.0 &&
            o.eps_p_fp32 >= 0.0 && o.recover_tol >= 0.0 && o.cleanup_max >= 0 &&
            (o.layout == LP_LAYOUT_CONDENSED || o.layout == LP_LAYOUT_FULL);
@@ -1254,7 +1483,8 @@ static lp_status finish_team_lp(lp_handle* h, const lp_options& o, cudaStream_t 
     const int m = h->m, ld = h->work.ld, E = 32 / elem;
     const double nsec = (double)(ld / E);
     h->stats.iters = ds.iters;
-    h->stats.pivot_ms = ms;
+    // ms < 0: a continuous launch, where the LP's team stamped its own start and end
+    h->stats.pivot_ms = ms >= 0.f ? (double)ms : 1e-6 * (double)(ds.phase_ns[1] - ds.phase_ns[0]);
     h->stats.dense_update_bytes = 2.0 * (double)(m + 1) * (double)h->W * elem * (double)ds.iters;
     h->stats.update_bytes = ((64.0 * (double)(m - 1) + 96.0) * nsec + 64.0 * (double)(m + 1) +
                              3.0 * elem * (double)ld) * (double)ds.iters;
@@ -1513,6 +1743,306 @@ static lp_status solve_many_t(std::vector<lp_handle*>& hs, const lp_options& o, 
         status[k] = solve_nt<NT>(hs[k], oa, s);
     }
     return LP_OPTIMAL;
+}
+
+// ------------------------------------------------ continuous team launch
+// The request server's lane for large LPs (k_team_serve in tsx_team.cuh):
+// one cooperative launch of teams that take jobs from rings in mapped host
+// memory while it runs.  The host publishes a job per admitted LP, polls the
+// per-job done words, and starts a new launch whenever jobs wait and the last
+// one has ended (teams exit after idle_ns without work).
+namespace {
+constexpr unsigned kLaneCap = 4096;               // ring entries per list
+constexpr long long kLaneIdleNs = 2'000'000;      // the teams exit 2 ms after the last one's work
+constexpr long long kLaneIdleCapNs = 10'000'000'000LL;   // bound on one team's wait for work
+constexpr double kLaneHeavyWork = 1.5e10;         // (m+1) (n+1) (m+n) above this: the wide teams' list
+}
+
+struct tsx::TeamLane {
+    std::mutex mu;
+    lp_options o{};
+    int device = 0, nsm = 0;
+    bool fp32 = false;
+    int reserve = 0;
+    int C = 16, CB = 64, grid = 0, nteams = 0;
+    size_t smem = 0;
+    int ld_cap = 0, rows_cap = 0;
+    // mapped host memory: rings, tails, done words, stop word
+    char* hmem = nullptr;
+    char* hmem_d = nullptr;
+    void* ring_h = nullptr;
+    unsigned *tail_h = nullptr, *done_h = nullptr, *stop_h = nullptr;
+    void* ring_d = nullptr;
+    unsigned *tail_d = nullptr, *done_d = nullptr, *stop_d = nullptr;
+    // device memory: heads, team states, team tables, job copies
+    void* dmem = nullptr;
+    size_t dmem_bytes = 0, o_teams = 0, o_tab = 0, o_jc = 0;
+    unsigned* head_d = nullptr;
+    cudaStream_t ks = nullptr;
+    cudaEvent_t kev = nullptr;
+    bool running = false;
+    long long launches = 0;
+    unsigned pub[2] = {0, 0};
+    struct Out {
+        lp_handle* h;
+        unsigned list, seq;
+    };
+    std::vector<Out> out;
+};
+
+template <typename V>
+static lp_status lane_launch(TeamLane* L) {
+    constexpr int NT = 256;
+    const int ntab = L->grid + 3 * L->nteams;
+    std::vector<int> tab;
+    tab.reserve(ntab);
+    std::vector<int> first, size, list;
+    int nw = 0;
+    {
+        int cap = L->grid;
+        const int nwide = std::max(0, std::min((cap / 2) / L->CB, 8));
+        for (int t = 0; t < nwide; ++t) {
+            first.push_back((int)tab.size());
+            size.push_back(L->CB);
+            list.push_back(1);
+            tab.insert(tab.end(), L->CB, (int)first.size() - 1);
+        }
+        nw = nwide;
+        while ((int)tab.size() + L->C <= cap) {
+            first.push_back((int)tab.size());
+            size.push_back(L->C);
+            list.push_back(0);
+            tab.insert(tab.end(), L->C, (int)first.size() - 1);
+        }
+    }
+    (void)nw;
+    const int grid = (int)tab.size(), nteams = (int)first.size();
+    tab.insert(tab.end(), first.begin(), first.end());
+    tab.insert(tab.end(), size.begin(), size.end());
+    tab.insert(tab.end(), list.begin(), list.end());
+    char* base = (char*)L->dmem;
+    CUDA_TRY(cudaMemcpyAsync(base + L->o_tab, tab.data(), sizeof(int) * tab.size(), cudaMemcpyHostToDevice, L->ks),
+             LP_ERR_CUDA);
+    CUDA_TRY(cudaMemsetAsync(base + L->o_teams, 0, sizeof(TeamState) * (size_t)nteams, L->ks), LP_ERR_CUDA);
+    CUDA_TRY(cudaMemsetAsync(L->head_d + 2, 0, sizeof(unsigned), L->ks), LP_ERR_CUDA);   // busy teams
+    TeamServeParams<V> P{};
+    P.tp.teams = (TeamState*)(base + L->o_teams);
+    P.tp.team_of = (const int*)(base + L->o_tab);
+    P.tp.first = P.tp.team_of + grid;
+    P.tp.size = P.tp.first + nteams;
+    P.tp.list = P.tp.size + nteams;
+    P.tp.eps_d = L->fp32 ? L->o.eps_d_fp32 : L->o.eps_d;
+    P.tp.eps_p = L->fp32 ? L->o.eps_p_fp32 : L->o.eps_p;
+    P.tp.max_iters = L->o.max_iters;
+    P.tp.k_cyc = L->o.k_cyc;
+    P.tp.rule = L->o.rule;
+    P.tp.timeout_ns = std::max(0LL, L->o.barrier_timeout_ns);
+    P.ring.jobs = (TeamJob<V>*)L->ring_d;
+    P.ring.tail = L->tail_d;
+    P.ring.done = L->done_d;
+    P.ring.stop = L->stop_d;
+    P.cap = kLaneCap;
+    P.head = L->head_d;
+    P.busy = L->head_d + 2;
+    P.jcopy = (TeamJob<V>*)(base + L->o_jc);
+    P.idle_ns = kLaneIdleNs;
+    P.idle_cap_ns = kLaneIdleCapNs;
+    int ldm = L->ld_cap;
+    void* args[] = {(void*)&P, (void*)&ldm};
+    CUDA_TRY(cudaLaunchCooperativeKernel((const void*)k_team_serve<NT, V>, grid, NT, args, L->smem, L->ks),
+             LP_ERR_CUDA);
+    CUDA_TRY(cudaEventRecord(L->kev, L->ks), LP_ERR_CUDA);
+    L->running = true;
+    ++L->launches;
+    return LP_OPTIMAL;
+}
+
+template <typename V>
+static lp_status lane_setup(TeamLane* L) {
+    constexpr int NT = 256;
+    constexpr int elem = (int)sizeof(V);
+    CUDA_TRY(cudaGetDevice(&L->device), LP_ERR_CUDA);
+    cudaDeviceGetAttribute(&L->nsm, cudaDevAttrMultiProcessorCount, L->device);
+    // shared memory for two blocks per SM: R (ld_cap entries) and the
+    // multipliers of a block's rows (rows_cap entries)
+    int per_sm = 0, reserved = 0;
+    cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, L->device);
+    cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, L->device);
+    cudaFuncAttributes fa{};
+    CUDA_TRY(cudaFuncGetAttributes(&fa, k_team_serve<NT, V>), LP_ERR_CUDA);
+    const size_t per_block = (size_t)per_sm / 2 - (size_t)reserved - fa.sharedSizeBytes - 1024;
+    const size_t entries = per_block / elem / 32 * 32;
+    L->ld_cap = (int)(entries * 3 / 4 / 32 * 32);
+    L->rows_cap = (int)entries - L->ld_cap;
+    L->smem = entries * elem;
+    CUDA_TRY(cudaFuncSetAttribute((const void*)k_team_serve<NT, V>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)L->smem),
+             LP_ERR_CUDA);
+    int per = 0;
+    CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_team_serve<NT, V>, NT, L->smem), LP_ERR_CUDA);
+    L->grid = per * L->nsm - L->reserve;
+    L->C = L->o.blocks > 0 ? std::min(L->o.blocks, kTeamMax) : 16;
+    if (L->grid < L->C) {
+        set_error("lane: the team kernel cannot be resident (%d blocks)", L->grid);
+        return LP_ERR_CUDA;
+    }
+    L->CB = std::min(std::min(4 * L->C, kTeamMax), std::max(L->C, L->grid / 2));
+    L->nteams = L->grid;   // upper bound for the tables
+    // mapped host memory
+    const size_t ring_bytes = sizeof(TeamJob<V>) * 2 * kLaneCap;
+    const size_t hbytes = ring_bytes + 64 + sizeof(unsigned) * 2 * kLaneCap + 64;
+    CUDA_TRY(cudaHostAlloc((void**)&L->hmem, hbytes, cudaHostAllocMapped), LP_ERR_NOMEM);
+    memset(L->hmem, 0, hbytes);
+    CUDA_TRY(cudaHostGetDevicePointer((void**)&L->hmem_d, L->hmem, 0), LP_ERR_CUDA);
+    L->ring_h = L->hmem;
+    L->tail_h = (unsigned*)(L->hmem + ring_bytes);
+    L->stop_h = L->tail_h + 4;
+    L->done_h = (unsigned*)(L->hmem + ring_bytes + 64);
+    L->ring_d = L->hmem_d;
+    L->tail_d = (unsigned*)(L->hmem_d + ring_bytes);
+    L->stop_d = L->tail_d + 4;
+    L->done_d = (unsigned*)(L->hmem_d + ring_bytes + 64);
+    // device memory
+    Carve cv;
+    const size_t o_head = cv.take(4 * sizeof(unsigned));   // heads [2], busy teams
+    L->o_teams = cv.take(sizeof(TeamState) * (size_t)L->nteams);
+    L->o_tab = cv.take(sizeof(int) * (size_t)(4 * L->grid + 8));
+    L->o_jc = cv.take(sizeof(TeamJob<V>) * (size_t)L->nteams);
+    L->dmem_bytes = align_up(cv.off, 256);
+    CUDA_TRY(cudaMalloc(&L->dmem, L->dmem_bytes), LP_ERR_NOMEM);
+    L->head_d = (unsigned*)((char*)L->dmem + o_head);
+    CUDA_TRY(cudaMemset(L->dmem, 0, L->dmem_bytes), LP_ERR_CUDA);
+    CUDA_TRY(cudaStreamCreateWithFlags(&L->ks, cudaStreamNonBlocking), LP_ERR_CUDA);
+    CUDA_TRY(cudaEventCreateWithFlags(&L->kev, cudaEventDisableTiming), LP_ERR_CUDA);
+    return LP_OPTIMAL;
+}
+
+TeamLane* tsx::lane_open(const lp_options* opt, int reserve_blocks) {
+    TeamLane* L = new TeamLane();
+    if (opt)
+        L->o = *opt;
+    else
+        lp_options_init(&L->o);
+    L->fp32 = L->o.precision == LP_PREC_FP32;
+    L->reserve = std::max(0, reserve_blocks);
+    const lp_status st = L->fp32 ? lane_setup<float>(L) : lane_setup<double>(L);
+    if (st != LP_OPTIMAL) {
+        lane_close(L);
+        return nullptr;
+    }
+    return L;
+}
+
+long long tsx::lane_submit(TeamLane* L, lp_t h) {
+    if (!L || !h) return -1;
+    const int elem = L->fp32 ? 4 : 8;
+    CUDA_TRY(cudaSetDevice(h->device), -1);
+    CUDA_TRY(cudaStreamWaitEvent(h->stream, h->ready, 0), -1);
+    if (ensure_work(h, elem, 1) != LP_OPTIMAL) return -1;
+    const int rows = (h->m + 1 + L->C - 1) / L->C;
+    if (h->work.ld > L->ld_cap || rows > L->rows_cap) return -2;   // solve it another way
+    h->stats = lp_stats{};
+    h->sol_ready = false;
+    h->final_basis.clear();
+    // the team resets the LP's state words when it takes the job; the
+    // buffers' stream-ordered allocation is complete before it is published
+    CUDA_TRY(cudaStreamSynchronize(h->stream), -1);
+    TeamJob<double> J{};   // same layout for both element types (pointers and ints)
+    J.A = h->A;
+    J.b = h->b;
+    J.c = h->c;
+    J.T = (double*)h->work.T;
+    J.basis = h->basis;
+    J.var = h->work.var;
+    J.st = h->st;
+    J.m = h->m;
+    J.n = h->n;
+    J.ld = h->work.ld;
+    const double work = (double)(h->m + 1) * (double)(h->n + 1) * (double)(h->m + h->n);
+    const unsigned l = work > kLaneHeavyWork ? 1u : 0u;
+    std::lock_guard<std::mutex> lk(L->mu);
+    if (L->out.size() >= (size_t)kLaneCap) {
+        set_error("lane: %u jobs outstanding", kLaneCap);
+        return -1;
+    }
+    const unsigned seq = L->pub[l];
+    const unsigned slot = l * kLaneCap + (seq & (kLaneCap - 1u));
+    memcpy((char*)L->ring_h + sizeof(TeamJob<double>) * slot, &J, sizeof J);
+    __atomic_store_n(L->done_h + slot, 0u, __ATOMIC_RELAXED);
+    L->pub[l] = seq + 1u;
+    __atomic_store_n(L->tail_h + l, seq + 1u, __ATOMIC_RELEASE);
+    L->out.push_back(TeamLane::Out{h, l, seq});
+    if (!L->running) {
+        const lp_status st = L->fp32 ? lane_launch<float>(L) : lane_launch<double>(L);
+        if (st != LP_OPTIMAL) return -1;
+    }
+    return (long long)l * kLaneCap + seq;
+}
+
+int tsx::lane_poll(TeamLane* L, std::vector<lp_t>& done) {
+    std::lock_guard<std::mutex> lk(L->mu);
+    for (size_t k = 0; k < L->out.size();) {
+        const TeamLane::Out& o = L->out[k];
+        const unsigned slot = o.list * kLaneCap + (o.seq & (kLaneCap - 1u));
+        if (__atomic_load_n(L->done_h + slot, __ATOMIC_ACQUIRE) == o.seq + 1u) {
+            done.push_back(o.h);
+            L->out[k] = L->out.back();
+            L->out.pop_back();
+        } else {
+            ++k;
+        }
+    }
+    if (L->running && cudaEventQuery(L->kev) == cudaSuccess) {
+        L->running = false;
+        unsigned head[2] = {0, 0};
+        if (cudaMemcpyAsync(head, L->head_d, sizeof head, cudaMemcpyDeviceToHost, L->ks) == cudaSuccess &&
+            cudaStreamSynchronize(L->ks) == cudaSuccess) {
+            // jobs a team claimed but did not finish (a team barrier ran out):
+            // their state still says running, which the finish reports
+            for (size_t k = 0; k < L->out.size();) {
+                const TeamLane::Out& o = L->out[k];
+                const unsigned slot = o.list * kLaneCap + (o.seq & (kLaneCap - 1u));
+                if ((int)(head[o.list] - o.seq) > 0 &&
+                    __atomic_load_n(L->done_h + slot, __ATOMIC_ACQUIRE) != o.seq + 1u) {
+                    done.push_back(o.h);
+                    L->out[k] = L->out.back();
+                    L->out.pop_back();
+                } else {
+                    ++k;
+                }
+            }
+            if (head[0] != L->pub[0] || head[1] != L->pub[1]) {
+                if ((L->fp32 ? lane_launch<float>(L) : lane_launch<double>(L)) != LP_OPTIMAL) cudaGetLastError();
+            }
+        } else {
+            cudaGetLastError();
+        }
+    }
+    return (int)L->out.size();
+}
+
+lp_status tsx::lane_finish(TeamLane* L, lp_t h, cudaStream_t s, lp_status* status) {
+    lp_options of = L->o;
+    of.blocks = L->reserve;
+    CUDA_TRY(cudaSetDevice(h->device), LP_ERR_CUDA);
+    return L->fp32 ? finish_team_lp<float>(h, of, s, -1.f, L->C, 256, status)
+                   : finish_team_lp<double>(h, of, s, -1.f, L->C, 256, status);
+}
+
+long long tsx::lane_launches(TeamLane* L) {
+    std::lock_guard<std::mutex> lk(L->mu);
+    return L->launches;
+}
+
+void tsx::lane_close(TeamLane* L) {
+    if (!L) return;
+    if (L->stop_h) __atomic_store_n(L->stop_h, 1u, __ATOMIC_RELEASE);
+    if (L->ks) cudaStreamSynchronize(L->ks);
+    if (L->kev) cudaEventDestroy(L->kev);
+    if (L->ks) cudaStreamDestroy(L->ks);
+    if (L->dmem) cudaFree(L->dmem);
+    if (L->hmem) cudaFreeHost(L->hmem);
+    delete L;
 }
 
 lp_status lp_solve_many(lp_t* handles, int count, const lp_options* opt, lp_status* status) {

@@ -5,6 +5,7 @@
 
 #include <cstddef>
 #include <functional>
+#include <vector>
 
 #include "tabsimplex.h"
 
@@ -55,6 +56,31 @@ lp_t create_device_unchecked(int m, int n, const double* dA, const double* db, c
 // launch has completed, before the per-LP bookkeeping and FP64 recovery.
 lp_status solve_many_hooked(lp_t* handles, int count, const lp_options* opt, lp_status* status,
                             int reserve_blocks, const std::function<void()>& after_kernel);
+
+// Continuous team launch for the request server (k_team_serve): LPs are
+// added while the launch runs, each solved by the next free team, and each
+// reports its end on its own.
+struct TeamLane;
+// Opens a lane with the given options (precision, tolerances, blocks = narrow
+// team size); the launch leaves `reserve_blocks` co-resident blocks free.
+// NULL on error.
+TeamLane* lane_open(const lp_options* opt, int reserve_blocks);
+// Adds an LP (a handle from lp_create or create_device_unchecked, not solved
+// concurrently elsewhere) and starts a launch if none runs.  Returns a token
+// >= 0; -2 if the LP does not fit a team's shared memory (solve it another
+// way); -1 on error.
+long long lane_submit(TeamLane* lane, lp_t h);
+// Appends the handles whose team has finished (or, after a launch ended, whose
+// team gave up) to `done`; starts a new launch when jobs wait and none runs.
+// Returns the number of LPs still in the lane; waits on the device only to
+// read the claim counters after a launch has ended.
+int lane_poll(TeamLane* lane, std::vector<lp_t>& done);
+// Statistics and, for FP32, the FP64 recovery of a finished LP on stream s
+// (as lp_solve_many); *status receives its outcome.
+lp_status lane_finish(TeamLane* lane, lp_t h, cudaStream_t s, lp_status* status);
+long long lane_launches(TeamLane* lane);
+// Stops the launch (teams leave once idle) and frees the lane.
+void lane_close(TeamLane* lane);
 
 }  // namespace tsx
 

@@ -106,6 +106,159 @@ __global__ void __launch_bounds__(NT) k_rec_gauss_jordan(double* M, int k, int* 
     }
 }
 
+// The same elimination in place on the k x k block (the default): step c
+// frees column c of M, which then holds the right-hand column of the pivot
+// row pr_c, i.e. what column k + pr_c of [A_RS | I] would hold (that column is
+// the unit vector of row pr_c until step c: M[pr_c][c] becomes 1, and every
+// other row r gets fma(-l_r, 1, 0) = -l_r).  Every stored value goes through
+// the same operations as in k_rec_gauss_jordan, in k^3 instead of 1.5 k^3
+// fused multiply-adds and half the memory.  A warp updates one row at a time
+// (its multiplier l_r = M[r][c] / M[pr][c] computed once), the pivot row is
+// staged in shared memory, and the next column's pivot search rides on the
+// update: each block posts its best (|M[r][c+1]|, r) over its unused rows, so
+// a step has one grid barrier.  dpiv[c] = the pivot element of step c.
+struct PivVal {
+    double v;     // |pivot candidate|, -1 if none
+    double val;   // its signed value
+    int r;        // its row (lowest on ties), INT_MAX if none
+    int pad;
+};
+
+__device__ __forceinline__ void pivval_merge(PivVal& a, const PivVal& b) {
+    if (b.v > a.v || (b.v == a.v && b.r < a.r)) a = b;
+}
+
+__device__ __forceinline__ PivVal warp_pivval(PivVal a) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        PivVal b;
+        b.v = __shfl_xor_sync(0xffffffffu, a.v, o);
+        b.val = __shfl_xor_sync(0xffffffffu, a.val, o);
+        b.r = __shfl_xor_sync(0xffffffffu, a.r, o);
+        pivval_merge(a, b);
+    }
+    return a;
+}
+
+template <int NT>
+__device__ __forceinline__ void block_post_pivval(PivVal a, PivVal* sp, PivVal* dst) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    a = warp_pivval(a);
+    if (lane == 0) sp[w] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        PivVal b = sp[0];
+        for (int q = 1; q < NT / 32; ++q) pivval_merge(b, sp[q]);
+        *dst = b;
+    }
+}
+
+template <int NT>
+__global__ void __launch_bounds__(NT) k_rec_gj_inplace(double* M, int k, int* pivrow, double* dpiv, PivVal* parts,
+                                                      int* singular, DevState* st, long long timeout_ns) {
+    __shared__ PivVal sp[NT / 32];
+    __shared__ BlockScratch s;
+    extern __shared__ double gj_smem[];
+    double* P = gj_smem;                                            // pivot row, k entries
+    unsigned* used_bits = reinterpret_cast<unsigned*>(P + k);      // rows used as pivots
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int gw = blockIdx.x * (NT / 32) + warp, nwarps = gridDim.x * (NT / 32);
+    const size_t kk = (size_t)k;
+    const int nwords = (k + 31) / 32;
+    for (int w = threadIdx.x; w < nwords; w += NT) used_bits[w] = 0u;
+    // pivot search of column 0
+    {
+        PivVal best{-1.0, 0.0, INT_MAX, 0};
+        for (int r = blockIdx.x * NT + threadIdx.x; r < k; r += gridDim.x * NT) {
+            const double v = __ldcg(M + r * kk);
+            pivval_merge(best, PivVal{fabs(v), v, r, 0});
+        }
+        block_post_pivval<NT>(best, sp, parts + blockIdx.x);
+    }
+    if (!grid_barrier(st, timeout_ns, s)) return;
+    for (int c = 0; c < k; ++c) {
+        const PivVal* cur = parts + (size_t)(c & 1) * gridDim.x;
+        PivVal* nxt = parts + (size_t)((c + 1) & 1) * gridDim.x;
+        // the pivot of column c: every block merges the same posts
+        PivVal pv{-1.0, 0.0, INT_MAX, 0};
+        for (int b = lane; b < (int)gridDim.x; b += 32) {
+            const PivVal q{__ldcg(&cur[b].v), __ldcg(&cur[b].val), __ldcg(&cur[b].r), 0};
+            pivval_merge(pv, q);
+        }
+        pv = warp_pivval(pv);   // every warp computes it
+        const int pr = pv.r;
+        if (pr == INT_MAX || !(pv.v > 0.0)) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) *singular = 1;
+            return;   // every block takes the same branch
+        }
+        const double ip = 1.0 / pv.val;
+        for (int j = threadIdx.x; j < k; j += NT) P[j] = j == c ? 1.0 : __ldcg(M + pr * kk + j);
+        if (threadIdx.x == 0) used_bits[pr >> 5] |= 1u << (pr & 31);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            pivrow[c] = pr;
+            dpiv[c] = pv.val;
+        }
+        __syncthreads();
+        PivVal best{-1.0, 0.0, INT_MAX, 0};
+        const int cn = c + 1;
+        for (int r = gw; r < k; r += nwarps) {
+            double* row = M + r * kk;
+            if (r == pr) {
+                if (lane == 0) row[c] = 1.0;
+                continue;
+            }
+            const double l = __ldcg(row + c) * ip;
+            const bool unused = !((used_bits[r >> 5] >> (r & 31)) & 1u);
+            // eight entries per lane in flight: all loads of a chunk before its stores
+            for (int j0 = lane; j0 < k; j0 += 32 * 8) {
+                double v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int j = j0 + 32 * u;
+                    v[u] = j < k ? __ldcg(row + j) : 0.0;
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int j = j0 + 32 * u;
+                    if (j < k) {
+                        const double w = __fma_rn(-l, P[j], j == c ? 0.0 : v[u]);
+                        row[j] = w;
+                        if (j == cn && unused) pivval_merge(best, PivVal{fabs(w), w, r, 0});
+                    }
+                }
+            }
+        }
+        if (cn < k) block_post_pivval<NT>(best, sp, nxt + blockIdx.x);
+        if (!grid_barrier(st, timeout_ns, s)) return;
+    }
+}
+
+// inv[c][a] = M[pivrow[c]][pivstep[a]] / dpiv[c] (pivstep = the inverse of
+// pivrow): the rows of A_RS^-1 from the in-place elimination.
+__global__ void k_rec_finish_inplace(const double* __restrict__ M, int k, const int* __restrict__ pivrow,
+                                     const int* __restrict__ pivstep, const double* __restrict__ dpiv,
+                                     double* __restrict__ inv) {
+    const size_t total = (size_t)k * k;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int c = (int)(t / k), a = (int)(t - (size_t)c * k);
+        inv[t] = M[(size_t)pivrow[c] * k + pivstep[a]] / dpiv[c];
+    }
+}
+
+__global__ void k_rec_pivstep(const int* __restrict__ pivrow, int k, int* __restrict__ pivstep) {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < k; c += gridDim.x * blockDim.x) pivstep[pivrow[c]] = c;
+}
+
+// M = A_RS, k x k row-major.
+__global__ void k_rec_gather_square(int n, const double* __restrict__ A, const int* __restrict__ S,
+                                    const int* __restrict__ Rr, int k, double* __restrict__ M) {
+    const size_t total = (size_t)k * k;
+    for (size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (size_t)gridDim.x * blockDim.x) {
+        const int a = (int)(t / k), b = (int)(t - (size_t)a * k);
+        M[t] = A[(size_t)Rr[a] * n + S[b]];
+    }
+}
+
 // inv[c][a] = M[pivrow[c]][k + a] / M[pivrow[c]][c]: the rows of A_RS^-1.
 __global__ void k_rec_finish(const double* __restrict__ M, int k, const int* __restrict__ pivrow,
                              double* __restrict__ inv) {

@@ -48,6 +48,7 @@ struct __align__(256) TeamState {   // one per team
     int job;
     int fail;                  // set when a team barrier wait ran out
     int bad;                   // the current LP's inputs are not finite or b < 0
+    unsigned seq;              // continuous launch: sequence number of the job
     ArgPart ent;               // next entering candidate (block 0)
     RatPart rat[kTeamMax];     // ratio-test partial of each block
 };
@@ -352,6 +353,160 @@ __global__ void __launch_bounds__(NT, team_sm_threads(NT) / NT) k_team_solve(Tea
         if (k < 0) return;
         const TeamJob<V> J = P.jobs[k];
         if (!team_solve_one<team_rows_in_flight(NT)>(P, J, ts, bt, C, R, Floc, s, sok, tpass)) return;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Continuous team launch (the request server's lane for large LPs): the same
+// teams and the same team_solve_one, but the jobs come from rings that the
+// host appends to while the launch runs, so an LP admitted at any moment is
+// taken by the next team that finishes one, and each LP reports its end on
+// its own instead of at the end of a launch.
+//   - rings in mapped host memory, one per list (light / heavy LPs): the host
+//     writes a job entry, then publishes it by a release store of the list's
+//     tail; a team's leader claims the next entry with a compare-and-swap on
+//     the list's head (device memory) after an acquire load of the tail, and
+//     copies the entry into device memory for the team;
+//   - when an LP is solved (after the team's commit barrier) the leader
+//     stores the job's sequence number + 1 into its done word (release,
+//     system scope), which the host polls;
+//   - a team that finds nothing to claim keeps polling while another team
+//     still works (a job published meanwhile is taken at once); once no team
+//     has had work for idle_ns (or the stop word is set) every team exits, and
+//     the host starts a new launch when jobs are waiting and none runs.  Every
+//     wait is bounded: the claim loop by idle_cap_ns and a spin cap, the team
+//     barriers as in k_team_solve (a team that gives up clears its busy mark).
+// ---------------------------------------------------------------------------
+template <typename V>
+struct ServeRing {
+    TeamJob<V>* jobs;          // host memory: 2 lists x cap entries
+    unsigned* tail;            // host memory: jobs published per list [2]
+    unsigned* done;            // host memory: per entry, its sequence number + 1 once solved
+    unsigned* stop;            // host memory: nonzero: teams with nothing to claim exit now
+};
+
+template <typename V>
+struct TeamServeParams {
+    TeamParams<V> tp;          // tolerances, rules and team tables (jobs, order, count, next unused)
+    ServeRing<V> ring;
+    unsigned cap;              // entries per list, a power of two
+    unsigned* head;            // device memory: jobs claimed per list [2]
+    unsigned* busy;            // device memory: teams solving a job (zero at launch)
+    TeamJob<V>* jcopy;         // device memory: per team, the job it solves
+    long long idle_ns;         // every team leaves once none has had work for this long
+    long long idle_cap_ns;     // bound on a team's wait while others still work
+};
+
+__device__ __forceinline__ unsigned ld_acquire_sys(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.sys.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_sys(unsigned* p, unsigned v) {
+    asm volatile("st.release.sys.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+template <int NT, typename V>
+__global__ void __launch_bounds__(NT, team_sm_threads(NT) / NT) k_team_serve(TeamServeParams<V> P, int ld_max) {
+    extern __shared__ __align__(32) unsigned char team_smem[];
+    __shared__ BlockScratch s;
+    __shared__ int sok;
+    __shared__ unsigned tpass;
+    if (threadIdx.x == 0) tpass = 0;
+    const int t = P.tp.team_of[blockIdx.x];
+    const int bt = blockIdx.x - P.tp.first[t];
+    const unsigned C = (unsigned)P.tp.size[t];
+    TeamState* ts = P.tp.teams + t;
+    V* R = reinterpret_cast<V*>(team_smem);
+    V* Floc = R + ld_max;
+    const int li = P.tp.list[t];
+    TeamJob<V>* jc = P.jcopy + t;
+    for (;;) {
+        if (bt == 0 && threadIdx.x == 0) {
+            ts->bad = 0;   // read after the next barrier; set during the build
+            int got = -1;
+            unsigned gseq = 0;
+            const long long t0 = global_ns();
+            const unsigned long long max_spins =
+                (unsigned long long)(P.idle_cap_ns > 0 ? P.idle_cap_ns : 0) / 500ull + 64ull;
+            long long t_idle = t0;   // since when no team has been seen working
+            for (unsigned long long spins = 0;; ++spins) {
+                for (int pass = 0; pass < 2 && got < 0; ++pass) {
+                    const int l = pass == 0 ? li : 1 - li;
+                    const unsigned tl = ld_acquire_sys(P.ring.tail + l);
+                    unsigned h = *(volatile unsigned*)(P.head + l);
+                    while ((int)(tl - h) > 0) {
+                        const unsigned prev = atomicCAS(P.head + l, h, h + 1u);
+                        if (prev == h) {
+                            got = l;
+                            gseq = h;
+                            break;
+                        }
+                        h = prev;
+                    }
+                }
+                if (got >= 0) {
+                    atomicAdd(P.busy, 1u);
+                    break;
+                }
+                const long long now = global_ns();
+                if (*(volatile unsigned*)P.busy != 0u) t_idle = now;
+                if (ld_acquire_sys(P.ring.stop) != 0u || now - t_idle >= P.idle_ns || now - t0 >= P.idle_cap_ns ||
+                    spins >= max_spins)
+                    break;
+                __nanosleep(500);
+            }
+            if (got >= 0) {
+                const unsigned slot = (unsigned)got * P.cap + (gseq & (P.cap - 1u));
+                const volatile unsigned long long* src =
+                    reinterpret_cast<const volatile unsigned long long*>(P.ring.jobs + slot);
+                unsigned long long* dst = reinterpret_cast<unsigned long long*>(jc);
+                for (int w = 0; w < (int)(sizeof(TeamJob<V>) / 8); ++w) dst[w] = src[w];
+                ts->job = (int)slot;
+                ts->seq = gseq;
+            } else {
+                ts->job = -1;
+            }
+        }
+        if (!team_barrier(ts, C, P.tp.timeout_ns, sok, tpass)) return;
+        const int slot = *(volatile const int*)&ts->job;
+        if (slot < 0) return;
+        TeamJob<V> J;
+        {
+            const unsigned long long* src = reinterpret_cast<const unsigned long long*>(jc);
+            unsigned long long* dst = reinterpret_cast<unsigned long long*>(&J);
+            for (int w = 0; w < (int)(sizeof(TeamJob<V>) / 8); ++w) dst[w] = __ldcg(src + w);
+        }
+        if (bt == 0 && threadIdx.x == 0) {
+            // the LP's state words start from zero here (no reset launch per job)
+            DevState* st = J.st;
+            st->status = kRunning;
+            st->q = -1;
+            st->p = -1;
+            st->bland = 0;
+            st->degen_run = 0;
+            st->bad = 0;
+            st->iters = 0;
+            st->active_sectors = 0;
+            st->theta = 0.0;
+            st->bar_count = 0;
+            st->bar_gen = 0;
+            st->nact = 0;
+            st->next_slot = 0;
+            for (int q = 2; q < 6; ++q) st->phase_ns[q] = 0;
+            st->phase_ns[1] = 0;
+            st->phase_ns[0] = global_ns();
+        }
+        if (!team_solve_one<team_rows_in_flight(NT)>(P.tp, J, ts, bt, C, R, Floc, s, sok, tpass)) {
+            if (bt == 0 && threadIdx.x == 0) atomicSub(P.busy, 1u);
+            return;
+        }
+        if (bt == 0 && threadIdx.x == 0) {
+            J.st->phase_ns[1] = global_ns();
+            __threadfence_system();
+            st_release_sys(P.ring.done + slot, *(volatile unsigned*)&ts->seq + 1u);
+            atomicSub(P.busy, 1u);
+        }
     }
 }
 

@@ -46,6 +46,7 @@ def test_options_defaults_roundtrip(lib):
     assert o.log_capacity == 0 and o.stream is None
     assert o.precision == tsx.LP_PREC_FP64 and o.eps_d_fp32 == 1e-5 and o.eps_p_fp32 == 1e-6
     assert o.recover_tol == 1e-9 and o.cleanup_max == 1000
+    assert o.gpu_share == 0.95 and o.cpu_threads == 0
     assert "sm_103a" in tsx.lp_version()
 
 

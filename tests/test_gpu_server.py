@@ -50,14 +50,16 @@ def _alone_fp32(tsx, A, b, c):
         return st, pr.solution()
 
 
-def test_results_same_alone_and_in_the_mix(tsx):
-    # a mix of small (micro-batched) and larger (single-path) LPs submitted
-    # from two client threads while earlier ones are being solved
+@pytest.mark.parametrize("continuous", [1, 0])
+def test_results_same_alone_and_in_the_mix(tsx, continuous):
+    # a mix of small (micro-batched) and larger (team-solved) LPs submitted
+    # from two client threads while earlier ones are being solved; the large
+    # ones go to the continuous team launch (1) or to lp_solve_many waves (0)
     shapes = [(20, 30), (64, 64), (300, 250), (16, 128), (128, 16), (700, 400), (50, 50),
               (256, 1024), (90, 120), (33, 77), (1500, 600), (128, 128), (1200, 1100)] * 3
     problems = [lpgen.dense_lp(m, n, 4000 + k) for k, (m, n) in enumerate(shapes)]
     tickets = [None] * len(problems)
-    with tsx.Server(workers=4) as sv:
+    with tsx.Server(workers=4, continuous=continuous) as sv:
         def client(idx):
             for k in idx:
                 tickets[k] = sv.submit(*problems[k])
@@ -73,7 +75,12 @@ def test_results_same_alone_and_in_the_mix(tsx):
             results.append(sv.result(t))
         st = sv.stats()
     assert st["completed"] == len(problems) and st["batched_lps"] > 0
-    assert st["waves"] > 0 and st["wave_lps"] + st["batched_lps"] == len(problems)
+    if continuous:
+        assert st["waves"] == 0 and st["lane_launches"] >= 1
+        assert st["lane_lps"] + st["batched_lps"] == len(problems)
+    else:
+        assert st["lane_lps"] == 0 and st["waves"] > 0
+        assert st["wave_lps"] + st["batched_lps"] == len(problems)
     for k, ((m, n), (A, b, c), r) in enumerate(zip(shapes, problems, results)):
         ref = oracle.solve(A, b, c)
         if (m + 1) * (n + 2) * 8 < 200_000:
@@ -164,7 +171,32 @@ def test_plain_mode_and_stats(tsx):
             sv.submit(*lpgen.dense_lp(500, 500, 1))
 
 
-def test_invalid_device_request_in_a_wave(tsx):
+def test_request_admitted_into_running_work_finishes_first(tsx):
+    # a large LP is being solved by the continuous team launch when a medium
+    # one arrives: the medium one is taken by another team at once and its
+    # result comes back before the large one's (no wave boundary to wait for)
+    big = lpgen.dense_lp(4000, 4000, 31)
+    mid = lpgen.dense_lp(400, 300, 32)
+    with tsx.Server(workers=2) as sv:
+        tb = sv.submit(*big)
+        time.sleep(0.005)
+        tm = sv.submit(*mid)
+        assert sv.wait(tm, 120.0) == tsx.LP_OPTIMAL
+        assert sv.wait(tb, 0.0) == tsx.LP_PENDING      # the large one is still running
+        rm = sv.result(tm)
+        assert sv.wait(tb, 120.0) == tsx.LP_OPTIMAL
+        rb = sv.result(tb)
+        st = sv.stats()
+    assert rm.t_done < rb.t_done and st["lane_lps"] == 2
+    for (A, b, c), r in ((mid, rm), (big, rb)):
+        st1, alone = _alone_fp32(tsx, A, b, c)
+        assert st1 == tsx.LP_OPTIMAL and r.obj == alone.obj and r.iters == alone.iters
+        np.testing.assert_array_equal(r.x, alone.x)
+        np.testing.assert_array_equal(r.y, alone.y)
+
+
+@pytest.mark.parametrize("continuous", [1, 0])
+def test_invalid_device_request_in_a_wave(tsx, continuous):
     # device inputs are checked in the team kernel's build: a request with
     # b_i < 0 ends LP_ERR_INVALID, the others of its wave are unaffected
     import torch
@@ -178,7 +210,7 @@ def test_invalid_device_request_in_a_wave(tsx):
             b[7] = -1.0
         reqs.append((m, n, *(torch.from_numpy(v).cuda() for v in (A.ravel(), b, c))))
     torch.cuda.synchronize()
-    with tsx.Server(workers=2) as sv:
+    with tsx.Server(workers=2, continuous=continuous) as sv:
         tickets = [sv.submit_device(m, n, dA, db, dc) for (m, n, dA, db, dc) in reqs]
         codes = [sv.wait(t, 120.0) for t in tickets]
         res = [sv.result(t) for t in tickets]
