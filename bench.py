@@ -49,7 +49,8 @@ def parse_args(argv=None):
     ap.add_argument("--m", type=int, default=8192)
     ap.add_argument("--n", type=int, default=8192)
     ap.add_argument("--seeds", type=int, default=3, help="distinct LPs cycled through the steps")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=-1,
+                    help="solves of the e2e figure (default: as many as the timed steps)")
     ap.add_argument("--skip-zero", type=int, default=1)
     ap.add_argument("--max-iters", type=int, default=-1,
                     help="pivot cap per solve (a truncated solve; default: to the end)")
@@ -97,6 +98,8 @@ def parse_args(argv=None):
     args = ap.parse_args(argv)
     if args.steps is None:
         args.steps = 2000 if args.workload == "batch" else 6
+    if args.e2e_steps < 0:
+        args.e2e_steps = 3 if args.workload == "batch" else args.steps
     if args.precision == "fp32" and args.max_iters >= 0:
         # the FP32 path treats a pivot cap as the end of its float phase and
         # lets the FP64 cleanup finish the solve: a truncated FP32 solve is not
@@ -196,7 +199,7 @@ def measured_peaks():
         return 6800.0, "fallback"
 
 
-def profile_traffic(m, n, max_iters=-1, layout="condensed"):
+def profile_traffic(m, n, max_iters=-1, layout="condensed", grid=None, block=None):
     """ncu DRAM bytes per launch of the pivot kernel, if a summary for this
     exact kernel build and workload (FP64; a full solve, or the first
     max_iters pivots) is committed under profiles/."""
@@ -213,12 +216,68 @@ def profile_traffic(m, n, max_iters=-1, layout="condensed"):
     from paper_2211_10979_gb300 import build as b
     if ent.get("source_digest") != b.source_digest(b.PIVOT_SOURCES):
         return None   # the kernel changed since the counters were taken
+    if (grid, block) != (ent.get("grid", grid), ent.get("block", block)):
+        return None   # another launch shape
     return ent
+
+
+def host_cpu():
+    """The host's CPU model (lscpu, else /proc/cpuinfo) and its core count."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.split(":")[0].strip() == "Model name":
+                model = ln.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if model is None:
+        try:
+            with open("/proc/cpuinfo") as fh:
+                for ln in fh:
+                    if ln.lower().startswith(("model name", "cpu part")):
+                        model = ln.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    return {"cpu_model": model or "unknown", "nproc": os.cpu_count()}
+
+
+class pinned_to_one_core:
+    """Runs the block with the process pinned to one core (the last one the
+    process may use), then restores the previous affinity."""
+
+    def __enter__(self):
+        self.prev = None
+        try:
+            self.prev = os.sched_getaffinity(0)
+            self.core = max(self.prev)
+            os.sched_setaffinity(0, {self.core})
+        except (AttributeError, OSError):
+            self.core = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.prev is not None:
+            try:
+                os.sched_setaffinity(0, self.prev)
+            except OSError:
+                pass
 
 
 def oracle_sample(m, n, seed, budget_s):
     """The CPU oracle on a bounded sample of the workload: the tableau build and
-    the first K pivots of the same LP, K chosen so the pivots take ~budget_s."""
+    the first K pivots of the same LP, K chosen so the pivots take ~budget_s,
+    on one core (the process pinned to it)."""
+    with pinned_to_one_core() as pin:
+        r = _oracle_sample(m, n, seed, budget_s)
+    r.update(host_cpu())
+    r["pinned_core"] = pin.core
+    return r
+
+
+def _oracle_sample(m, n, seed, budget_s):
     import oracle
     A, b, c = lpgen.dense_lp(m, n, seed)
     t0 = time.perf_counter()
@@ -260,8 +319,9 @@ def run_reference(args, rank, world):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"dense LP m={args.m} n={args.n} FP64 (seeded U[1,10)/U[100,1000)/U[1,10))",
                    "step": "tableau build (untimed) + first K pivots per seed, oracle on host cores"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{pivs} pivots over {args.steps} steps of {args.m}x{args.n} LPs"},
+        "cpu_baseline": dict({"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                              "sample": f"{pivs} pivots over {args.steps} steps of {args.m}x{args.n} LPs, "
+                                        "the process pinned to one core"}, **host_cpu()),
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -358,23 +418,36 @@ def run_gpu(args, rank, world, local):
     oo = torch.empty(1, dtype=torch.float64).pin_memory()
     bo = torch.empty(m, dtype=torch.int32).pin_memory()
 
+    split = {"create_h2d_s": 0.0, "solve_s": 0.0, "readout_d2h_s": 0.0, "destroy_s": 0.0}
+
     def e2e_step(seed):
         A, b, c = pinned[seed]
-        h = tsx.lp_create(m, n, A, b, c)
+        t0 = time.perf_counter()
+        h = tsx.lp_create(m, n, A, b, c)      # H2D of A, b, c and the input check
+        t1 = time.perf_counter()
         try:
             st = tsx.lp_solve(h, tsx.options(skip_zero_columns=args.skip_zero, path=args.path,
                                              threads=args.threads, blocks=args.blocks,
                                              precision=prec, layout=layout))
+            t2 = time.perf_counter()
             if st != tsx.LP_OPTIMAL:
                 raise RuntimeError(f"solve ended {tsx.STATUS_NAMES.get(st, st)}")
             _, it = tsx.lp_get_solution(h, xo, yo, oo, bo)
-            return it
+            t3 = time.perf_counter()
         finally:
             tsx.lp_destroy(h)
+        t4 = time.perf_counter()
+        split["create_h2d_s"] += t1 - t0
+        split["solve_s"] += t2 - t1
+        split["readout_d2h_s"] += t3 - t2
+        split["destroy_s"] += t4 - t3
+        return it
 
     e2e_piv, e2e_secs = 0, 0.0
     if args.e2e_steps > 0:
         e2e_step(seeds[0])
+        for k in split:
+            split[k] = 0.0
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
@@ -425,7 +498,7 @@ def run_gpu(args, rank, world, local):
         upd_bytes = sum(s["update_bytes"] for s in stats) / len(stats)
         dense_bytes = sum(s["dense_update_bytes"] for s in stats) / len(stats)
         achieved = upd_bytes / (kernel_ms / 1000.0) / 1e9
-        traffic = profile_traffic(m, n, args.max_iters, args.layout)
+        traffic = profile_traffic(m, n, args.max_iters, args.layout, stats[0]["grid"], stats[0]["block"])
         launches = sum(s["kernel_launches"] + 4 for s in stats)   # + validate/reset + 2 extract
         cpu = None
         if not args.no_cpu_baseline:
@@ -469,7 +542,13 @@ def run_gpu(args, rank, world, local):
             },
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": 8 * (m * n + m + n),
-                    "d2h_bytes_per_step": 8 * (n + m + 1) + 4 * m},
+                    "d2h_bytes_per_step": 8 * (n + m + 1) + 4 * m,
+                    "steps": args.e2e_steps,
+                    "ms_per_step": {k.replace("_s", "_ms"): round(1e3 * v / max(1, args.e2e_steps), 3)
+                                    for k, v in split.items()},
+                    "what": "wall time per solve through the public API from pinned host buffers: "
+                            "lp_create (H2D + input check), lp_solve, lp_get_solution (D2H), "
+                            "lp_destroy"},
             "gpu_launches": launches * world,
             "clocks": clk,
         }
@@ -558,16 +637,18 @@ def batch_problems(count, seed):
 
 def oracle_batch_sample(problems, budget_s):
     import oracle
-    t0 = time.perf_counter()
-    done = 0
-    for A, b, c in problems:
-        oracle.solve(A, b, c, log_cap=1)
-        done += 1
-        if time.perf_counter() - t0 > budget_s:
-            break
-    secs = time.perf_counter() - t0
-    return {"value": done / secs, "unit": "LPs/s", "cores": 1, "kind": "oracle",
-            "sample": f"first {done} LPs of the batch, solved one by one (single-threaded C, FP64)"}
+    with pinned_to_one_core() as pin:
+        t0 = time.perf_counter()
+        done = 0
+        for A, b, c in problems:
+            oracle.solve(A, b, c, log_cap=1)
+            done += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        secs = time.perf_counter() - t0
+    return dict({"value": done / secs, "unit": "LPs/s", "cores": 1, "kind": "oracle",
+                 "sample": f"first {done} LPs of the batch, solved one by one (single-threaded C, FP64)",
+                 "pinned_core": pin.core}, **host_cpu())
 
 
 def run_batch(args, rank, world, local):

@@ -172,7 +172,7 @@ __device__ void batch_solve_one(const BatchParams& P, int k, unsigned char* smem
         const double ratio = dkey_value(best.rk);
         if (!dbits_finite(piv) || !dbits_finite(ratio)) { status = kNumeric; break; }
         // Step 3: scaled pivot row; the leaving variable takes slot qs
-        for (int j = tid; j <= n; j += NT) R[j] = j == qs ? __ddiv_rn(1.0, piv) : __ddiv_rn(T[(size_t)p * ldc + j], piv);
+        for (int j = tid; j <= n; j += NT) R[j] = __ddiv_rn(j == qs ? 1.0 : T[(size_t)p * ldc + j], piv);
         if (tid == 0) {
             const int leaving = basis[p - 1];
             basis[p - 1] = var[qs];
@@ -400,7 +400,7 @@ __device__ void batch_solve_one_flat(const BatchParams& P, int k, unsigned char*
         const double ratio = dkey_value(best.rk);
         if (!dbits_finite(piv) || !dbits_finite(ratio)) { status = kNumeric; break; }
         // Step 3: scaled pivot row; the leaving variable takes slot qs
-        for (int j = tid; j <= n; j += NT) R[j] = j == qs ? __ddiv_rn(1.0, piv) : __ddiv_rn(T[(size_t)p * ldc + j], piv);
+        for (int j = tid; j <= n; j += NT) R[j] = __ddiv_rn(j == qs ? 1.0 : T[(size_t)p * ldc + j], piv);
         if (tid == 0) {
             const int leaving = basis[p - 1];
             basis[p - 1] = var[qs];

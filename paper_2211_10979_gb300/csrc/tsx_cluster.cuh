@@ -320,7 +320,7 @@ __global__ void __launch_bounds__(NT) k_cluster_solve(ClusterParams P) {
         // Step 3, pivot row: this block's slice of R from row p at the owner
         for (int j = j0 + tid; j < j1; j += NT) {
             const double v = cl_ld_f64(cl_map(smem_addr(Tl + (size_t)pl * ldc + j), owner));
-            R[j] = j == qs ? __ddiv_rn(1.0, piv) : __ddiv_rn(v, piv);
+            R[j] = __ddiv_rn(j == qs ? 1.0 : v, piv);   // one division, whichever operand
         }
         __syncthreads();
         for (int t = tid; t < (j1 - j0) * (int)C; t += NT) {

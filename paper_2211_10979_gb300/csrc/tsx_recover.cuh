@@ -179,13 +179,19 @@ __global__ void __launch_bounds__(NT) k_rec_gj_inplace(double* M, int k, int* pi
     for (int c = 0; c < k; ++c) {
         const PivVal* cur = parts + (size_t)(c & 1) * gridDim.x;
         PivVal* nxt = parts + (size_t)((c + 1) & 1) * gridDim.x;
-        // the pivot of column c: every block merges the same posts
-        PivVal pv{-1.0, 0.0, INT_MAX, 0};
-        for (int b = lane; b < (int)gridDim.x; b += 32) {
-            const PivVal q{__ldcg(&cur[b].v), __ldcg(&cur[b].val), __ldcg(&cur[b].r), 0};
-            pivval_merge(pv, q);
+        // the pivot of column c: warp 0 of every block merges the same posts
+        if (warp == 0) {
+            PivVal pv{-1.0, 0.0, INT_MAX, 0};
+            for (int b = lane; b < (int)gridDim.x; b += 32) {
+                const PivVal q{__ldcg(&cur[b].v), __ldcg(&cur[b].val), __ldcg(&cur[b].r), 0};
+                pivval_merge(pv, q);
+            }
+            pv = warp_pivval(pv);
+            if (lane == 0) sp[0] = pv;
         }
-        pv = warp_pivval(pv);   // every warp computes it
+        __syncthreads();
+        const PivVal pv = sp[0];
+        __syncthreads();   // sp is written again by this step's post
         const int pr = pv.r;
         if (pr == INT_MAX || !(pv.v > 0.0)) {
             if (blockIdx.x == 0 && threadIdx.x == 0) *singular = 1;
@@ -220,12 +226,15 @@ __global__ void __launch_bounds__(NT) k_rec_gj_inplace(double* M, int k, int* pi
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int j = j0 + 32 * u;
-                    if (j < k) {
-                        const double w = __fma_rn(-l, P[j], j == c ? 0.0 : v[u]);
-                        row[j] = w;
-                        if (j == cn && unused) pivval_merge(best, PivVal{fabs(w), w, r, 0});
-                    }
+                    if (j < k) row[j] = __fma_rn(-l, P[j], j == c ? 0.0 : v[u]);
                 }
+            }
+            // the next column's candidate of this row, read back once (no
+            // predicated FP64 work inside the loop above)
+            __syncwarp();
+            if (lane == 0 && unused && cn < k) {
+                const double w = row[cn];
+                pivval_merge(best, PivVal{fabs(w), w, r, 0});
             }
         }
         if (cn < k) block_post_pivval<NT>(best, sp, nxt + blockIdx.x);
