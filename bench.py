@@ -619,12 +619,23 @@ def run_fp64_peak(args, rank, world, local):
     clocks = ClockSampler(local)
     clocks.start()
     tflops, info = fp64_fma_rate(tsx, sptr, seconds=1.0, repeats=max(1, args.steps))
+    # how the pipe charges partial warps and divisions (warp instructions/s)
+    from paper_2211_10979_gb300 import abi
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    blocks = props.multi_processor_count * 8
+    charge = {}
+    for op, name, iters in ((0, "fma", 20000), (1, "div", 2000)):
+        for lanes in (32, 16, 1):
+            abi.lp_measure_fp64_op_rate(op, lanes, blocks, 256, iters // 10, sptr)
+            ms, wps = abi.lp_measure_fp64_op_rate(op, lanes, blocks, 256, iters, sptr)
+            charge[f"{name}_lanes{lanes}_warp_instr_per_s"] = wps
+    charge["div_cost_in_fma"] = charge["fma_lanes32_warp_instr_per_s"] / charge["div_lanes32_warp_instr_per_s"]
     clk = clocks.stop()
     if rank == 0:
         print(json.dumps({"metric": "FP64 fma rate", "value": tflops, "unit": "TFLOP/s",
                           "fma_per_s": tflops * 1e12 / 2.0, "n_gpus": 1, "probe": info,
                           "nominal_tflops": FP64_PEAK_TFLOPS, "frac_of_nominal": tflops / FP64_PEAK_TFLOPS,
-                          "clocks": clk}), flush=True)
+                          "pipe_charge": charge, "clocks": clk}), flush=True)
     return 0
 
 

@@ -516,6 +516,14 @@ lp_status lp_generate_dense(int m, int n, unsigned long long seed, double *dA, d
 lp_status lp_measure_fp64_fma_rate(int blocks, int threads, long long iters, void *stream,
                                    double *ms_out, double *fma_per_s_out);
 
+/* Measurement helper, not part of the method: how the FP64 pipe charges a
+ * warp instruction.  Same launch as above, but only `lanes` (1..32) lanes of
+ * each warp run the chains, of op 0 = fma(a, x, y) or op 1 = IEEE division
+ * y / a.  *warp_ops_per_s_out receives warp instructions (chain steps of a
+ * warp) per second, whatever the active lanes.  HOST outputs, may be NULL. */
+lp_status lp_measure_fp64_op_rate(int op, int lanes, int blocks, int threads, long long iters,
+                                  void *stream, double *ms_out, double *warp_ops_per_s_out);
+
 /* Solve without allocating any device memory.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory
  * themselves or let the library do it -- for example a plugin running inside

@@ -31,7 +31,7 @@ EXPORTS = ("lp_options_init", "lp_create", "lp_create_device", "lp_solve", "lp_g
            "lp_batch_get_tableau", "lp_batch_get_stats", "lp_batch_destroy", "lps_options_init",
            "lps_open", "lps_submit", "lps_submit_device", "lps_wait", "lps_result", "lps_release",
            "lps_get_stats", "lps_last_error", "lps_close", "lp_generate_dense",
-           "lp_measure_fp64_fma_rate")
+           "lp_measure_fp64_fma_rate", "lp_measure_fp64_op_rate")
 LP_PENDING = 100
 
 # capacity of the library's fixed work-buffer array used by lp_solve_noalloc
@@ -237,6 +237,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "lp_measure_fp64_fma_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_longlong, vp,
                                                         ctypes.POINTER(ctypes.c_double),
                                                         ctypes.POINTER(ctypes.c_double)]),
+            "lp_measure_fp64_op_rate": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                       ctypes.c_longlong, vp, ctypes.POINTER(ctypes.c_double),
+                                                       ctypes.POINTER(ctypes.c_double)]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -482,6 +485,17 @@ def lp_measure_fp64_fma_rate(blocks: int, threads: int, iters: int, stream=None)
     ms, rate = ctypes.c_double(0.0), ctypes.c_double(0.0)
     st = load().lp_measure_fp64_fma_rate(int(blocks), int(threads), int(iters), stream,
                                          ctypes.byref(ms), ctypes.byref(rate))
+    if st != 0:
+        raise RuntimeError(lp_last_error())
+    return ms.value, rate.value
+
+
+def lp_measure_fp64_op_rate(op: int, lanes: int, blocks: int, threads: int, iters: int, stream=None):
+    """Measurement helper: (launch ms, warp instructions per second) of fma
+    (op 0) or division (op 1) chains with `lanes` active lanes per warp."""
+    ms, rate = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = load().lp_measure_fp64_op_rate(int(op), int(lanes), int(blocks), int(threads), int(iters), stream,
+                                        ctypes.byref(ms), ctypes.byref(rate))
     if st != 0:
         raise RuntimeError(lp_last_error())
     return ms.value, rate.value
