@@ -419,6 +419,7 @@ def run_gpu(args, rank, world, local):
     bo = torch.empty(m, dtype=torch.int32).pin_memory()
 
     split = {"create_h2d_s": 0.0, "solve_s": 0.0, "readout_d2h_s": 0.0, "destroy_s": 0.0}
+    create_dev = {"copy_ms": [], "check_ms": [], "wall_ms": []}   # lp_create's own timings, per step
 
     def e2e_step(seed):
         A, b, c = pinned[seed]
@@ -434,6 +435,10 @@ def run_gpu(args, rank, world, local):
                 raise RuntimeError(f"solve ended {tsx.STATUS_NAMES.get(st, st)}")
             _, it = tsx.lp_get_solution(h, xo, yo, oo, bo)
             t3 = time.perf_counter()
+            cs = tsx.lp_get_stats(h)
+            create_dev["copy_ms"].append(cs.create_copy_ms)
+            create_dev["check_ms"].append(cs.create_check_ms)
+            create_dev["wall_ms"].append(cs.create_wall_ms)
         finally:
             tsx.lp_destroy(h)
         t4 = time.perf_counter()
@@ -448,6 +453,8 @@ def run_gpu(args, rank, world, local):
         e2e_step(seeds[0])
         for k in split:
             split[k] = 0.0
+        for v in create_dev.values():
+            v.clear()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
@@ -546,9 +553,11 @@ def run_gpu(args, rank, world, local):
                     "steps": args.e2e_steps,
                     "ms_per_step": {k.replace("_s", "_ms"): round(1e3 * v / max(1, args.e2e_steps), 3)
                                     for k, v in split.items()},
+                    "create_ms_by_step": {k: [round(x, 3) for x in v] for k, v in create_dev.items()},
                     "what": "wall time per solve through the public API from pinned host buffers: "
                             "lp_create (H2D + input check), lp_solve, lp_get_solution (D2H), "
-                            "lp_destroy"},
+                            "lp_destroy; create_ms_by_step: lp_create's own device times of the "
+                            "copy and the check (CUDA events) and host time of the call"},
             "gpu_launches": launches * world,
             "clocks": clk,
         }

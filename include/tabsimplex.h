@@ -183,6 +183,15 @@ typedef struct {
     double dual_violation;        /* FP32 path: max(0, -min objective-row entry)*/
     double gap;                   /* FP32 path: |c^T x - b^T y|                 */
     int layout;                   /* LP_LAYOUT_CONDENSED or LP_LAYOUT_FULL      */
+    double create_copy_ms;        /* lp_create: device time of the host-to-
+                                     device copy of A, b, c (0: the handle came
+                                     from lp_create_device)                     */
+    double create_check_ms;       /* lp_create: device time of the input check
+                                     (0 when A, b, c are page-locked: the GPU
+                                     reads them over the host link and checks
+                                     them in the same pass, counted as copy)   */
+    double create_wall_ms;        /* lp_create: host time of the whole call
+                                     (allocation, copy, check, synchronisation) */
 } lp_stats;
 
 /* Fill *opt with the defaults listed above.  NULL is ignored. */
@@ -191,6 +200,10 @@ void lp_options_init(lp_options *opt);
 /* Create an LP from HOST arrays (Section III problem statement, Table I):
  * A is m x n row-major, b has m entries, c has n entries, all float64.  The
  * data are copied to the device; the caller keeps ownership of its arrays.
+ * When all three are page-locked (cudaHostAlloc, cudaHostRegister) and mapped
+ * for the current device, one kernel reads them over the host link and checks
+ * them in the same pass; otherwise they are copied with cudaMemcpyAsync and
+ * checked on the device.  Returns after the copy and the check completed.
  * Requires m > 0, n > 0, every entry finite and b >= 0 (the slack basis must be
  * feasible: Section III, Initialization Step; no phase I).  Returns NULL on
  * error (see lp_last_error()).  Runs on the current CUDA device. */

@@ -85,6 +85,9 @@ class lp_stats(ctypes.Structure):
         ("dual_violation", ctypes.c_double),
         ("gap", ctypes.c_double),
         ("layout", ctypes.c_int),
+        ("create_copy_ms", ctypes.c_double),
+        ("create_check_ms", ctypes.c_double),
+        ("create_wall_ms", ctypes.c_double),
     ]
 
     def as_dict(self):

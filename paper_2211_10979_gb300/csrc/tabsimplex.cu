@@ -150,6 +150,7 @@ struct lp_handle {
     std::vector<int> final_basis;    // float path: basic variables after the recovery
     long long iters = 0;
     lp_stats stats{};
+    double create_ms[3] = {0, 0, 0};   // lp_create: copy and check (device), whole call (host)
 };
 
 namespace {
@@ -410,12 +411,14 @@ static lp_handle* create_common(int m, int n, cudaStream_t stream, bool own_stre
     return h;
 }
 
-// Validates the device-resident inputs; returns false (and sets the error) if bad.
-static bool validate_inputs(lp_handle* h) {
+// Validates the device-resident inputs; returns false (and sets the error) if
+// bad.  `done` (may be null) is recorded on the handle stream after the check.
+static bool validate_inputs(lp_handle* h, cudaEvent_t done = nullptr) {
     k_reset_state<<<1, 32, 0, h->stream>>>(h->st);
     const size_t total = (size_t)h->m * h->n + h->m + h->n;
     int grid = (int)std::min<size_t>((total + 255) / 256, 4096);
     k_validate<<<grid, 256, 0, h->stream>>>(h->m, h->n, h->A, h->b, h->c, h->st);
+    if (done) cudaEventRecord(done, h->stream);
     int bad = 0;
     if (cudaMemcpyAsync(&bad, &h->st->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
         cudaStreamSynchronize(h->stream) != cudaSuccess) {
@@ -429,13 +432,37 @@ static bool validate_inputs(lp_handle* h) {
     return true;
 }
 
+// Device alias of a page-locked host array of `count` doubles (cudaHostAlloc,
+// cudaHostRegister, or torch's pinned tensors) that the current device may
+// read directly; null for pageable memory or memory not mapped for it.
+static const double* host_alias(const double* p, size_t count) {
+    cudaPointerAttributes a0{}, a1{};
+    if (cudaPointerGetAttributes(&a0, p) != cudaSuccess ||
+        cudaPointerGetAttributes(&a1, p + (count - 1)) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer ||
+        !a1.devicePointer)
+        return nullptr;
+    const char* d0 = static_cast<const char*>(a0.devicePointer);
+    if (static_cast<const char*>(a1.devicePointer) - d0 != (ptrdiff_t)((count - 1) * sizeof(double)))
+        return nullptr;   // not one mapping
+    return reinterpret_cast<const double*>(d0);
+}
+
 lp_t lp_create(int m, int n, const double* A, const double* b, const double* c) {
     if (!A || !b || !c) {
         set_error("lp_create: NULL input array");
         return nullptr;
     }
+    const auto t_call = std::chrono::steady_clock::now();
     lp_handle* h = create_common(m, n, nullptr, true);
     if (!h) return nullptr;
+    if (!ensure_events(h)) {
+        destroy_impl(h);
+        return nullptr;
+    }
     const size_t mn = (size_t)m * (size_t)n;
     Carve cv;
     const size_t o_A = cv.take(mn * sizeof(double));
@@ -450,6 +477,40 @@ lp_t lp_create(int m, int n, const double* A, const double* b, const double* c) 
     h->A = (const double*)(base + o_A);
     h->b = (const double*)(base + o_b);
     h->c = (const double*)(base + o_c);
+    const double* gA = host_alias(A, mn);
+    const double* gb = gA ? host_alias(b, (size_t)m) : nullptr;
+    const double* gc = gb ? host_alias(c, (size_t)n) : nullptr;
+    if (gc) {
+        // page-locked inputs: one kernel reads them over the host link,
+        // stores them and checks them (the check's time is part of the copy)
+        int nsm = 0;
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
+        cudaEventRecord(h->ev[0], h->stream);
+        k_reset_state<<<1, 32, 0, h->stream>>>(h->st);
+        k_ingest<<<std::max(1, nsm) * 2, 256, 0, h->stream>>>(gA, (double*)h->A, mn, gb, (double*)h->b, m, gc,
+                                                            (double*)h->c, n, h->st);
+        cudaEventRecord(h->ev[1], h->stream);
+        int bad = 0;
+        if (cudaMemcpyAsync(&bad, &h->st->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess) {
+            set_error("lp_create: reading the inputs failed: %s", cudaGetErrorString(cudaGetLastError()));
+            destroy_impl(h);
+            return nullptr;
+        }
+        if (bad) {
+            set_error("lp_create: inputs must be finite with b >= 0");
+            destroy_impl(h);
+            return nullptr;
+        }
+        float ms_copy = 0.f;
+        cudaEventElapsedTime(&ms_copy, h->ev[0], h->ev[1]);
+        cudaEventRecord(h->ready, h->stream);
+        h->create_ms[0] = ms_copy;
+        h->create_ms[1] = 0.0;
+        h->create_ms[2] = 1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - t_call).count();
+        return h;
+    }
+    cudaEventRecord(h->ev[0], h->stream);
     if (cudaMemcpyAsync((void*)h->A, A, mn * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaMemcpyAsync((void*)h->b, b, (size_t)m * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaMemcpyAsync((void*)h->c, c, (size_t)n * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
@@ -457,11 +518,18 @@ lp_t lp_create(int m, int n, const double* A, const double* b, const double* c) 
         destroy_impl(h);
         return nullptr;
     }
-    if (!validate_inputs(h)) {
+    cudaEventRecord(h->ev[1], h->stream);
+    if (!validate_inputs(h, h->ev[2])) {
         destroy_impl(h);
         return nullptr;
     }
+    float ms_copy = 0.f, ms_check = 0.f;
+    cudaEventElapsedTime(&ms_copy, h->ev[0], h->ev[1]);
+    cudaEventElapsedTime(&ms_check, h->ev[1], h->ev[2]);
     cudaEventRecord(h->ready, h->stream);
+    h->create_ms[0] = ms_copy;
+    h->create_ms[1] = ms_check;
+    h->create_ms[2] = 1e3 * std::chrono::duration<double>(std::chrono::steady_clock::now() - t_call).count();
     return h;
 }
 
@@ -2229,6 +2297,9 @@ lp_status lp_get_stats(lp_t h, lp_stats* stats) {
         return LP_ERR_STATE;
     }
     *stats = h->stats;
+    stats->create_copy_ms = h->create_ms[0];
+    stats->create_check_ms = h->create_ms[1];
+    stats->create_wall_ms = h->create_ms[2];
     return LP_OPTIMAL;
 }
 

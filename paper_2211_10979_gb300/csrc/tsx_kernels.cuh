@@ -2,6 +2,8 @@
 // tableau of doubles or floats (V):
 //   k_reset_state         zero the per-solve state word block
 //   k_validate            inputs finite, b >= 0 (create)
+//   k_ingest              create from page-locked host inputs: read over the
+//                         host link, copied and checked in one pass
 //   k_build<V>            Initialization Step: Table I tableau (full or
 //                         condensed), slack basis
 //   k_pivot_persistent    Steps 1-3 iterated inside one cooperative launch
@@ -52,6 +54,69 @@ __global__ void k_validate(int m, int n, const double* __restrict__ A, const dou
             v = c[k - mn - m];
             bad |= !isfinite(v);
         }
+    }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->bad, 1);
+}
+
+// lp_create from page-locked host inputs: the GPU reads A, b, c over the host
+// link itself (src = the arrays' device aliases) and checks them in the same
+// pass -- entries finite, b >= 0 (-0 allowed) -- so the inputs are read once
+// and no check kernel follows.  Checks on the bits (integer pipes).  16-byte
+// accesses for A where both addresses allow them; four in flight per thread.
+__device__ __forceinline__ int ingest_bad(unsigned long long u, int nonneg) {
+    const int nonfinite = ((u >> 52) & 0x7ffull) == 0x7ffull;
+    const int negative = nonneg && (u >> 63) && (u & 0x7fffffffffffffffull) != 0ull;
+    return nonfinite | negative;
+}
+
+__global__ void k_ingest(const double* __restrict__ sA, double* __restrict__ dA, size_t mn,
+                         const double* __restrict__ sb, double* __restrict__ db, int m,
+                         const double* __restrict__ sc, double* __restrict__ dc, int n, DevState* st) {
+    const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t nth = (size_t)gridDim.x * blockDim.x;
+    int bad = 0;
+    if ((((unsigned long long)sA | (unsigned long long)dA) & 15ull) == 0ull) {
+        const size_t np = mn / 2;
+        const ulonglong2* s2 = reinterpret_cast<const ulonglong2*>(sA);
+        ulonglong2* d2 = reinterpret_cast<ulonglong2*>(dA);
+        constexpr int U = 4;
+        size_t k = tid;
+        for (; k + (U - 1) * nth < np; k += U * nth) {
+            ulonglong2 v[U];
+#pragma unroll
+            for (int u = 0; u < U; ++u) v[u] = s2[k + u * nth];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                d2[k + u * nth] = v[u];
+                bad |= ingest_bad(v[u].x, 0) | ingest_bad(v[u].y, 0);
+            }
+        }
+        for (; k < np; k += nth) {
+            const ulonglong2 v = s2[k];
+            d2[k] = v;
+            bad |= ingest_bad(v.x, 0) | ingest_bad(v.y, 0);
+        }
+        if ((mn & 1) && tid == 0) {
+            const unsigned long long u = __double_as_longlong(sA[mn - 1]);
+            dA[mn - 1] = __longlong_as_double(u);
+            bad |= ingest_bad(u, 0);
+        }
+    } else {
+        for (size_t k = tid; k < mn; k += nth) {
+            const unsigned long long u = __double_as_longlong(sA[k]);
+            dA[k] = __longlong_as_double(u);
+            bad |= ingest_bad(u, 0);
+        }
+    }
+    for (size_t k = tid; k < (size_t)m; k += nth) {
+        const unsigned long long u = __double_as_longlong(sb[k]);
+        db[k] = __longlong_as_double(u);
+        bad |= ingest_bad(u, 1);
+    }
+    for (size_t k = tid; k < (size_t)n; k += nth) {
+        const unsigned long long u = __double_as_longlong(sc[k]);
+        dc[k] = __longlong_as_double(u);
+        bad |= ingest_bad(u, 0);
     }
     if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->bad, 1);
 }

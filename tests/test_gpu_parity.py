@@ -170,6 +170,60 @@ def test_invalid_inputs_rejected_on_device(tsx):
         tsx.Problem(A, b, np.array([1.0, np.inf, 2.0]))
 
 
+@pytest.mark.parametrize("m,n,offset", [(37, 53, 0), (37, 53, 1), (64, 64, 0), (1, 1, 0)])
+def test_page_locked_inputs_read_by_the_gpu(tsx, m, n, offset):
+    # page-locked A, b, c: one kernel reads them over the host link and checks
+    # them (odd m*n: the 16-byte loop's tail; offset 1: 8-byte aligned A, the
+    # element-wise loop); the solve equals the oracle's exactly
+    import torch
+    A, b, c = lpgen.dense_lp(m, n, 11 + m + n)
+    buf = torch.empty(m * n + offset, dtype=torch.float64).pin_memory()
+    buf[offset:] = torch.from_numpy(A.ravel())
+    pA = buf[offset:]
+    pb, pc = torch.from_numpy(b).pin_memory(), torch.from_numpy(c).pin_memory()
+    ref = _oracle_run(A, b, c)
+    h = tsx.lp_create(m, n, pA, pb, pc)
+    try:
+        assert tsx.lp_solve(h, tsx.options()) == ref.status
+        s = tsx.lp_get_stats(h)
+        assert s.create_copy_ms > 0 and s.create_check_ms == 0.0
+        T = np.empty_like(ref.T)
+        assert tsx.lp_get_tableau(h, T) == 0
+        np.testing.assert_array_equal(T, ref.T)
+    finally:
+        tsx.lp_destroy(h)
+    # b page-locked, A pageable: the copy-and-check path
+    h = tsx.lp_create(m, n, A, pb, pc)
+    try:
+        tsx.lp_solve(h, tsx.options())
+        assert tsx.lp_get_stats(h).create_check_ms > 0
+    finally:
+        tsx.lp_destroy(h)
+
+
+def test_page_locked_inputs_checked(tsx):
+    import torch
+    A, b, c = lpgen.dense_lp(5, 4, 3)
+    pin = lambda v: torch.from_numpy(np.ascontiguousarray(v)).pin_memory()
+    bad_b = b.copy()
+    bad_b[4] = -1e-300
+    with pytest.raises(ValueError, match="b >= 0"):
+        tsx.lp_create(5, 4, pin(A), pin(bad_b), pin(c))
+    zero_b = b.copy()
+    zero_b[0] = -0.0   # -0 >= 0
+    h = tsx.lp_create(5, 4, pin(A), pin(zero_b), pin(c))
+    tsx.lp_destroy(h)
+    for k, v in [(0, np.nan), (19, np.inf), (7, -np.inf)]:
+        bad_A = A.copy().ravel()
+        bad_A[k] = v
+        with pytest.raises(ValueError, match="finite"):
+            tsx.lp_create(5, 4, pin(bad_A), pin(b), pin(c))
+    bad_c = c.copy()
+    bad_c[3] = np.nan
+    with pytest.raises(ValueError, match="finite"):
+        tsx.lp_create(5, 4, pin(A), pin(b), pin(bad_c))
+
+
 def test_state_errors(tsx):
     A, b, c = lpgen.dense_lp(4, 3, 1)
     with tsx.Problem(A, b, c) as pr:
@@ -209,6 +263,29 @@ def test_stats_account_for_the_update(tsx, layout):
         assert ld == -(-W // 16) * 16
         assert 0 < stats["update_bytes"] <= 2.0 * (m + 1) * ld * 8 * it + side
     assert stats["pivot_ms"] > 0 and stats["kernel_launches"] >= 3
+
+
+def test_create_timings(tsx):
+    # lp_create times its own copy and input check (device) and the whole
+    # call (host); a handle over device inputs copies nothing
+    import torch
+    A, b, c = lpgen.dense_lp(512, 384, 5)
+    h = tsx.lp_create(512, 384, A, b, c)
+    try:
+        assert tsx.lp_solve(h, tsx.options(max_iters=3)) in (tsx.LP_OPTIMAL, tsx.LP_ITER_LIMIT)
+        s = tsx.lp_get_stats(h)
+        assert s.create_copy_ms > 0 and s.create_check_ms > 0
+        assert s.create_wall_ms >= s.create_copy_ms + s.create_check_ms
+    finally:
+        tsx.lp_destroy(h)
+    dev = [torch.from_numpy(v).cuda() for v in (A, b, c)]
+    h = tsx.lp_create_device(512, 384, *dev)
+    try:
+        tsx.lp_solve(h, tsx.options(max_iters=3))
+        s = tsx.lp_get_stats(h)
+        assert s.create_copy_ms == s.create_check_ms == s.create_wall_ms == 0.0
+    finally:
+        tsx.lp_destroy(h)
 
 
 # the cluster path (LP_PATH_CLUSTER, chosen by default for FP64 condensed LPs
