@@ -346,6 +346,18 @@ lp_batch_t lp_batch_create(int count, const int* m, const int* n, const double* 
     h->A = (const double*)(base + o_A);
     h->b = (const double*)(base + o_b);
     h->c = (const double*)(base + o_c);
+    const double* gA = host_alias(A, h->sum_mn);
+    const double* gb = gA ? host_alias(b, h->sum_m) : nullptr;
+    const double* gc = gb ? host_alias(c, h->sum_n) : nullptr;
+    if (gc) {   // page-locked inputs: read by one kernel over the host link
+        if (launch_ingest(gA, (double*)h->A, (size_t)h->sum_mn, gb, (double*)h->b, (size_t)h->sum_m, gc, (double*)h->c,
+                          (size_t)h->sum_n, nullptr, h->stream) != cudaSuccess) {
+            set_error("lp_batch_create: upload of the inputs failed");
+            lp_batch_destroy(h);
+            return nullptr;
+        }
+        return h;
+    }
     if (cudaMemcpyAsync((void*)h->A, A, sizeof(double) * h->sum_mn, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaMemcpyAsync((void*)h->b, b, sizeof(double) * h->sum_m, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaMemcpyAsync((void*)h->c, c, sizeof(double) * h->sum_n, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {

@@ -432,10 +432,8 @@ static bool validate_inputs(lp_handle* h, cudaEvent_t done = nullptr) {
     return true;
 }
 
-// Device alias of a page-locked host array of `count` doubles (cudaHostAlloc,
-// cudaHostRegister, or torch's pinned tensors) that the current device may
-// read directly; null for pageable memory or memory not mapped for it.
-static const double* host_alias(const double* p, size_t count) {
+const double* tsx::host_alias(const double* p, size_t count) {
+    if (!p || count == 0) return nullptr;
     cudaPointerAttributes a0{}, a1{};
     if (cudaPointerGetAttributes(&a0, p) != cudaSuccess ||
         cudaPointerGetAttributes(&a1, p + (count - 1)) != cudaSuccess) {
@@ -449,6 +447,15 @@ static const double* host_alias(const double* p, size_t count) {
     if (static_cast<const char*>(a1.devicePointer) - d0 != (ptrdiff_t)((count - 1) * sizeof(double)))
         return nullptr;   // not one mapping
     return reinterpret_cast<const double*>(d0);
+}
+
+cudaError_t tsx::launch_ingest(const double* sA, double* dA, size_t mn, const double* sb, double* db, size_t m,
+                               const double* sc, double* dc, size_t n, DevState* st, cudaStream_t s) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    k_ingest<<<std::max(1, nsm) * 2, 256, 0, s>>>(sA, dA, mn, sb, db, m, sc, dc, n, st);
+    return cudaGetLastError();
 }
 
 lp_t lp_create(int m, int n, const double* A, const double* b, const double* c) {
@@ -483,15 +490,13 @@ lp_t lp_create(int m, int n, const double* A, const double* b, const double* c) 
     if (gc) {
         // page-locked inputs: one kernel reads them over the host link,
         // stores them and checks them (the check's time is part of the copy)
-        int nsm = 0;
-        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, h->device);
         cudaEventRecord(h->ev[0], h->stream);
         k_reset_state<<<1, 32, 0, h->stream>>>(h->st);
-        k_ingest<<<std::max(1, nsm) * 2, 256, 0, h->stream>>>(gA, (double*)h->A, mn, gb, (double*)h->b, m, gc,
-                                                            (double*)h->c, n, h->st);
+        cudaError_t e = launch_ingest(gA, (double*)h->A, mn, gb, (double*)h->b, (size_t)m, gc, (double*)h->c, (size_t)n, h->st,
+                                      h->stream);
         cudaEventRecord(h->ev[1], h->stream);
         int bad = 0;
-        if (cudaMemcpyAsync(&bad, &h->st->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        if (e != cudaSuccess || cudaMemcpyAsync(&bad, &h->st->bad, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
             cudaStreamSynchronize(h->stream) != cudaSuccess) {
             set_error("lp_create: reading the inputs failed: %s", cudaGetErrorString(cudaGetLastError()));
             destroy_impl(h);

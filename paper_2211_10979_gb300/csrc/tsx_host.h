@@ -38,6 +38,18 @@ void event_put(cudaEvent_t e, bool timing);
 cudaStream_t stream_get();
 void stream_put(cudaStream_t s);
 
+// Device alias of a page-locked host array of `count` doubles (cudaHostAlloc,
+// cudaHostRegister, torch's pinned tensors) that the current device may read
+// directly; null for pageable memory or memory not mapped for it.
+const double* host_alias(const double* p, size_t count);
+
+struct DevState;
+// Uploads A (mn), b (m) and c (n) from their device aliases (host_alias) with
+// one kernel on stream s, reading over the host link; with st != null it also
+// checks them (entries finite, b >= 0) and sets st->bad on a violation.
+cudaError_t launch_ingest(const double* sA, double* dA, size_t mn, const double* sb, double* db, size_t m,
+                          const double* sc, double* dc, size_t n, DevState* st, cudaStream_t s);
+
 // Shared-memory bytes the batched solver has for one LP on the current device,
 // and whether an m x n LP fits in them.
 size_t batch_smem_limit();

@@ -61,7 +61,8 @@ __global__ void k_validate(int m, int n, const double* __restrict__ A, const dou
 // lp_create from page-locked host inputs: the GPU reads A, b, c over the host
 // link itself (src = the arrays' device aliases) and checks them in the same
 // pass -- entries finite, b >= 0 (-0 allowed) -- so the inputs are read once
-// and no check kernel follows.  Checks on the bits (integer pipes).  16-byte
+// and no check kernel follows (st == null: copy only, the batched solver's
+// upload, whose solve reports invalid inputs per LP).  Checks on the bits (integer pipes).  16-byte
 // accesses for A where both addresses allow them; four in flight per thread.
 __device__ __forceinline__ int ingest_bad(unsigned long long u, int nonneg) {
     const int nonfinite = ((u >> 52) & 0x7ffull) == 0x7ffull;
@@ -70,8 +71,8 @@ __device__ __forceinline__ int ingest_bad(unsigned long long u, int nonneg) {
 }
 
 __global__ void k_ingest(const double* __restrict__ sA, double* __restrict__ dA, size_t mn,
-                         const double* __restrict__ sb, double* __restrict__ db, int m,
-                         const double* __restrict__ sc, double* __restrict__ dc, int n, DevState* st) {
+                         const double* __restrict__ sb, double* __restrict__ db, size_t m,
+                         const double* __restrict__ sc, double* __restrict__ dc, size_t n, DevState* st) {
     const size_t tid = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     const size_t nth = (size_t)gridDim.x * blockDim.x;
     int bad = 0;
@@ -108,17 +109,17 @@ __global__ void k_ingest(const double* __restrict__ sA, double* __restrict__ dA,
             bad |= ingest_bad(u, 0);
         }
     }
-    for (size_t k = tid; k < (size_t)m; k += nth) {
+    for (size_t k = tid; k < m; k += nth) {
         const unsigned long long u = __double_as_longlong(sb[k]);
         db[k] = __longlong_as_double(u);
         bad |= ingest_bad(u, 1);
     }
-    for (size_t k = tid; k < (size_t)n; k += nth) {
+    for (size_t k = tid; k < n; k += nth) {
         const unsigned long long u = __double_as_longlong(sc[k]);
         dc[k] = __longlong_as_double(u);
         bad |= ingest_bad(u, 0);
     }
-    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&st->bad, 1);
+    if (__syncthreads_or(bad) && threadIdx.x == 0 && st) atomicOr(&st->bad, 1);
 }
 
 // Initialization Step (Section III, Table I): row 0 = [-c, 0 | 0],

@@ -118,6 +118,26 @@ def test_device_inputs(tsx):
         _check(bt.results(), problems, refs)
 
 
+def test_page_locked_inputs(tsx):
+    # page-locked packed inputs are read by one kernel over the host link; an
+    # invalid LP in them is still reported per LP by the solve
+    import torch
+    problems = _problems([(20, 30), (50, 10), (64, 64), (7, 9)], 91)
+    bad = list(problems[3])
+    bad[1] = bad[1].copy()
+    bad[1][2] = -1.0
+    problems[3] = tuple(bad)
+    refs = [oracle.solve(*p) for p in problems[:3]]
+    m = np.array([p[0].shape[0] for p in problems], dtype=np.int32)
+    n = np.array([p[0].shape[1] for p in problems], dtype=np.int32)
+    pA, pb, pc = (torch.from_numpy(np.concatenate([np.ravel(p[k]) for p in problems])).pin_memory() for k in range(3))
+    with tsx.Batch(m=m, n=n, A=pA, b=pb, c=pc) as bt:
+        bt.solve(tsx.batch_options())
+        sol = bt.results()
+        _check(sol, problems[:3], refs)
+        assert sol.status[3] == tsx.LP_ERR_INVALID
+
+
 @pytest.mark.parametrize("threads", [0, 64, 256, 512])
 def test_lps_beyond_shared_memory_use_global_workspace(tsx, threads):
     # condensed tableaux above the shared-memory limit (m = n = 200: 323 KB)
