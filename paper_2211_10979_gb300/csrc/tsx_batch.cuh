@@ -326,11 +326,12 @@ __device__ void batch_solve_one_flat(const BatchParams& P, int k, unsigned char*
     const int i_first = tid / W1, j_first = tid - (tid / W1) * W1;
     const int di = NT / W1, dj = NT - (NT / W1) * W1;
     const bool row0_warp = warp * 32 < W1;   // warps whose entries include row 0
+    const int NW0 = min(NW, (W1 + 31) / 32);   // ... are the first NW0 (the others post none)
     while (status == kRunning) {
         // Step 1: merge the objective-row partials of the previous update
         BArg a = sc.arg[0];
 #pragma unroll 1
-        for (int w = 1; w < NW; ++w) barg_merge(a, sc.arg[w]);
+        for (int w = 1; w < NW0; ++w) barg_merge(a, sc.arg[w]);
         const int qs = bland ? a.fslot : a.slot;
         if (qs < 0) { status = kOptimal; break; }
         if (it >= cap) { status = kIterLimit; break; }
@@ -339,24 +340,40 @@ __device__ void batch_solve_one_flat(const BatchParams& P, int k, unsigned char*
         // every eligible row without a usable estimate, on the candidate list
         if (tid == 0) F[0] = T[qs];
         float emin = __int_as_float(0x7f800000);   // +inf
+        // the thread's first row (its only one when m <= NT) keeps its screen
+        // result in a register for the second pass: -1 not eligible, NaN
+        // eligible without a usable estimate, else the estimate (> 0)
+        float scr0 = -1.f;
         for (int i = 1 + tid; i <= m; i += NT) {
             const double av = T[(size_t)i * ldc + qs];
             F[i] = av;
-            float est;
-            if (eligible_bits(av, eps_bits) && ratio_estimate(T[(size_t)i * ldc + n], av, est))
-                emin = fminf(emin, est);
+            float scr = -1.f;
+            if (eligible_bits(av, eps_bits)) {
+                float est;
+                if (ratio_estimate(T[(size_t)i * ldc + n], av, est)) {
+                    scr = est;
+                    emin = fminf(emin, est);
+                } else {
+                    scr = __int_as_float(0x7fc00000);
+                }
+            }
+            if (i == 1 + tid) scr0 = scr;
         }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) emin = fminf(emin, __shfl_xor_sync(0xffffffffu, emin, o));
         const float band = __fmul_ru(emin, 1.0f + 0x1p-18f);
         for (int base = 1 + warp * 32; base <= m; base += NT) {
-            const int i = base + lane;
+            const int i = base + lane;   // base == 1 + warp * 32: the row 1 + tid of the first pass
             bool keep = false;
             if (i <= m) {
-                const double av = F[i];
-                if (eligible_bits(av, eps_bits)) {
-                    float est;
-                    keep = !ratio_estimate(T[(size_t)i * ldc + n], av, est) || est <= band;
+                if (base == 1 + warp * 32) {
+                    keep = isnan(scr0) || (scr0 >= 0.f && scr0 <= band);
+                } else {
+                    const double av = F[i];
+                    if (eligible_bits(av, eps_bits)) {
+                        float est;
+                        keep = !ratio_estimate(T[(size_t)i * ldc + n], av, est) || est <= band;
+                    }
                 }
             }
             const unsigned ball = __ballot_sync(0xffffffffu, keep);
@@ -369,7 +386,9 @@ __device__ void batch_solve_one_flat(const BatchParams& P, int k, unsigned char*
         }
         __syncthreads();
         // Step 2, exact: warp 0 divides the candidates (IEEE division) and
-        // takes the minimum (ties: row, or basic variable in Bland mode)
+        // takes the minimum (ties: row, or basic variable in Bland mode).  One
+        // warp only: GB300's FP64 pipe charges a division by warp
+        // instruction, however few lanes are active.
         if (warp == 0) {
             BRat best = brat_none();
             const int nc = sc.ncand;
@@ -386,11 +405,21 @@ __device__ void batch_solve_one_flat(const BatchParams& P, int k, unsigned char*
                     brat_merge(best, cnd);
                 }
             }
-            best = warp_brat(best);
-            if (lane == 0) {
-                sc.rat_out = best;
-                sc.ncand = 0;
+            // lanes nc.. hold none while nc < 32: fold only the lanes with
+            // candidates into lane 0 (nothing to fold for a single candidate)
+            if (nc >= 32) {
+                best = warp_brat(best);
+            } else {
+                for (int o = 1; o < nc; o <<= 1) {
+                    BRat b;
+                    b.rk = __shfl_down_sync(0xffffffffu, best.rk, o);
+                    b.key = __shfl_down_sync(0xffffffffu, best.key, o);
+                    b.i = __shfl_down_sync(0xffffffffu, best.i, o);
+                    b.a = __shfl_down_sync(0xffffffffu, best.a, o);
+                    brat_merge(best, b);
+                }
             }
+            if (lane == 0) sc.rat_out = best;
         }
         __syncthreads();
         const BRat best = sc.rat_out;
@@ -399,13 +428,11 @@ __device__ void batch_solve_one_flat(const BatchParams& P, int k, unsigned char*
         const double piv = best.a;
         const double ratio = dkey_value(best.rk);
         if (!dbits_finite(piv) || !dbits_finite(ratio)) { status = kNumeric; break; }
-        // Step 3: scaled pivot row; the leaving variable takes slot qs
+        // Step 3: scaled pivot row; the leaving variable takes slot qs (the
+        // swap is written after the barrier below, when no warp reads them)
+        const int leaving = basis[p - 1];
+        const int entering = var[qs];
         for (int j = tid; j <= n; j += NT) R[j] = __ddiv_rn(j == qs ? 1.0 : T[(size_t)p * ldc + j], piv);
-        if (tid == 0) {
-            const int leaving = basis[p - 1];
-            basis[p - 1] = var[qs];
-            var[qs] = leaving;
-        }
         ++it;
         if (P.rule == 0) {
             if (best.rk <= 0) {   // ratio <= 0
@@ -417,9 +444,14 @@ __device__ void batch_solve_one_flat(const BatchParams& P, int k, unsigned char*
             }
         }
         __syncthreads();
+        if (tid == 0) {
+            sc.ncand = 0;   // every warp has read these before the barrier above
+            basis[p - 1] = entering;
+            var[qs] = leaving;
+        }
         // rank-1 update over the flat index space; row p becomes R; the
         // objective row's new entries feed the next Step 1
-        BArg an = flat_update(T, ldc, m, W1, n, F, R, qs, p, var, epsk, i_first, j_first, di, dj);
+        BArg an = flat_update(T, ldc, m, W1, n, F, R, qs, p, var, epsk, i_first, j_first, di, dj, leaving);
         if (row0_warp) an = warp_barg(an);
         if (lane == 0) sc.arg[warp] = an;
         __syncthreads();

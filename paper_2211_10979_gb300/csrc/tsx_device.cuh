@@ -62,6 +62,9 @@ constexpr int kRunning = 100;      // status while the iteration is in progress
 #ifndef TSX_ALTERNATE
 #define TSX_ALTERNATE 1   // alternate the update's sweep direction per pivot
 #endif
+#ifndef TSX_RHS_PREFETCH
+#define TSX_RHS_PREFETCH 1   // persistent kernel: P2's first right-hand side loaded before P1
+#endif
 constexpr int kRowsInFlight = 8;   // rows a warp loads before its first store (128 registers a thread)
 
 // Threads per SM of the persistent kernel with blocks of nt threads, and the
@@ -533,23 +536,34 @@ __device__ ArgPart phase_entering(const Params<V>& P, BlockScratch& s) {
     return block_arg(a, s);
 }
 
+// The right-hand side of the first row a thread scans in P2 (the row depends
+// only on the thread's index), loaded before P1 has found the entering column
+// so that P2 waits on one load instead of two in a row.
+template <typename V>
+__device__ __forceinline__ V ratio_rhs_first(const Params<V>& P) {
+    const long long i = (long long)threadIdx.x * gridDim.x + blockIdx.x;
+    return i <= P.m ? __ldcg(P.T + (size_t)i * (size_t)P.ld + (P.W - 1)) : V(0);
+}
+
 // P2: ratio test on column q and copy of column q into F; one partial per block.
 // Row i goes to block i mod G, so the divisions spread over every SM.
+// rhs0: the first row's right-hand side from ratio_rhs_first, or null.
 template <typename V>
-__device__ void phase_ratio(const Params<V>& P, int q, int bland, BlockScratch& s) {
+__device__ void phase_ratio(const Params<V>& P, int q, int bland, BlockScratch& s, const V* rhs0 = nullptr) {
     RatPart best = rat_none();
     const long long nth = (long long)gridDim.x * blockDim.x;
     if (blockIdx.x == 0 && threadIdx.x == 0) {   // counted again in P3 / P4
         P.st->nact = 0;
         P.st->next_slot = 0;
     }
-    for (long long i = (long long)threadIdx.x * gridDim.x + blockIdx.x; i <= P.m; i += nth) {
+    const long long i0 = (long long)threadIdx.x * gridDim.x + blockIdx.x;
+    for (long long i = i0; i <= P.m; i += nth) {
         const V* row = P.T + (size_t)i * (size_t)P.ld;
         const V a = __ldcg(row + q);
         __stcg(P.F + i, a);
         if (i >= 1 && (double)a > P.eps_p) {
             RatPart c;
-            c.r = (double)div_rn(__ldcg(row + (P.W - 1)), a);
+            c.r = (double)div_rn(i == i0 && rhs0 ? *rhs0 : __ldcg(row + (P.W - 1)), a);
             c.i = (int)i;
             c.key = bland ? __ldcg(P.basis + (i - 1)) : (int)i;
             c.a = (double)a;

@@ -247,12 +247,14 @@ __global__ void __launch_bounds__(NT, persistent_sm_threads(NT) / NT) k_pivot_pe
     int degen = 0;
     clk.start();
     for (;;) {
+        V rhs0 = V(0);
+        if (TSX_RHS_PREFETCH) rhs0 = ratio_rhs_first(P);   // in flight during Step 1
         const ArgPart e = phase_entering(P, s);           // Step 1
         const int q = bland ? e.fslot : e.slot;
         const int qv = bland ? e.fkey : e.key;
         if (qv == INT_MAX) { finish(P, kOptimal, it, bland, degen, clk.acc); return; }
         if (it >= P.max_iters) { finish(P, kIterLimit, it, bland, degen, clk.acc); return; }
-        phase_ratio(P, q, bland, s);                      // Step 2 (block partials)
+        phase_ratio(P, q, bland, s, TSX_RHS_PREFETCH ? &rhs0 : nullptr);   // Step 2 (block partials)
         clk.lap(0);
         if (!pivot_barrier(P.st, P.timeout_ns, s)) return;
         clk.lap(3);

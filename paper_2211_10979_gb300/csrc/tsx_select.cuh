@@ -139,9 +139,11 @@ __device__ __forceinline__ void barg_consider_key(BArg& a, double v, int vj, int
 // the returned partial holds.  (i, j) is the calling thread's first entry and
 // (di, dj) the step between its entries (NT threads).  Four entries are in
 // flight per thread.
+// var_qs >= 0: the variable slot qs holds after this pivot, for the
+// objective-row candidates (var[qs] may still be changing meanwhile).
 __device__ __forceinline__ BArg flat_update(double* T, int ld, int last, int W1, int n, const double* F,
                                            const double* R, int qs, int lp, const int* var, long long epsk,
-                                           int i, int j, int di, int dj) {
+                                           int i, int j, int di, int dj, int var_qs = -1) {
     BArg an = barg_none();
     // the objective row's entries (candidate test on each)
     for (; i == 0 && i <= last;) {
@@ -150,7 +152,7 @@ __device__ __forceinline__ BArg flat_update(double* T, int ld, int last, int W1,
         double v = __fma_rn(-F[0], r, j == qs ? 0.0 : *tp);
         if (lp == 0) v = r;
         *tp = v;
-        if (j < n) barg_consider_key(an, v, var[j], j, epsk);
+        if (j < n) barg_consider_key(an, v, j == qs && var_qs >= 0 ? var_qs : var[j], j, epsk);
         i += di;
         j += dj;
         if (j >= W1) { j -= W1; ++i; }
