@@ -452,7 +452,7 @@ __device__ void batch_solve_one_flat(const BatchParams& P, int k, unsigned char*
         // rank-1 update over the flat index space; row p becomes R; the
         // objective row's new entries feed the next Step 1
         BArg an = flat_update(T, ldc, m, W1, n, F, R, qs, p, var, epsk, i_first, j_first, di, dj, leaving);
-        if (row0_warp) an = warp_barg(an);
+        if (row0_warp) an = warp_barg_rule(an, bland);   // the next Step 1 reads these fields only
         if (lane == 0) sc.arg[warp] = an;
         __syncthreads();
     }

@@ -365,7 +365,7 @@ __global__ void __launch_bounds__(NT) k_cluster_solve(ClusterParams P) {
                 Tl[j] = v;
                 if (j < n) barg_consider_key(an, v, var[j], j, epsk);
             }
-            an = warp_barg(an);
+            an = warp_barg_rule(an, bland);   // the next Step 1 reads these fields only
             if (lane == 0) sc.arg[0] = an;
         } else {
             // the own constraint rows, flat over warps 1..NW-1

@@ -72,6 +72,29 @@ __device__ __forceinline__ BArg warp_barg(BArg a) {
     return a;
 }
 
+// The same for the fields the next Step 1 reads under the rule in force
+// (Dantzig: value, variable, slot; Bland: lowest variable and its slot); the
+// other fields keep the lane's own values.
+__device__ __forceinline__ BArg warp_barg_rule(BArg a, int bland) {
+    if (bland) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const int fv = __shfl_xor_sync(0xffffffffu, a.fvar, o);
+            const int fs = __shfl_xor_sync(0xffffffffu, a.fslot, o);
+            if (fv < a.fvar) { a.fvar = fv; a.fslot = fs; }
+        }
+    } else {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long vk = __shfl_xor_sync(0xffffffffu, a.vk, o);
+            const int v = __shfl_xor_sync(0xffffffffu, a.var, o);
+            const int sl = __shfl_xor_sync(0xffffffffu, a.slot, o);
+            if (vk < a.vk || (vk == a.vk && v < a.var)) { a.vk = vk; a.var = v; a.slot = sl; }
+        }
+    }
+    return a;
+}
+
 __device__ __forceinline__ BArg barg_none() {
     return BArg{kKeyInf, INT_MAX, -1, INT_MAX, -1};
 }
