@@ -566,13 +566,13 @@ lp_status lp_measure_fp64_op_rate(int op, int lanes, int blocks, int threads, lo
  * plus about 1.5 KiB of alignment and state, at most LP_NOALLOC_SCRATCH_BYTES
  * (about m + ld <= 2.2e5, e.g. m = n = 70000); larger sizes return LP_ERR_INVALID
  * before any device work, with the sizes in lp_last_error().
- * The first call on a device looks up the array's device address on that
- * device (the current one); make that first call before any stream capture.
  * Every call on a device uses the same array and leaves its contents behind
  * (each call resets what must start from zero), so calls whose GPU work
  * overlaps -- concurrent streams or host threads -- race: serialise them.
- * Blocks until the device is done; returns the termination status (>= 0) or
- * an error (< 0). */
+ * Blocks until the device is done (it reads status words back), so it cannot
+ * be recorded into a CUDA graph: on a stream that is being captured it
+ * returns LP_ERR_STATE without any device work.  Returns the termination
+ * status (>= 0) or an error (< 0). */
 #define LP_NOALLOC_SCRATCH_BYTES (2u * 1024u * 1024u)
 lp_status lp_solve_noalloc(int m, int n, const double *dA, const double *db,
                            const double *dc, double *dT, long long ld,

@@ -2444,6 +2444,18 @@ lp_status lp_solve_noalloc(int m, int n, const double* dA, const double* db, con
                   kNoAllocMaxGrid);
         return LP_ERR_INVALID;
     }
+    {   // the call reads results back and waits for the device: no stream capture
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(static_cast<cudaStream_t>(o.stream), &cs) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("lp_solve_noalloc: cannot query the stream's capture state");
+            return LP_ERR_CUDA;
+        }
+        if (cs != cudaStreamCaptureStatusNone) {
+            set_error("lp_solve_noalloc: the stream is being captured; this call blocks and cannot be captured");
+            return LP_ERR_STATE;
+        }
+    }
     // layout of the array: F | R | act | cpart | rpart | state
     const size_t nstrips = ((size_t)ld + 127) / 128;
     const size_t off_R = align_up((size_t)(m + 1) * sizeof(double), 256);

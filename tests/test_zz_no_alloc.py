@@ -157,3 +157,31 @@ def test_noalloc_rejects_sizes_beyond_the_array(env):
     st, _ = tsx.lp_solve_noalloc(4, 3, fake, fake, fake, fake, 8, fake,
                                  tsx.options(log_capacity=10))
     assert st == tsx.LP_ERR_INVALID
+
+
+def test_noalloc_refuses_a_capturing_stream(env):
+    # the call reads status words back and waits for the device, so it cannot
+    # be recorded into a graph: on a capturing stream it returns LP_ERR_STATE
+    # before any device work, and the capture itself completes
+    torch, tsx = env
+    m, n = 6, 5
+    A, b, c = lpgen.dense_lp(m, n, 3)
+    dA, db, dc = (torch.from_numpy(v).cuda() for v in (A, b, c))
+    ld = (n + m + 1 + 3) // 4 * 4
+    dT = torch.zeros((m + 1) * ld, dtype=torch.float64, device="cuda")
+    dbasis = torch.zeros(m, dtype=torch.int32, device="cuda")
+    x = torch.zeros(4, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        x.add_(1.0)
+        st, iters = tsx.lp_solve_noalloc(m, n, dA, db, dc, dT, ld, dbasis, tsx.options(stream=s.cuda_stream))
+    assert st == tsx.LP_ERR_STATE and iters == 0
+    assert "captured" in tsx.lp_last_error()
+    g.replay()
+    torch.cuda.synchronize()
+    assert x.tolist() == [1.0] * 4
+    # outside the capture the same call solves
+    st, _ = tsx.lp_solve_noalloc(m, n, dA, db, dc, dT, ld, dbasis, tsx.options(stream=s.cuda_stream))
+    assert st == tsx.LP_OPTIMAL
