@@ -99,7 +99,7 @@ def parse_args(argv=None):
     if args.steps is None:
         args.steps = 2000 if args.workload == "batch" else 6
     if args.e2e_steps < 0:
-        args.e2e_steps = 3 if args.workload == "batch" else args.steps
+        args.e2e_steps = 100 if args.workload == "batch" else args.steps
     if args.precision == "fp32" and args.max_iters >= 0:
         # the FP32 path treats a pivot cap as the end of its float phase and
         # lets the FP64 cleanup finish the solve: a truncated FP32 solve is not
