@@ -451,6 +451,11 @@ def run_gpu(args, rank, world, local):
     e2e_piv, e2e_secs = 0, 0.0
     if args.e2e_steps > 0:
         e2e_step(seeds[0])
+        # warm-up: one upload from every pinned buffer (the GPU's first read of
+        # a pinned buffer maps it and runs at ~50 GB/s; later reads at the
+        # link's ~210 GB/s), untimed
+        for s_ in seeds[1:]:
+            tsx.lp_destroy(tsx.lp_create(m, n, *pinned[s_]))
         for k in split:
             split[k] = 0.0
         for v in create_dev.values():
