@@ -350,7 +350,9 @@ void lp_batch_options_init(lp_batch_options *opt);
 /* Create a batch from HOST arrays: LP k has m[k] constraints and n[k]
  * variables; A holds the LPs' constraint matrices back to back (each m[k] x
  * n[k] row-major), b the right-hand sides back to back (sum of m[k]) and c the
- * price vectors back to back (sum of n[k]).  Copied to the device.  Each LP
+ * price vectors back to back (sum of n[k]).  Copied to the device before
+ * the call returns (page-locked arrays are read by one kernel over the host
+ * link, others copied with cudaMemcpyAsync).  Each LP
  * needs m, n > 0, else NULL (lp_last_error names the LP).  Per-LP input errors
  * found on the device (non-finite data, b < 0) are reported as that LP's
  * status. */

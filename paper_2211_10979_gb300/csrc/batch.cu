@@ -351,8 +351,9 @@ lp_batch_t lp_batch_create(int count, const int* m, const int* n, const double* 
     const double* gc = gb ? host_alias(c, h->sum_n) : nullptr;
     if (gc) {   // page-locked inputs: read by one kernel over the host link
         if (launch_ingest(gA, (double*)h->A, (size_t)h->sum_mn, gb, (double*)h->b, (size_t)h->sum_m, gc, (double*)h->c,
-                          (size_t)h->sum_n, nullptr, h->stream) != cudaSuccess) {
-            set_error("lp_batch_create: upload of the inputs failed");
+                          (size_t)h->sum_n, nullptr, h->stream) != cudaSuccess ||
+            cudaStreamSynchronize(h->stream) != cudaSuccess) {   // the caller may reuse its arrays on return
+            set_error("lp_batch_create: upload of the inputs failed: %s", cudaGetErrorString(cudaGetLastError()));
             lp_batch_destroy(h);
             return nullptr;
         }
@@ -362,6 +363,13 @@ lp_batch_t lp_batch_create(int count, const int* m, const int* n, const double* 
         cudaMemcpyAsync((void*)h->b, b, sizeof(double) * h->sum_m, cudaMemcpyHostToDevice, h->stream) != cudaSuccess ||
         cudaMemcpyAsync((void*)h->c, c, sizeof(double) * h->sum_n, cudaMemcpyHostToDevice, h->stream) != cudaSuccess) {
         set_error("lp_batch_create: host-to-device copy failed");
+        lp_batch_destroy(h);
+        return nullptr;
+    }
+    // a page-locked array among the inputs is copied asynchronously: wait, so
+    // that the caller may reuse its arrays on return
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+        set_error("lp_batch_create: host-to-device copy failed: %s", cudaGetErrorString(cudaGetLastError()));
         lp_batch_destroy(h);
         return nullptr;
     }
