@@ -62,6 +62,12 @@ constexpr int kRunning = 100;      // status while the iteration is in progress
 #ifndef TSX_ALTERNATE
 #define TSX_ALTERNATE 1   // alternate the update's sweep direction per pivot
 #endif
+#ifndef TSX_SLOT_PIPE
+#define TSX_SLOT_PIPE 1      // the update's next grab read after the current slot, not before it
+#endif
+#ifndef TSX_STATIC_FIRST
+#define TSX_STATIC_FIRST 1   // each warp's first update slot given by its index, not the counter
+#endif
 #ifndef TSX_RHS_PREFETCH
 #define TSX_RHS_PREFETCH 1   // persistent kernel: P2's first right-hand side loaded before P1
 #endif
@@ -710,14 +716,28 @@ __device__ void phase_update_bulk(const Params<V>& P, int p, int zq, unsigned na
     // float update has twice the slots per pivot, and pairs keep the counter's
     // atomics off its critical path)
     constexpr unsigned grab = TSX_GRAB > 0 ? (unsigned)TSX_GRAB : (sizeof(V) == 8 ? 1u : 2u);
-    unsigned next = 0;
-    if (lane == 0) next = atomicAdd(&P.st->next_slot, grab);
-    next = __shfl_sync(0xffffffffu, next, 0);
-    while ((long long)next < total) {
-        const long long u0 = next;
+    // TSX_STATIC_FIRST: warp w of the grid takes slots w*grab .. first, without
+    // the counter, and the counter hands out the slots after the first
+    // (warps x grab).  TSX_SLOT_PIPE: the grab for a warp's next slot is
+    // requested before the current slot and read after it, so its round trip
+    // never holds the warp (reading it at once would).
+    const long long base = TSX_STATIC_FIRST ? (((long long)gridDim.x * blockDim.x) >> 5) * grab : 0;
+    unsigned mine = 0;   // lane 0: a requested grab
+    if (lane == 0) mine = atomicAdd(&P.st->next_slot, grab);
+    long long cur;
+    if (TSX_STATIC_FIRST) {
+        cur = (((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * grab;
+    } else {
+        cur = (long long)__shfl_sync(0xffffffffu, mine, 0);
+        if (lane == 0 && cur < total) mine = atomicAdd(&P.st->next_slot, grab);
+    }
+    while (cur < total) {
+        const long long u0 = cur;
         const long long u1 = min(total, u0 + (long long)grab);
-        if (lane == 0) next = atomicAdd(&P.st->next_slot, grab);
-        next = __shfl_sync(0xffffffffu, next, 0);
+        if (!TSX_SLOT_PIPE) {
+            cur = base + (long long)__shfl_sync(0xffffffffu, mine, 0);
+            if (lane == 0 && cur < total) mine = atomicAdd(&P.st->next_slot, grab);
+        }
         for (long long u = u0; u < u1; ++u) {
             // odd pivots sweep backwards: they start on the rows the previous
             // sweep wrote last, which are still in L2
@@ -732,6 +752,10 @@ __device__ void phase_update_bulk(const Params<V>& P, int p, int zq, unsigned na
                 for (int k = 0; k < R; ++k) f[k] = k < nrows ? __ldcg(P.F + i0 + k) : V(0);
             }
             update_slot<V, R>(P, p, zq, nact, c, i0, nrows, f);
+        }
+        if (TSX_SLOT_PIPE) {
+            cur = base + (long long)__shfl_sync(0xffffffffu, mine, 0);
+            if (lane == 0 && cur < total) mine = atomicAdd(&P.st->next_slot, grab);
         }
     }
 }
