@@ -230,7 +230,9 @@ struct PhaseClock {
 // Steps 1-3 iterated inside one cooperative launch; three grid barriers per
 // pivot (after P2, after P3, after P4).  Every block takes the same decisions
 // from the same reduced values, so all leave the loop together.
-template <int NT, typename V>
+// RS: rows of an update slot (fewer for LPs whose slots would be too few to
+// spread evenly over the grid's warps).
+template <int NT, typename V, int RS = persistent_rows(NT)>
 __global__ void __launch_bounds__(NT, persistent_sm_threads(NT) / NT) k_pivot_persistent(Params<V> P) {
     __shared__ BlockScratch s;
     __shared__ PhaseClock clk;
@@ -267,7 +269,7 @@ __global__ void __launch_bounds__(NT, persistent_sm_threads(NT) / NT) k_pivot_pe
         clk.lap(1);
         if (!pivot_barrier(P.st, P.timeout_ns, s)) return;
         clk.lap(4);
-        phase_update<V, persistent_rows(NT)>(P, l.i, q, it, ringp);   // Step 3 (rank-1 update)
+        phase_update<V, RS>(P, l.i, q, it, ringp);   // Step 3 (rank-1 update)
         ++it;
         degeneracy_step(P, l.r, bland, degen);
         clk.lap(2);
