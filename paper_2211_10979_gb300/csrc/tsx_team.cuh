@@ -246,7 +246,10 @@ __device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, Team
     int bland = P.rule == 1, degen = 0;
     int status = ld_relaxed(&ts->bad) ? kInvalid : kRunning;
     const int lo = max(r0, 1);
+    const int i_first = lo + (int)threadIdx.x;   // the thread's first row in Step 2
     while (status == kRunning) {
+        // its right-hand side, in flight while Step 1's candidate is read
+        const V rhs0 = i_first < r1 ? __ldcg(J.T + (size_t)i_first * (size_t)ld + n) : V(0);
         const ArgPart e = load_arg(&ts->ent);                // Step 1
         const int q = bland ? e.fslot : e.slot;
         const int qv = bland ? e.fkey : e.key;
@@ -255,13 +258,13 @@ __device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, Team
         // Step 2 on the block's rows; their column-q entries become the multipliers
         RatPart best = rat_none();
         if (bt == 0 && threadIdx.x == 0) Floc[0] = __ldcg(J.T + q);
-        for (int i = lo + threadIdx.x; i < r1; i += blockDim.x) {
+        for (int i = i_first; i < r1; i += blockDim.x) {
             const V* row = J.T + (size_t)i * (size_t)ld;
             const V a = __ldcg(row + q);
             Floc[i - r0] = a;
             if ((double)a > P.eps_p) {
                 RatPart c;
-                c.r = (double)div_rn(__ldcg(row + n), a);
+                c.r = (double)div_rn(i == i_first ? rhs0 : __ldcg(row + n), a);
                 c.i = i;
                 c.key = bland ? __ldcg(J.basis + (i - 1)) : i;
                 c.a = (double)a;
