@@ -71,7 +71,10 @@ def _certificate(A, b, c, x, y, obj, tol=1e-9):
     assert abs(b @ y - obj) <= tol * scale
 
 
-@pytest.mark.parametrize("m,n,layout", [(8192, 8192, 0), (4096, 16384, 0), (8192, 8192, 1)])
+# (3071, 3072) and (3072, 3072): the last size with 8-row update slots and
+# the first with 16-row slots
+@pytest.mark.parametrize("m,n,layout", [(8192, 8192, 0), (4096, 16384, 0), (8192, 8192, 1),
+                                        (3071, 3072, 0), (3072, 3072, 0)])
 def test_full_size_first_pivots_and_certificates(tsx, m, n, layout):
     # layout 0 (the bench's): condensed device tableau, expanded to Table I on
     # read-out, so the unit-column check below holds by construction there and
