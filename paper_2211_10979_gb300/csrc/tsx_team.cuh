@@ -24,6 +24,9 @@ constexpr int kTeamMax = 160;  // blocks per team, upper bound
 #ifndef TSX_TEAM_SM_THREADS
 #define TSX_TEAM_SM_THREADS 512   // threads per SM the team kernel is compiled for
 #endif
+#ifndef TSX_TEAM_SLICE_LD
+#define TSX_TEAM_SLICE_LD 1024   // FP64 rows this long or longer: row p scaled a slice per block
+#endif
 // Threads per SM of the team kernel with blocks of nt threads, and the rows a
 // warp of its update keeps in flight (16 where a thread may hold 255 registers).
 __host__ __device__ constexpr int team_sm_threads(int nt) { return nt > TSX_TEAM_SM_THREADS ? nt : TSX_TEAM_SM_THREADS; }
@@ -282,9 +285,22 @@ __device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, Team
         const int p = l.i;
         const V piv = (V)l.a;
         if (!isfinite((double)piv) || !isfinite(l.r)) { status = kNumeric; break; }
-        // Step 3: every block scales row p itself; the leaving variable takes slot q
-        const V* rowp = J.T + (size_t)p * (size_t)ld;
-        for (int j = threadIdx.x; j < ld; j += blockDim.x) R[j] = div_rn(j == q ? V(1) : __ldcg(rowp + j), piv);
+        // Step 3, pivot row; the leaving variable takes slot q.  FP64 rows of
+        // TSX_TEAM_SLICE_LD entries or more: each block scales its slice of
+        // row p in place (the new row p), a team barrier, then every block
+        // reads the whole row (GB300's FP64 pipe charges ~9 fused
+        // multiply-adds per division, ld of them a block otherwise).  Shorter
+        // or FP32 rows: every block scales the whole row itself.
+        V* rowp = J.T + (size_t)p * (size_t)ld;
+        const bool slice = sizeof(V) == 8 && ld >= TSX_TEAM_SLICE_LD;
+        if (slice) {
+            const int sl = (ld + (int)C - 1) / (int)C;
+            const int j0 = min(ld, bt * sl), j1 = min(ld, j0 + sl);
+            for (int j = j0 + (int)threadIdx.x; j < j1; j += blockDim.x)
+                rowp[j] = div_rn(j == q ? V(1) : __ldcg(rowp + j), piv);
+        } else {
+            for (int j = threadIdx.x; j < ld; j += blockDim.x) R[j] = div_rn(j == q ? V(1) : __ldcg(rowp + j), piv);
+        }
         if (bt == 0 && threadIdx.x == 0) {
             const int leaving = J.basis[p - 1];
             J.basis[p - 1] = qv;
@@ -299,12 +315,16 @@ __device__ bool team_solve_one(const TeamParams<V>& P, const TeamJob<V>& J, Team
                 bland = 0;
             }
         }
+        if (slice) {
+            if (!team_barrier(ts, C, P.timeout_ns, sok, tpass)) return false;
+            for (int j = threadIdx.x; j < ld; j += blockDim.x) R[j] = __ldcg(rowp + j);
+        }
         __syncthreads();
         if (bt == 0) team_row0(J, R, Floc[0], q, P, ts, s);   // the next Step 1 on the new row 0
         team_update<V, RF>(J, R, Floc, r0, lo, r1, p, q);
         ++it;
         if (!team_barrier(ts, C, P.timeout_ns, sok, tpass)) return false;
-        if (p >= r0 && p < r1) {   // every block has read row p: its owner stores R there
+        if (!slice && p >= r0 && p < r1) {   // every block has read row p: its owner stores R there
             for (int j = threadIdx.x; j < ld; j += blockDim.x) J.T[(size_t)p * (size_t)ld + j] = R[j];
             __syncthreads();
         }

@@ -27,7 +27,7 @@ def tsx():
 
 
 SHAPES = [(1, 1), (1, 9), (9, 1), (3, 4), (37, 53), (64, 64), (200, 150), (150, 200), (300, 700),
-          (700, 300), (1024, 512), (129, 257), (16, 2000), (2000, 16)]
+          (700, 300), (1024, 512), (129, 257), (16, 2000), (2000, 16), (600, 1100)]
 
 
 def _check(tsx, pr, ref, tableau=True):
